@@ -1,0 +1,387 @@
+"""Throughput benchmark of the colour-gradient LBM step (MLUPS = million fluid-node updates/s).
+
+Default workload: the batched parameter sweep -- 64 displacement channels, widths W drawn
+from U{40..200} (seed 0), lengths 10 W, velocity inlet / pressure outlet, walls top and
+bottom, (M, Ca, theta) drawn from the grids M in {1,5,20,50,100}, Ca in {0.01,0.05,0.1},
+theta in {30,...,150} deg -- in FP32.  One benchmark step = one time step of all 64
+channels (one launch per kernel for the whole batch).  The state (about 1.5 GB) is far
+larger than the 129 MB L2, so no flush is needed; smaller workloads flush L2 before every
+timed step and are timed per step with CUDA events.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--precision P]
+    python bench.py --impl reference ...      # the FP64 CPU oracle on the host cores
+
+Under torchrun each rank runs its own batch (weak scaling, no collective on the data path);
+rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+from paper_1707_00198_gb300 import inputs as I  # noqa: E402
+
+L2_BYTES = 129 * 2 ** 20
+STORE_BYTES = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}
+DTYPE = {"fp64": "f64", "fp32": "f32", "fp16": "f16-store/f32-math", "bf16": "bf16-store/f32-math"}
+
+
+# ----------------------------------------------------------------------------- workloads
+def workload(name: str, seed: int = 0):
+    if name == "batched_sweep":
+        return I.channel_sweep(64, seed=seed), "64 displacement channels, W~U{40..200}, L=10W, (M,Ca,theta) grids"
+    if name == "capillary":
+        g, p = I.config_capillary()
+        return ([g], [p]), "capillary filling 1200x80, d=40, L=800, theta=30deg, sigma=1e-2"
+    if name == "fingering":
+        g, p = I.config_fingering(M=1.0, Ca=0.05, theta_deg=90.0, seed=seed)
+        return ([g], [p]), "displacement channel 2000x102, M=1, Ca=0.05, theta=90deg"
+    if name == "static_droplet":
+        g, p = I.config_static_droplet()
+        return ([g], [p]), "static droplet 100x50, R=20, theta=60deg"
+    if name == "roofline_box":
+        g = I.two_wall_box(8192, 4096, bands=8, noise=1e-3, seed=seed)
+        return ([g], [I.Params(sigma=0.01, theta=math.radians(60))]), "two-wall box 8192x4096, 8 colour bands"
+    raise SystemExit(f"unknown workload {name}")
+
+
+def reference_sample(geoms, prms):
+    """A bounded sample of the workload for the CPU oracle: the first lattice cropped to a
+    100-node-long section (same width, boundaries and parameters)."""
+    g, p = geoms[0], prms[0]
+    if g.bc_x == "inout":
+        g2 = I.displacement_channel(W=g.ny - 2, L=min(100, g.nx), x_I=min(25.0, g.nx / 4), seed=7)
+    else:
+        nx = min(100, g.nx)
+        bc_x = g.bc_x
+        solid = g.solid[:, :nx].copy()
+        if bc_x == "closed":
+            solid[:, -1] = 1
+        g2 = I.Geometry(nx, g.ny, solid, g.rhoN0[:, :nx].copy(), bc_x=bc_x, bc_y=g.bc_y)
+    return g2, p
+
+
+def fluid_nodes(geoms) -> int:
+    return int(sum(int((g.solid == 0).sum()) for g in geoms))
+
+
+# ----------------------------------------------------------------------------- helpers
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        os.unlink(self.path)
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            r = [c.strip() for c in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def kernel_source_digest() -> str:
+    h = hashlib.sha256()
+    for f in ("lbcg_kernels.cu", "lbcg_device.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1707_00198_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str, n_fluid: int):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, scaled by fluid
+    nodes, or None if the kernel source changed since the counters were taken."""
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))[kernel]
+    except Exception:
+        return None
+    if rec.get("src_digest") != kernel_source_digest():
+        return None
+    return rec["dram_bytes_per_fluid_node"] * n_fluid
+
+
+def cpu_oracle_rate(geoms, prms, budget_s: float = 15.0, max_steps: int = 100000):
+    """Time the FP64 oracle (as it stands) on a bounded sample; returns (MLUPS, steps, nodes, cores)."""
+    from oracle import lbcg_oracle as O
+    g, p = reference_sample(geoms, prms)
+    lat = O.make_lattice(g, p.theta)
+    fR, fB = O.init_state(lat, g.rhoN0, p.rho0)
+    nf = int((g.solid == 0).sum())
+    t0 = time.perf_counter()
+    fR, fB = O.run(lat, p, fR, fB, 2)
+    per = (time.perf_counter() - t0) / 2
+    n = int(max(3, min(max_steps, budget_s / max(per, 1e-6))))
+    t0 = time.perf_counter()
+    O.run(lat, p, fR, fB, n)
+    dt = time.perf_counter() - t0
+    return nf * n / dt / 1e6, n, (g.nx, g.ny, nf), torch.get_num_threads()
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import lbcg_oracle as O
+    (geoms, prms), desc = workload(args.workload, seed=0)
+    g, p = reference_sample(geoms, prms)
+    lat = O.make_lattice(g, p.theta)
+    fR, fB = O.init_state(lat, g.rhoN0, p.rho0)
+    nf = int((g.solid == 0).sum())
+    fR, fB = O.run(lat, p, fR, fB, args.warmup)
+    t0 = time.perf_counter()
+    fR, fB = O.run(lat, p, fR, fB, args.steps)
+    dt = time.perf_counter() - t0
+    v = nf * args.steps / dt / 1e6
+    sample = f"{g.nx}x{g.ny} section ({nf} fluid nodes) of the first lattice of: {desc}"
+    line = {"impl": "reference", "metric": "MLUPS", "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "description": desc, "precision": "fp64 (CPU oracle)"},
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": torch.get_num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- our arm
+def timed_steps(lat, stream, K, flush_buf):
+    """K steps; returns total device ms (per-step events when flushing L2 between steps)."""
+    from paper_1707_00198_gb300 import lbcg
+    if flush_buf is None:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(K):
+            lat.step(1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    with torch.cuda.stream(stream):
+        for k in range(K):
+            flush_buf.add_(1)
+            evs[k][0].record(stream)
+            lat.step(1)
+            evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in evs)
+
+
+def measure_form(geoms, prms, precision, K, W, stream, with_profile=False):
+    from paper_1707_00198_gb300 import lbcg
+    lat = lbcg.Lattice(geoms, prms, precision, stream=stream.cuda_stream)
+    lat.step(W)
+    torch.cuda.synchronize()
+    flush = None
+    if lat.state_bytes < 2 * L2_BYTES:
+        flush = torch.zeros(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    if with_profile:
+        lbcg.lbcg_profile(lat.h, True)
+    ms = timed_steps(lat, stream, K, flush)
+    kt = None
+    if with_profile:
+        kt = lbcg.lbcg_kernel_times(lat.h)
+        lbcg.lbcg_profile(lat.h, False)
+    return lat, ms, kt, flush is not None
+
+
+def run_ours(args):
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_1707_00198_gb300 import lbcg
+
+    (geoms, prms), desc = workload(args.workload, seed=rank)
+    nf = fluid_nodes(geoms)
+    nodes = sum(g.nx * g.ny for g in geoms)
+    stream = torch.cuda.Stream()
+    s_bytes = STORE_BYTES[args.precision]
+
+    # ---- timed region: K steps of the whole batch, kernels timed with events on the stream
+    clocks = Clocks(local)
+    lat = lbcg.Lattice(geoms, prms, args.precision, stream=stream.cuda_stream)
+    lat.step(args.warmup)
+    torch.cuda.synchronize()
+    flush = torch.zeros(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda") if lat.state_bytes < 2 * L2_BYTES \
+        else None
+    lbcg.lbcg_profile(lat.h, True)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ms = timed_steps(lat, stream, args.steps, flush)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if ws > 1:
+        torch.distributed.barrier()
+    kms, ksteps = lbcg.lbcg_kernel_times(lat.h)
+    lbcg.lbcg_profile(lat.h, False)
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    nf_all = torch.tensor([float(nf)], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(nf_all)
+    ms_max = float(t.item())
+    value = float(nf_all.item()) * args.steps / (ms_max / 1e3) / 1e6
+    launches = args.steps * lat.launches_per_step
+    obs = lbcg.lbcg_observables(lat.h, 0, lbcg.obs_spec(ny=geoms[0].ny), raise_on_diverged=False)
+
+    # ---- roofline of the dominant kernel (k_step)
+    step_ms = kms[2] / max(ksteps, 1)
+    alg_bytes = 36 * s_bytes * nf
+    achieved = alg_bytes / (step_ms / 1e3) / 1e9
+    peaks = measured_peaks()
+    peak, peak_src = (peaks["hbm_gbs"], "measured") if peaks and "hbm_gbs" in peaks else (6800.0, "fallback")
+    traffic = recorded_traffic(f"k_step<{args.precision},ty8>", nf)
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "kernel": "k_step", "peak_source": peak_src,
+            "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": step_ms,
+            "kernel_ms_share": {"k_band": kms[0] / ms, "k_wall": kms[1] / ms, "k_step": kms[2] / ms}}
+    whole_gbs = alg_bytes * args.steps / (ms / 1e3) / 1e9
+
+    # ---- end to end through the C ABI with host buffers (pinned): upload state, step, download
+    sb = lat.state_bytes
+    pin = torch.empty(sb, dtype=torch.uint8, pin_memory=True)
+    lbcg.lbcg_download_state(lat.h, pin.data_ptr(), sb)
+    Ke = max(3, min(args.steps, 20))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(Ke):
+        lbcg.lbcg_upload_state(lat.h, pin.data_ptr(), sb)
+        lat.step(1)
+        lbcg.lbcg_download_state(lat.h, pin.data_ptr(), sb)
+    torch.cuda.synchronize()
+    te = time.perf_counter() - t0
+    e2e = {"value": nf * Ke / te / 1e6 * (float(nf_all.item()) / nf), "unit": "MLUPS", "h2d_bytes_per_step": sb,
+           "d2h_bytes_per_step": sb, "steps": Ke,
+           "path": "lbcg_upload_state (pinned) + lbcg_step(1) + lbcg_download_state per step"}
+    lat.close()
+
+    # ---- the other storage forms on the same workload (shorter)
+    forms = {}
+    if not args.no_forms:
+        for prec in ("fp32", "fp16", "bf16"):
+            if prec == args.precision:
+                forms[prec] = {"MLUPS": value / ws, "hbm_gbs_alg": whole_gbs}
+                continue
+            Kf = max(10, args.steps // 4)
+            L2, msf, _, _ = measure_form(geoms, prms, prec, Kf, args.warmup, stream)
+            L2.close()
+            forms[prec] = {"MLUPS": nf * Kf / (msf / 1e3) / 1e6,
+                           "hbm_gbs_alg": 36 * STORE_BYTES[prec] * nf * Kf / (msf / 1e3) / 1e9}
+
+    # ---- CPU baseline: the oracle on a bounded sample (rank 0, N=1 only)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        v, n, (sx, sy, snf), cores = cpu_oracle_rate(geoms, prms)
+        cpu = {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+               "sample": f"{n} FP64 steps of a {sx}x{sy} section ({snf} fluid nodes) of the first lattice"}
+
+    if rank == 0:
+        line = {"metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
+                "config": {"workload": args.workload, "description": desc, "lattices": len(geoms), "nodes": nodes,
+                           "fluid_nodes_per_gpu": nf, "precision": args.precision,
+                           "state_bytes": sb, "l2": "flushed before every timed step" if flush is not None
+                           else "inputs larger than L2", "mlups_counts": "fluid-node updates"},
+                "hbm_gbs_alg": whole_gbs, "hbm_frac_alg": whole_gbs / peak,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+                "forms": forms, "nonfinite_lattice0": obs.get("nonfinite", None)}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", default="batched_sweep",
+                    choices=("batched_sweep", "capillary", "fingering", "static_droplet", "roofline_box"))
+    ap.add_argument("--precision", default="fp32", choices=("fp64", "fp32", "fp16", "bf16"))
+    ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

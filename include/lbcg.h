@@ -1,0 +1,186 @@
+/*
+ * lbcg.h -- C ABI of liblbcg.so: the time step of the two-colour D2Q9 MRT colour-gradient
+ * lattice Boltzmann method with the improved geometric wetting condition of
+ * Yu, Liu, Zhang & Liang, "Lattice Boltzmann simulation of viscous fingering of immiscible
+ * displacement in a channel using an improved wetting scheme" (arXiv 1707.00198).
+ *
+ * One call of lbcg_step() advances every lattice of a handle by whole time steps, each made
+ * of (Sec. II.A-C):
+ *   rho_R, rho_B, rho^N from the populations          (Eq. 12, 16)
+ *   grad rho^N, virtual values on outermost solid     (Eq. 28, 29)
+ *   wetting correction on the outermost fluid nodes   (Eq. 30-36, E8 normal Eq. 32-33)
+ *   n, virtual n, grad n, curvature, CSF force        (Eq. 10, 11, 13, 29, 44)
+ *   velocity and local viscosity                       (Eq. 5, 17, 18)
+ *   MRT collision with Guo forcing                     (Eq. 1-9)
+ *   recolouring                                        (Eq. 14)
+ *   streaming with half-way bounce-back                (Eq. 15; Sec. II.A after Eq. 6)
+ *   optional Zou-He velocity inlet / pressure outlet   (Sec. III.D)
+ * on one GPU, entirely in CUDA kernels; nothing of the step runs on the host.
+ *
+ * Conventions
+ *   - Arrays are row-major [ny][nx], x fastest.  Direction order of the populations follows
+ *     the paper: e0=(0,0), e1=(1,0), e2=(0,1), e3=(-1,0), e4=(0,-1), e5=(1,1), e6=(-1,1),
+ *     e7=(-1,-1), e8=(1,-1).
+ *   - Contact angles are in radians, measured through the red fluid.
+ *   - All pointers in the structs below are HOST pointers, read during the call and not
+ *     kept; the handle owns every device allocation it makes.
+ *   - Every function returns an lbcg_status; no exception or abort crosses the ABI.  After
+ *     an error lbcg_last_error() returns a message for the calling thread.  A failed CUDA
+ *     call marks the handle dead (later calls return LBCG_E_CUDA).
+ *   - Calls on one handle must not be made concurrently from several threads.
+ */
+#ifndef LBCG_H
+#define LBCG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LBCG_OK = 0,
+  LBCG_E_ARG = 1,             /* NULL pointer, bad size, bad enum value              */
+  LBCG_E_GEOMETRY = 2,        /* no fluid node, fluid on a closed edge, bad normal    */
+  LBCG_E_UNSTABLE_PARAM = 3,  /* nu <= 0, theta outside (0, pi), |u_in| >= 1, ...     */
+  LBCG_E_CUDA = 4,            /* a CUDA call failed; the handle is dead               */
+  LBCG_E_DIVERGED = 5,        /* non-finite density found by lbcg_observables         */
+  LBCG_E_TIMEOUT = 6,         /* reserved for bounded device waits                    */
+  LBCG_E_UNSUPPORTED = 7,     /* request outside what this build supports             */
+  LBCG_E_NOMEM = 8            /* device or host allocation failed                     */
+} lbcg_status;
+
+/* Storage and arithmetic of the populations.
+ *   LBCG_FP64: populations f_R, f_B stored and computed in double.
+ *   LBCG_FP32: populations f_R, f_B stored and computed in float.
+ *   LBCG_FP16_STORE / LBCG_BF16_STORE: 16-bit storage of d = f_R + f_B - w_a rho0 (deviation
+ *     from the rest state) and g = f_R - f_B, all arithmetic in float. */
+typedef enum { LBCG_FP64 = 0, LBCG_FP32 = 1, LBCG_FP16_STORE = 2, LBCG_BF16_STORE = 3 } lbcg_precision;
+
+/* x boundaries: periodic; closed (columns 0 and nx-1 must be solid); or a Zou-He velocity
+ * inlet carrying pure red fluid at x = 0 and a Zou-He pressure outlet at x = nx-1. */
+typedef enum { LBCG_BCX_PERIODIC = 0, LBCG_BCX_CLOSED = 1, LBCG_BCX_INOUT = 2 } lbcg_bc_x;
+/* y boundaries: periodic, or closed (rows 0 and ny-1 must be solid). */
+typedef enum { LBCG_BCY_PERIODIC = 0, LBCG_BCY_CLOSED = 1 } lbcg_bc_y;
+
+/* Geometry of one lattice (host arrays, copied at create). */
+typedef struct {
+  int32_t nx, ny;              /* lattice size, 1 <= nx, ny and nx*ny <= 2^31-1           */
+  int32_t bc_x, bc_y;          /* lbcg_bc_x, lbcg_bc_y                                    */
+  const uint8_t* solid;        /* [ny*nx], nonzero = solid node (Eq. 32 indicator s)      */
+  const double* rhoN0;         /* [ny*nx], initial colour field in [-1, 1]; the initial
+                                  populations are f_{a,R} = w_a rho0 (1 + rhoN0)/2,
+                                  f_{a,B} = w_a rho0 (1 - rhoN0)/2 at rest                 */
+  const double* normal;        /* [2][ny*nx] analytic solid normal n_s pointing into the
+                                  solid (Sec. II.C.1.a, curved walls), or NULL to use the
+                                  E8 estimate of Eq. 32-33                                 */
+  const double* theta_node;    /* [ny*nx] contact angle per node in radians, or NULL to use
+                                  lbcg_params.theta everywhere                             */
+} lbcg_geometry;
+
+/* Parameters of one lattice (Sec. II.A; Eq. 4-6, 10, 14, 18; Sec. III.D). */
+typedef struct {
+  double nu_R, nu_B;           /* kinematic viscosities of red and blue (Eq. 18)          */
+  double sigma;                /* interfacial tension coefficient (Eq. 10)                */
+  double theta;                /* prescribed contact angle [rad] (Eq. 34)                 */
+  double beta;                 /* segregation parameter, 0.7 in the paper (Eq. 14)        */
+  double s_e, s_eps, s_q;      /* fixed MRT rates, 1.64, 1.54, 1.9 in the paper (Eq. 6)   */
+  double rho0;                 /* reference density of both fluids                        */
+  double u_in;                 /* inlet velocity (LBCG_BCX_INOUT)                         */
+  double rho_out;              /* outlet density (LBCG_BCX_INOUT)                         */
+  double grad_eps;             /* n = 0 where |grad rho^N| <= grad_eps                    */
+} lbcg_params;
+
+/* What lbcg_observables measures (all rows are 0-based y indices). */
+typedef struct {
+  double wall_y;               /* flat-wall height for the contact angle (e.g. 0.5)       */
+  double cyl_x, cyl_y, cyl_r;  /* if cyl_r > 0: angle against this solid cylinder instead */
+  int32_t tip_row0, tip_row1;  /* finger tip: first rho^N >= 0 -> < 0 change along the
+                                  mean of these two rows, scanning from x = 0             */
+  int32_t cl_row0, cl_row1;    /* contact line: the same change along each of these rows,
+                                  averaged over the rows where one is found                */
+} lbcg_obs_spec;
+
+/* Observables of one lattice, in FP64 whatever the precision of the populations. */
+typedef struct {
+  int64_t step;                /* time steps taken since create                           */
+  double mass_R, mass_B;       /* sum of rho_R, rho_B over fluid nodes (Eq. 16)           */
+  double umax;                 /* max |u| over fluid nodes (Eq. 46, u of Eq. 17)          */
+  double n_pts;                /* interface points used by the circle fit                  */
+  double xc, yc, R;            /* algebraic circle fit through the rho^N = 0 crossings     */
+  double theta_deg;            /* contact angle from the fit (flat wall or cylinder)      */
+  double dp_laplace;           /* mean rho/3 over rho^N > 0.9 minus over rho^N < -0.9     */
+  double x_tip, x_cl;          /* finger tip and contact line, -1 if not found            */
+  double moments[9];           /* n, Sx, Sy, Sxx, Syy, Sxy, Szx, Szy, Sz of the points,
+                                  relative to (nx/2, ny/2), z = x^2 + y^2                  */
+  int32_t nonfinite;           /* 1 if any fluid density is NaN or Inf                    */
+} lbcg_obs;
+
+typedef struct lbcg_handle lbcg_handle;
+
+/* Create a handle with ONE lattice.  `stream` is the cudaStream_t on which all later work
+ * of the handle is enqueued; with NULL the handle creates (and later destroys) its own
+ * non-blocking stream.  The calls that return data synchronise that stream.  Copies the geometry,
+ * classifies nodes (outermost fluid / outermost solid, Sec. II.C), computes solid normals
+ * (Eq. 32-33 unless given), initialises the populations and uploads everything. */
+lbcg_status lbcg_create(const lbcg_geometry* geom, const lbcg_params* prm, int32_t precision,
+                        void* stream, lbcg_handle** out);
+
+/* Create a handle holding `n` independent lattices of any sizes and parameters; every
+ * later lbcg_step advances all of them with one kernel launch per kernel of the step. */
+lbcg_status lbcg_create_batch(int32_t n, const lbcg_geometry* geoms, const lbcg_params* prms,
+                              int32_t precision, void* stream, lbcg_handle** out);
+
+/* Enqueue `nsteps` >= 0 time steps on the handle's stream (asynchronous; replayed from a
+ * captured CUDA graph when nsteps is large). */
+lbcg_status lbcg_step(lbcg_handle* h, int64_t nsteps);
+
+/* Measure the observables of lattice `lattice` of the current state (synchronises the
+ * stream).  Returns LBCG_E_DIVERGED (with *out filled) if a density is not finite. */
+lbcg_status lbcg_observables(lbcg_handle* h, int32_t lattice, const lbcg_obs_spec* spec,
+                             lbcg_obs* out);
+
+/* Copy the populations of lattice `lattice` to/from host memory as double
+ * [2][9][ny][nx] (red block then blue block).  Synchronises the stream.  Values at solid
+ * nodes are ignored on input and returned as 0. */
+lbcg_status lbcg_get_populations(lbcg_handle* h, int32_t lattice, double* host_out);
+lbcg_status lbcg_set_populations(lbcg_handle* h, int32_t lattice, const double* host_in);
+
+/* Per-node fields of the current state of lattice `lattice`, as double [4][ny][nx]:
+ * rho, rho^N, u_x, u_y (Eq. 12, 16, 17; zeros on solid nodes).  Synchronises. */
+lbcg_status lbcg_get_fields(lbcg_handle* h, int32_t lattice, double* host_out);
+
+/* The raw device state in its storage format: `bytes` must equal lbcg_state_bytes(h);
+ * the host buffer should be pinned for full copy speed.  Enqueued on the stream;
+ * lbcg_download_state synchronises before returning. */
+size_t lbcg_state_bytes(const lbcg_handle* h);
+lbcg_status lbcg_upload_state(lbcg_handle* h, const void* host_in, size_t bytes);
+lbcg_status lbcg_download_state(lbcg_handle* h, void* host_out, size_t bytes);
+
+/* Tile shape of the fused step kernel (rows of 32-wide tiles); 0 = the built-in default.
+ * Valid ty: 4, 8, 16.  Drops captured graphs. */
+lbcg_status lbcg_set_tile(lbcg_handle* h, int32_t ty);
+
+/* Kernel timing with CUDA events on the handle's stream.  While enabled, lbcg_step launches
+ * the kernels of each step directly (no graph) with an event recorded before and after each
+ * of k_band, k_wall and k_step.  lbcg_kernel_times synchronises, returns in ms3[0..2] the
+ * summed milliseconds of those three kernels over the steps taken since the last call (or
+ * since enabling) and their number in *steps, and restarts the sums. */
+lbcg_status lbcg_profile(lbcg_handle* h, int32_t enable);
+lbcg_status lbcg_kernel_times(lbcg_handle* h, double* ms3, int64_t* steps);
+
+/* Number of kernel launches one time step enqueues, and the number of lattice nodes
+ * (fluid and solid) all lattices hold. */
+int32_t lbcg_launches_per_step(const lbcg_handle* h);
+int64_t lbcg_total_nodes(const lbcg_handle* h);
+
+lbcg_status lbcg_destroy(lbcg_handle* h);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char* lbcg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBCG_H */

@@ -1,0 +1,225 @@
+// Device-side building blocks of the colour-gradient LBM step (arXiv 1707.00198, Sec. II).
+//
+// Layout in HBM (one "pool" per kind, lattices of a batch packed one after another):
+//   populations : 18 planes [k][a][y][pitch] of the storage type S, plane-major, x fastest;
+//                 planes 0..8 hold direction a of the first stored quantity, 9..17 of the
+//                 second one.  Direct storage (double, float): f_{a,R} then f_{a,B}.
+//                 Deviation storage (half, bfloat16): d_a = f_a - w_a rho0 then
+//                 g_a = f_{a,R} - f_{a,B} (an exact linear transform of the pair).
+//                 The stored state is post-collision, pre-streaming; streaming is folded
+//                 into the next step's loads (pull), bounce-back into the choice of address.
+//   node arrays : flags (uint8), and in the compute type T the rho^N of the wall band and
+//                 the corrected gradient / normal of the outermost fluid nodes.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbcg {
+
+// node flags
+enum : uint8_t {
+  F_SOLID = 1,    // solid node (indicator s = 1 of Eq. 32)
+  F_OFB = 2,      // outermost fluid node (fluid with a solid D2Q9 neighbour), Omega_Fb
+  F_OSOLID = 4,   // outermost solid node (solid with a fluid D2Q9 neighbour), Eq. 29
+  F_NEAR = 8,     // within Chebyshev distance 3 of a solid node (excluded from the fit)
+};
+
+enum { BC_PERIODIC = 0, BC_CLOSED = 1, BC_INOUT = 2 };
+
+// Per-lattice constants, resident in global memory, one entry per lattice of a handle.
+struct LatDev {
+  int nx, ny, pitch, bcx, bcy, pad_;
+  long long pop_off;   // element offset of plane 0 of this lattice in the population pool
+  long long plane;     // elements per plane (pitch * ny)
+  long long node_off;  // element offset of node (0,0) in the node arrays
+  double nu_R, nu_B, sigma, beta, s_e, s_eps, s_q, rho0, u_in, rho_out, grad_eps;
+};
+
+// Entry of the outermost-fluid list: node, its solid normal and contact angle.
+struct OfbEntry {
+  int lat, x, y, pad_;
+  double nsx, nsy, cos_t, sin_t;
+};
+
+// D2Q9 velocity set (Sec. II.A), as constant-folding functions of the direction index.
+__host__ __device__ constexpr int ex(int a) {
+  return (a == 1 || a == 5 || a == 8) ? 1 : ((a == 3 || a == 6 || a == 7) ? -1 : 0);
+}
+__host__ __device__ constexpr int ey(int a) {
+  return (a == 2 || a == 5 || a == 6) ? 1 : ((a == 4 || a == 7 || a == 8) ? -1 : 0);
+}
+__host__ __device__ constexpr int opp(int a) {
+  return a == 0 ? 0 : (a <= 4 ? ((a + 1) % 4) + 1 : ((a - 3) % 4) + 5);
+}
+template <typename T>
+__host__ __device__ constexpr T wgt(int a) {
+  return a == 0 ? T(4.0 / 9.0) : (a <= 4 ? T(1.0 / 9.0) : T(1.0 / 36.0));
+}
+
+// ------------------------------------------------------------------ storage traits
+template <typename S> struct Store;
+template <> struct Store<double> {
+  using T = double;
+  static constexpr bool kDeviation = false;
+  __device__ static double ld(const double* p) { return __ldg(p); }
+  __device__ static double cv(double v) { return v; }
+};
+template <> struct Store<float> {
+  using T = float;
+  static constexpr bool kDeviation = false;
+  __device__ static float ld(const float* p) { return __ldg(p); }
+  __device__ static float cv(float v) { return v; }
+};
+template <> struct Store<__half> {
+  using T = float;
+  static constexpr bool kDeviation = true;
+  __device__ static float ld(const __half* p) { return __half2float(__ldg(p)); }
+  __device__ static __half cv(float v) { return __float2half_rn(v); }
+};
+template <> struct Store<__nv_bfloat16> {
+  using T = float;
+  static constexpr bool kDeviation = true;
+  __device__ static float ld(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
+  __device__ static __nv_bfloat16 cv(float v) { return __float2bfloat16_rn(v); }
+};
+
+// stored pair (lo = plane a, hi = plane 9+a) -> (f_R, f_B)
+template <typename S, typename T>
+__device__ __forceinline__ void decode(T lo, T hi, T wr0, T& fr, T& fb) {
+  if constexpr (Store<S>::kDeviation) {
+    const T f = wr0 + lo;
+    fr = T(0.5) * (f + hi);
+    fb = T(0.5) * (f - hi);
+  } else {
+    fr = lo;
+    fb = hi;
+  }
+}
+template <typename S, typename T>
+__device__ __forceinline__ void encode(T fr, T fb, T wr0, T& lo, T& hi) {
+  if constexpr (Store<S>::kDeviation) {
+    lo = (fr + fb) - wr0;
+    hi = fr - fb;
+  } else {
+    lo = fr;
+    hi = fb;
+  }
+}
+
+// ------------------------------------------------------------------ rounding-exact helpers
+// The wall chain (Eq. 28-36) is evaluated without contraction into fused multiply-adds and
+// in a fixed order, so that exact cancellations (e.g. a gradient exactly normal to a flat
+// wall, which makes D1 == D2 in Eq. 35-36 an exact tie) are reproduced exactly.
+__device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double rsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double rdiv(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ double rsqrt_(double a) { return __dsqrt_rn(a); }
+__device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float rsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float rdiv(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float rsqrt_(float a) { return __fsqrt_rn(a); }
+
+// ------------------------------------------------------------------ neighbour mapping
+// Periodic axes wrap; other axes clamp (on an inlet/outlet axis the clamped ghost column
+// copies the edge column; closed axes have solid edges, so a clamp is never used there
+// for a fluid node).
+__device__ __forceinline__ int wrap_or_clamp(int v, int n, bool periodic) {
+  if (periodic) {
+    v %= n;
+    return v < 0 ? v + n : v;
+  }
+  return v < 0 ? 0 : (v >= n ? n - 1 : v);
+}
+
+// ------------------------------------------------------------------ pull with boundaries
+// Post-streaming populations of fluid node (x, y): f_a(x) = f''_a(x - e_a) if that node is
+// fluid, else the half-way bounce-back f''_{opp(a)}(x) (Eq. 15).  `solid_at(dx, dy)` tells
+// whether the node at offset (dx, dy) from (x, y) is solid; `xm[dx+1]`, `ym[dy+1]` are the
+// mapped coordinates of the neighbours.  On an inlet/outlet lattice the Zou-He conditions
+// replace the populations entering from outside (Sec. III.D).
+template <typename S, typename SolidFn>
+__device__ __forceinline__ void pull_node(const LatDev& L, const S* __restrict__ src, int x, const int xm[3],
+                                          const int ym[3], SolidFn solid_at,
+                                          typename Store<S>::T fr[9], typename Store<S>::T fb[9]) {
+  using T = typename Store<S>::T;
+  const S* base = src + L.pop_off;
+  const T r0 = T(L.rho0);
+  const bool inlet = (L.bcx == BC_INOUT) && (x == 0);
+  const bool outlet = (L.bcx == BC_INOUT) && (x == L.nx - 1);
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    const bool entering = (inlet && ex(a) == 1) || (outlet && ex(a) == -1);
+    T lo = T(0), hi = T(0);
+    if (!entering) {
+      long long idx;
+      int p;
+      if (a != 0 && solid_at(-ex(a), -ey(a))) {
+        p = opp(a);
+        idx = (long long)ym[1] * L.pitch + xm[1];
+      } else {
+        p = a;
+        idx = (long long)ym[1 - ey(a)] * L.pitch + xm[1 - ex(a)];
+      }
+      lo = Store<S>::ld(base + (long long)p * L.plane + idx);
+      hi = Store<S>::ld(base + (long long)(9 + p) * L.plane + idx);
+    }
+    decode<S, T>(lo, hi, wgt<T>(a) * r0, fr[a], fb[a]);
+  }
+  if (inlet) {
+    // Zou-He velocity inlet: u = (u_in, 0), unknown f1, f5, f8; the node carries red only
+    T f[9];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) f[a] = fr[a] + fb[a];
+    const T u = T(L.u_in);
+    const T rho = (f[0] + f[2] + f[4] + T(2) * (f[3] + f[6] + f[7])) / (T(1) - u);
+    f[1] = f[3] + T(2.0 / 3.0) * rho * u;
+    f[5] = f[7] - T(0.5) * (f[2] - f[4]) + rho * u / T(6);
+    f[8] = f[6] + T(0.5) * (f[2] - f[4]) + rho * u / T(6);
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+      fr[a] = f[a];
+      fb[a] = T(0);
+    }
+  } else if (outlet) {
+    // Zou-He pressure outlet: rho = rho_out, u_y = 0, unknown f3, f6, f7, which take the
+    // colour fraction of the known populations
+    T f[9];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) f[a] = fr[a] + fb[a];
+    const T r = T(L.rho_out);
+    const T ux = T(-1) + (f[0] + f[2] + f[4] + T(2) * (f[1] + f[5] + f[8])) / r;
+    const T f3 = f[1] - T(2.0 / 3.0) * r * ux;
+    const T f7 = f[5] + T(0.5) * (f[2] - f[4]) - r * ux / T(6);
+    const T f6 = f[8] - T(0.5) * (f[2] - f[4]) - r * ux / T(6);
+    const T kR = fr[0] + fr[1] + fr[2] + fr[4] + fr[5] + fr[8];
+    const T kT = f[0] + f[1] + f[2] + f[4] + f[5] + f[8];
+    const T frac = kT != T(0) ? kR / kT : T(0);
+    fr[3] = frac * f3;
+    fb[3] = (T(1) - frac) * f3;
+    fr[6] = frac * f6;
+    fb[6] = (T(1) - frac) * f6;
+    fr[7] = frac * f7;
+    fb[7] = (T(1) - frac) * f7;
+  }
+}
+
+// rho^N of Eq. 12 from the colour densities of Eq. 16 (sequential sums in direction order)
+template <typename T>
+__device__ __forceinline__ T colour_indicator(const T fr[9], const T fb[9], T& rhoR, T& rhoB) {
+  T sr = fr[0], sb = fb[0];
+#pragma unroll
+  for (int a = 1; a < 9; ++a) {
+    sr = radd(sr, fr[a]);
+    sb = radd(sb, fb[a]);
+  }
+  rhoR = sr;
+  rhoB = sb;
+  return rdiv(rsub(sr, sb), radd(sr, sb));
+}
+
+}  // namespace lbcg

@@ -1,0 +1,735 @@
+// Host runtime behind the C ABI of include/lbcg.h: validation, node classification
+// (Sec. II.C), solid normals (Eq. 32-33), work lists, device memory, graph-captured stepping,
+// observables and state transfer.  All arithmetic of the time step runs in the kernels of
+// lbcg_kernels.cu; the host only prepares geometry once per handle.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lbcg.h"
+#include "lbcg_internal.h"
+
+using namespace lbcg;
+
+namespace {
+
+thread_local std::string g_err;
+
+lbcg_status fail(lbcg_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+constexpr int kGraphSteps = 32;   // steps per captured graph (even: the graph starts and ends on pool A)
+constexpr int kDefaultTY = 8;
+
+size_t elem_size(int prec) { return prec == 0 ? 8 : (prec == 1 ? 4 : 2); }
+size_t compute_size(int prec) { return prec == 0 ? 8 : 4; }
+
+struct LatHost {
+  int nx, ny, pitch, bcx, bcy;
+  long long pop_off, plane, node_off;
+  lbcg_params prm;
+  int tile_begin, tile_end;
+  long long n_fluid;
+  std::vector<uint8_t> solid;   // [ny*nx]
+};
+
+}  // namespace
+
+struct lbcg_handle {
+  int prec = 1;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  bool dead = false;
+  int64_t step = 0;
+  int ty = kDefaultTY;
+  std::vector<LatHost> lats;
+  long long node_total = 0;
+  void* pool[2] = {nullptr, nullptr};
+  int cur = 0;
+  uint8_t* d_flags = nullptr;
+  void* d_band_rn = nullptr;
+  void* d_wall = nullptr;
+  double* d_macro = nullptr;
+  LatDev* d_lats = nullptr;
+  int4* d_tiles = nullptr;
+  int ntiles = 0;
+  int4* d_band = nullptr;
+  int nband = 0;
+  OfbEntry* d_ofb = nullptr;
+  int nofb = 0;
+  double* d_obs = nullptr;   // partials then outputs
+  cudaGraphExec_t graph = nullptr;
+  std::vector<uint8_t> flags_host;
+  bool profiling = false;
+  std::vector<cudaEvent_t> events;   // 6 per profiled step
+  size_t events_used = 0;
+};
+
+namespace {
+
+lbcg_status cuda_fail(lbcg_handle* h, cudaError_t e, const char* what) {
+  if (h) h->dead = true;
+  return fail(LBCG_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(h, call)                                   \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+  } while (0)
+
+int wrap_clamp(int v, int n, bool periodic) {
+  if (periodic) {
+    v %= n;
+    return v < 0 ? v + n : v;
+  }
+  return v < 0 ? 0 : (v >= n ? n - 1 : v);
+}
+
+const int EXH[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+const int EYH[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+
+lbcg_status validate(const lbcg_geometry* g, const lbcg_params* p, int idx) {
+  if (!g || !p) return fail(LBCG_E_ARG, "lattice %d: NULL geometry or params", idx);
+  if (g->nx < 1 || g->ny < 1 || (long long)g->nx * g->ny > 0x7fffffffLL)
+    return fail(LBCG_E_ARG, "lattice %d: bad size %d x %d", idx, g->nx, g->ny);
+  if (!g->solid || !g->rhoN0) return fail(LBCG_E_ARG, "lattice %d: solid and rhoN0 are required", idx);
+  if (g->bc_x < 0 || g->bc_x > 2 || g->bc_y < 0 || g->bc_y > 1)
+    return fail(LBCG_E_ARG, "lattice %d: bad boundary codes %d %d", idx, g->bc_x, g->bc_y);
+  if (g->bc_x == LBCG_BCX_INOUT && g->nx < 3) return fail(LBCG_E_GEOMETRY, "lattice %d: inlet/outlet needs nx >= 3", idx);
+  const int nx = g->nx, ny = g->ny;
+  if (g->bc_x == LBCG_BCX_CLOSED)
+    for (int y = 0; y < ny; ++y)
+      if (!g->solid[(size_t)y * nx] || !g->solid[(size_t)y * nx + nx - 1])
+        return fail(LBCG_E_GEOMETRY, "lattice %d: closed x needs solid columns 0 and nx-1", idx);
+  if (g->bc_y == LBCG_BCY_CLOSED)
+    for (int x = 0; x < nx; ++x)
+      if (!g->solid[x] || !g->solid[(size_t)(ny - 1) * nx + x])
+        return fail(LBCG_E_GEOMETRY, "lattice %d: closed y needs solid rows 0 and ny-1", idx);
+  long long nf = 0;
+  for (long long i = 0; i < (long long)nx * ny; ++i) nf += g->solid[i] == 0;
+  if (nf == 0) return fail(LBCG_E_GEOMETRY, "lattice %d: no fluid node", idx);
+  if (!(p->nu_R > 0) || !(p->nu_B > 0)) return fail(LBCG_E_UNSTABLE_PARAM, "lattice %d: viscosities must be > 0", idx);
+  if (!(p->sigma >= 0)) return fail(LBCG_E_UNSTABLE_PARAM, "lattice %d: sigma must be >= 0", idx);
+  if (!(p->rho0 > 0)) return fail(LBCG_E_UNSTABLE_PARAM, "lattice %d: rho0 must be > 0", idx);
+  if (!(std::fabs(p->u_in) < 1)) return fail(LBCG_E_UNSTABLE_PARAM, "lattice %d: |u_in| must be < 1", idx);
+  if (!(p->rho_out > 0)) return fail(LBCG_E_UNSTABLE_PARAM, "lattice %d: rho_out must be > 0", idx);
+  if (!(p->grad_eps >= 0)) return fail(LBCG_E_ARG, "lattice %d: grad_eps must be >= 0", idx);
+  const double pi = 3.14159265358979323846;
+  auto angle_ok = [&](double t) { return t > 0 && t < pi; };
+  if (!g->theta_node && !angle_ok(p->theta)) return fail(LBCG_E_UNSTABLE_PARAM, "lattice %d: theta outside (0, pi)", idx);
+  if (g->theta_node)
+    for (long long i = 0; i < (long long)nx * ny; ++i)
+      if (!g->solid[i] && !angle_ok(g->theta_node[i]))
+        return fail(LBCG_E_UNSTABLE_PARAM, "lattice %d: theta_node outside (0, pi) at %lld", idx, i);
+  for (long long i = 0; i < (long long)nx * ny; ++i)
+    if (!g->solid[i] && !(g->rhoN0[i] >= -1.0 && g->rhoN0[i] <= 1.0))
+      return fail(LBCG_E_ARG, "lattice %d: rhoN0 outside [-1, 1] at %lld", idx, i);
+  return LBCG_OK;
+}
+
+// Classification of one lattice (Sec. II.C): flags, wall band, outermost-fluid entries.
+void classify(const lbcg_geometry* g, const lbcg_params* p, int lat, std::vector<uint8_t>& flags_local,
+              std::vector<int4>& band, std::vector<OfbEntry>& ofb) {
+  const int nx = g->nx, ny = g->ny;
+  const bool px = g->bc_x == LBCG_BCX_PERIODIC, py = g->bc_y == LBCG_BCY_PERIODIC;
+  auto S = [&](int x, int y) { return g->solid[(size_t)y * nx + x] != 0; };
+  flags_local.assign((size_t)nx * ny, 0);
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      uint8_t f = 0;
+      const bool s = S(x, y);
+      bool any_s = false, any_f = false;
+      for (int a = 1; a < 9; ++a) {
+        const bool sn = S(wrap_clamp(x + EXH[a], nx, px), wrap_clamp(y + EYH[a], ny, py));
+        any_s |= sn;
+        any_f |= !sn;
+      }
+      if (s) {
+        f |= F_SOLID;
+        if (any_f) f |= F_OSOLID;
+      } else if (any_s) {
+        f |= F_OFB;
+      }
+      bool near = false;
+      for (int dy = -3; dy <= 3 && !near; ++dy)
+        for (int dx = -3; dx <= 3 && !near; ++dx)
+          near = S(wrap_clamp(x + dx, nx, px), wrap_clamp(y + dy, ny, py));
+      if (near) f |= F_NEAR;
+      flags_local[(size_t)y * nx + x] = f;
+    }
+  // wall band: outermost fluid nodes and their fluid neighbours
+  std::vector<uint8_t> inband((size_t)nx * ny, 0);
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      if (!(flags_local[(size_t)y * nx + x] & F_OFB)) continue;
+      inband[(size_t)y * nx + x] = 1;
+      for (int a = 1; a < 9; ++a) {
+        const int xx = wrap_clamp(x + EXH[a], nx, px), yy = wrap_clamp(y + EYH[a], ny, py);
+        if (!S(xx, yy)) inband[(size_t)yy * nx + xx] = 1;
+      }
+    }
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x)
+      if (inband[(size_t)y * nx + x]) band.push_back(make_int4(lat, x, y, 0));
+  // E8 stencil (Eq. 33): the weights are k/5040 with integer k, summed exactly as integers
+  struct C8 {
+    int cx, cy, k;
+  };
+  std::vector<C8> st;
+  for (int cy = -2; cy <= 2; ++cy)
+    for (int cx = -2; cx <= 2; ++cx) {
+      const int c2 = cx * cx + cy * cy;
+      const int k = c2 == 1 ? 240 : c2 == 2 ? 112 : c2 == 4 ? 84 : c2 == 5 ? 16 : c2 == 8 ? 1 : 0;
+      if (k) st.push_back({cx, cy, k});
+    }
+  auto s_e8 = [&](int x, int y) -> int {
+    // edge rule: periodic wrap; closed -> solid; inlet/outlet x -> copy of the edge column
+    if (x < 0 || x >= nx) {
+      if (px) x = wrap_clamp(x, nx, true);
+      else if (g->bc_x == LBCG_BCX_CLOSED) return 1;
+      else x = wrap_clamp(x, nx, false);
+    }
+    if (y < 0 || y >= ny) {
+      if (py) y = wrap_clamp(y, ny, true);
+      else return 1;
+    }
+    return S(x, y) ? 1 : 0;
+  };
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      if (!(flags_local[(size_t)y * nx + x] & F_OFB)) continue;
+      OfbEntry e{};
+      e.lat = lat;
+      e.x = x;
+      e.y = y;
+      const size_t i = (size_t)y * nx + x;
+      if (g->normal) {
+        e.nsx = g->normal[i];
+        e.nsy = g->normal[(size_t)nx * ny + i];
+      } else {
+        long long vx = 0, vy = 0;
+        for (const C8& c : st) {
+          const int s = s_e8(x + c.cx, y + c.cy);
+          vx += (long long)c.k * s * c.cx;
+          vy += (long long)c.k * s * c.cy;
+        }
+        const double dx = double(vx), dy = double(vy);
+        const double m = std::sqrt(dx * dx + dy * dy);
+        e.nsx = m > 0 ? dx / m : 0.0;
+        e.nsy = m > 0 ? dy / m : 0.0;
+      }
+      const double th = g->theta_node ? g->theta_node[i] : p->theta;
+      e.cos_t = std::cos(th);
+      e.sin_t = std::sin(th);
+      ofb.push_back(e);
+    }
+}
+
+void build_tiles(lbcg_handle* h, std::vector<int4>& tiles) {
+  tiles.clear();
+  for (size_t l = 0; l < h->lats.size(); ++l) {
+    LatHost& L = h->lats[l];
+    L.tile_begin = int(tiles.size());
+    for (int y0 = 0; y0 < L.ny; y0 += h->ty)
+      for (int x0 = 0; x0 < L.nx; x0 += 32) {
+        bool any = false;
+        for (int y = y0; y < std::min(y0 + h->ty, L.ny) && !any; ++y)
+          for (int x = x0; x < std::min(x0 + 32, L.nx) && !any; ++x) any = L.solid[(size_t)y * L.nx + x] == 0;
+        if (any) tiles.push_back(make_int4(int(l), x0, y0, 0));
+      }
+    L.tile_end = int(tiles.size());
+  }
+}
+
+LaunchStep make_launch(lbcg_handle* h, int src, double* macro, int tile_begin, int tile_end) {
+  LaunchStep p{};
+  p.lats = h->d_lats;
+  p.band = h->d_band;
+  p.nband = h->nband;
+  p.ofb = h->d_ofb;
+  p.nofb = h->nofb;
+  p.tiles = h->d_tiles + tile_begin;
+  p.ntiles = tile_end - tile_begin;
+  p.ty = h->ty;
+  p.src = h->pool[src];
+  p.dst = h->pool[src ^ 1];
+  p.flags = h->d_flags;
+  p.band_rn = h->d_band_rn;
+  p.wall = h->d_wall;
+  p.node_total = h->node_total;
+  p.macro = macro;
+  return p;
+}
+
+void free_handle(lbcg_handle* h) {
+  if (!h) return;
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+  void* ptrs[] = {h->pool[0], h->pool[1], h->d_flags, h->d_band_rn, h->d_wall, h->d_macro,
+                  h->d_lats,  h->d_tiles, h->d_band,  h->d_ofb,     h->d_obs};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+lbcg_status upload_tiles(lbcg_handle* h) {
+  std::vector<int4> tiles;
+  build_tiles(h, tiles);
+  if (h->d_tiles) cudaFree(h->d_tiles);
+  h->d_tiles = nullptr;
+  h->ntiles = int(tiles.size());
+  CK(h, cudaMalloc(&h->d_tiles, std::max<size_t>(1, tiles.size()) * sizeof(int4)));
+  if (!tiles.empty()) CK(h, cudaMemcpy(h->d_tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  return LBCG_OK;
+}
+
+lbcg_status ensure_macro(lbcg_handle* h) {
+  if (!h->d_macro) {
+    if (cudaMalloc(&h->d_macro, 4 * (size_t)h->node_total * sizeof(double)) != cudaSuccess)
+      return fail(LBCG_E_NOMEM, "cannot allocate the macroscopic fields");
+    CK(h, cudaMemsetAsync(h->d_macro, 0, 4 * (size_t)h->node_total * sizeof(double), h->stream));
+  }
+  return LBCG_OK;
+}
+
+lbcg_status check_handle(const lbcg_handle* h) {
+  if (!h) return fail(LBCG_E_ARG, "NULL handle");
+  if (h->dead) return fail(LBCG_E_CUDA, "handle is dead after an earlier CUDA error");
+  return LBCG_OK;
+}
+
+lbcg_status run_macro(lbcg_handle* h, int lat) {
+  lbcg_status s = ensure_macro(h);
+  if (s != LBCG_OK) return s;
+  const LatHost& L = h->lats[lat];
+  LaunchStep p = make_launch(h, h->cur, h->d_macro, L.tile_begin, L.tile_end);
+  CK(h, launch_step(h->prec, p, h->stream));
+  return LBCG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lbcg_last_error(void) { return g_err.c_str(); }
+
+lbcg_status lbcg_create_batch(int32_t n, const lbcg_geometry* geoms, const lbcg_params* prms, int32_t precision,
+                              void* stream, lbcg_handle** out) {
+  g_err.clear();
+  if (!out) return fail(LBCG_E_ARG, "NULL output handle pointer");
+  *out = nullptr;
+  if (n < 1 || !geoms || !prms) return fail(LBCG_E_ARG, "need n >= 1 lattices with geometry and params");
+  if (precision < 0 || precision > 3) return fail(LBCG_E_ARG, "bad precision %d", precision);
+  for (int l = 0; l < n; ++l) {
+    lbcg_status s = validate(&geoms[l], &prms[l], l);
+    if (s != LBCG_OK) return s;
+  }
+  lbcg_handle* h = new lbcg_handle();
+  h->prec = precision;
+  if (stream) {
+    h->stream = static_cast<cudaStream_t>(stream);
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      free_handle(h);
+      return fail(LBCG_E_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+    }
+    h->own_stream = true;
+  }
+  // layout
+  std::vector<LatDev> ld(n);
+  std::vector<int4> band;
+  std::vector<OfbEntry> ofb;
+  long long node_total = 0;
+  for (int l = 0; l < n; ++l) {
+    const lbcg_geometry* g = &geoms[l];
+    LatHost L{};
+    L.nx = g->nx;
+    L.ny = g->ny;
+    L.pitch = (g->nx + 31) / 32 * 32;
+    L.bcx = g->bc_x;
+    L.bcy = g->bc_y;
+    L.plane = (long long)L.pitch * L.ny;
+    L.node_off = node_total;
+    L.pop_off = 18 * node_total;
+    L.prm = prms[l];
+    L.solid.assign(g->solid, g->solid + (size_t)g->nx * g->ny);
+    L.n_fluid = 0;
+    for (uint8_t s : L.solid) L.n_fluid += s == 0;
+    node_total += L.plane;
+    h->lats.push_back(L);
+    LatDev& d = ld[l];
+    d.nx = L.nx;
+    d.ny = L.ny;
+    d.pitch = L.pitch;
+    d.bcx = L.bcx;
+    d.bcy = L.bcy;
+    d.pop_off = L.pop_off;
+    d.plane = L.plane;
+    d.node_off = L.node_off;
+    const lbcg_params& p = prms[l];
+    d.nu_R = p.nu_R;
+    d.nu_B = p.nu_B;
+    d.sigma = p.sigma;
+    d.beta = p.beta;
+    d.s_e = p.s_e;
+    d.s_eps = p.s_eps;
+    d.s_q = p.s_q;
+    d.rho0 = p.rho0;
+    d.u_in = p.u_in;
+    d.rho_out = p.rho_out;
+    d.grad_eps = p.grad_eps;
+  }
+  h->node_total = node_total;
+  h->flags_host.assign((size_t)node_total, F_SOLID);
+  for (int l = 0; l < n; ++l) {
+    std::vector<uint8_t> fl;
+    classify(&geoms[l], &prms[l], l, fl, band, ofb);
+    const LatHost& L = h->lats[l];
+    for (int y = 0; y < L.ny; ++y)
+      memcpy(&h->flags_host[L.node_off + (size_t)y * L.pitch], &fl[(size_t)y * L.nx], L.nx);
+  }
+  h->nband = int(band.size());
+  h->nofb = int(ofb.size());
+  const size_t es = elem_size(precision), cs = compute_size(precision);
+  auto alloc = [&](void** p, size_t bytes) { return cudaMalloc(p, std::max<size_t>(bytes, 16)) == cudaSuccess; };
+  bool ok = alloc(&h->pool[0], 18 * (size_t)node_total * es) && alloc(&h->pool[1], 18 * (size_t)node_total * es) &&
+            alloc((void**)&h->d_flags, (size_t)node_total) && alloc(&h->d_band_rn, (size_t)node_total * cs) &&
+            alloc(&h->d_wall, 4 * (size_t)node_total * cs) && alloc((void**)&h->d_lats, n * sizeof(LatDev)) &&
+            alloc((void**)&h->d_band, band.size() * sizeof(int4)) &&
+            alloc((void**)&h->d_ofb, ofb.size() * sizeof(OfbEntry)) &&
+            alloc((void**)&h->d_obs, (obs_partials_doubles() + kObsOut) * sizeof(double));
+  if (!ok) {
+    free_handle(h);
+    return fail(LBCG_E_NOMEM, "device allocation failed (%lld nodes)", node_total);
+  }
+#define CKC(call)                                         \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) {                              \
+      lbcg_status s_ = cuda_fail(h, e_, #call);           \
+      free_handle(h);                                     \
+      return s_;                                          \
+    }                                                     \
+  } while (0)
+  CKC(cudaMemcpy(h->d_flags, h->flags_host.data(), (size_t)node_total, cudaMemcpyHostToDevice));
+  CKC(cudaMemcpy(h->d_lats, ld.data(), n * sizeof(LatDev), cudaMemcpyHostToDevice));
+  if (!band.empty()) CKC(cudaMemcpy(h->d_band, band.data(), band.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  if (!ofb.empty()) CKC(cudaMemcpy(h->d_ofb, ofb.data(), ofb.size() * sizeof(OfbEntry), cudaMemcpyHostToDevice));
+  CKC(cudaMemset(h->pool[0], 0, 18 * (size_t)node_total * es));
+  CKC(cudaMemset(h->pool[1], 0, 18 * (size_t)node_total * es));
+  CKC(cudaMemset(h->d_band_rn, 0, (size_t)node_total * cs));
+  CKC(cudaMemset(h->d_wall, 0, 4 * (size_t)node_total * cs));
+  {
+    lbcg_status s = upload_tiles(h);
+    if (s != LBCG_OK) {
+      free_handle(h);
+      return s;
+    }
+  }
+  // initial populations at rest: f_{a,R} = w_a rho0 (1 + rhoN0)/2, f_{a,B} = w_a rho0 (1 - rhoN0)/2
+  const double W[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+  for (int l = 0; l < n; ++l) {
+    const lbcg_geometry* g = &geoms[l];
+    const size_t nn = (size_t)g->nx * g->ny;
+    std::vector<double> host(18 * nn, 0.0);
+    for (size_t i = 0; i < nn; ++i) {
+      if (g->solid[i]) continue;
+      const double r = g->rhoN0[i];
+      for (int a = 0; a < 9; ++a) {
+        host[a * nn + i] = W[a] * prms[l].rho0 * (1 + r) / 2;
+        host[(9 + a) * nn + i] = W[a] * prms[l].rho0 * (1 - r) / 2;
+      }
+    }
+    double* tmp = nullptr;
+    CKC(cudaMalloc(&tmp, 18 * nn * sizeof(double)));
+    cudaError_t e = cudaMemcpy(tmp, host.data(), 18 * nn * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_to_storage(precision, h->d_lats, l, (long long)nn, tmp, h->d_flags, h->pool[0], 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaFree(tmp);
+    CKC(e);
+  }
+  CKC(cudaMemcpy(h->pool[1], h->pool[0], 18 * (size_t)node_total * es, cudaMemcpyDeviceToDevice));
+#undef CKC
+  *out = h;
+  return LBCG_OK;
+}
+
+lbcg_status lbcg_create(const lbcg_geometry* geom, const lbcg_params* prm, int32_t precision, void* stream,
+                        lbcg_handle** out) {
+  return lbcg_create_batch(1, geom, prm, precision, stream, out);
+}
+
+lbcg_status lbcg_step(lbcg_handle* h, int64_t nsteps) {
+  lbcg_status s = check_handle(h);
+  if (s != LBCG_OK) return s;
+  if (nsteps < 0) return fail(LBCG_E_ARG, "nsteps < 0");
+  while (nsteps > 0) {
+    if (h->profiling) {
+      if (h->events.size() < h->events_used + 6) {
+        for (int k = 0; k < 6; ++k) {
+          cudaEvent_t e;
+          CK(h, cudaEventCreate(&e));
+          h->events.push_back(e);
+        }
+      }
+      LaunchStep p = make_launch(h, h->cur, nullptr, 0, h->ntiles);
+      p.ev = h->events.data() + h->events_used;
+      h->events_used += 6;
+      CK(h, launch_step(h->prec, p, h->stream));
+      h->cur ^= 1;
+      h->step += 1;
+      nsteps -= 1;
+      continue;
+    }
+    if (nsteps >= kGraphSteps && h->cur == 0) {
+      if (!h->graph) {
+        cudaGraph_t g = nullptr;
+        CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t le = cudaSuccess;
+        for (int k = 0; k < kGraphSteps && le == cudaSuccess; ++k)
+          le = launch_step(h->prec, make_launch(h, k & 1, nullptr, 0, h->ntiles), h->stream);
+        cudaError_t ee = cudaStreamEndCapture(h->stream, &g);
+        if (le != cudaSuccess) return cuda_fail(h, le, "launch during capture");
+        if (ee != cudaSuccess) return cuda_fail(h, ee, "cudaStreamEndCapture");
+        cudaError_t ie = cudaGraphInstantiate(&h->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) return cuda_fail(h, ie, "cudaGraphInstantiate");
+      }
+      CK(h, cudaGraphLaunch(h->graph, h->stream));
+      nsteps -= kGraphSteps;
+      h->step += kGraphSteps;
+      continue;
+    }
+    CK(h, launch_step(h->prec, make_launch(h, h->cur, nullptr, 0, h->ntiles), h->stream));
+    h->cur ^= 1;
+    h->step += 1;
+    nsteps -= 1;
+  }
+  return LBCG_OK;
+}
+
+lbcg_status lbcg_observables(lbcg_handle* h, int32_t lattice, const lbcg_obs_spec* spec, lbcg_obs* out) {
+  lbcg_status s = check_handle(h);
+  if (s != LBCG_OK) return s;
+  if (!spec || !out) return fail(LBCG_E_ARG, "NULL spec or output");
+  if (lattice < 0 || lattice >= int(h->lats.size())) return fail(LBCG_E_ARG, "bad lattice index %d", lattice);
+  s = run_macro(h, lattice);
+  if (s != LBCG_OK) return s;
+  const LatHost& L = h->lats[lattice];
+  double* parts = h->d_obs;
+  double* res = h->d_obs + obs_partials_doubles();
+  CK(h, launch_observables(h->d_lats, lattice, L.nx, L.ny, h->d_macro, h->node_total, h->d_flags, spec->tip_row0,
+                           spec->tip_row1, spec->cl_row0, spec->cl_row1, parts, res, h->stream));
+  double o[kObsOut];
+  CK(h, cudaMemcpyAsync(o, res, sizeof(o), cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  memset(out, 0, sizeof(*out));
+  out->step = h->step;
+  out->mass_R = o[0];
+  out->mass_B = o[1];
+  out->umax = o[2];
+  for (int q = 0; q < 9; ++q) out->moments[q] = o[3 + q];
+  out->n_pts = o[3];
+  out->dp_laplace = (o[13] > 0 && o[15] > 0) ? o[12] / o[13] - o[14] / o[15] : NAN;
+  out->nonfinite = o[16] != 0 ? 1 : 0;
+  out->x_tip = o[kObsQ + 0];
+  {
+    double sx = 0;
+    int c = 0;
+    for (int r = 1; r <= 2; ++r)
+      if (o[kObsQ + r] >= 0) {
+        sx += o[kObsQ + r];
+        ++c;
+      }
+    out->x_cl = c ? sx / c : -1.0;
+  }
+  // Kasa circle fit from the moment sums: solve the 3x3 normal equations (Cramer's rule)
+  const double* m = out->moments;  // n, Sx, Sy, Sxx, Syy, Sxy, Szx, Szy, Sz
+  out->xc = out->yc = out->R = out->theta_deg = NAN;
+  if (m[0] >= 3) {
+    const double A[3][3] = {{m[3], m[5], m[1]}, {m[5], m[4], m[2]}, {m[1], m[2], m[0]}};
+    const double b[3] = {-m[6], -m[7], -m[8]};
+    auto det3 = [](const double M[3][3]) {
+      return M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) - M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+             M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+    };
+    const double D = det3(A);
+    if (D != 0) {
+      double sol[3];
+      for (int c = 0; c < 3; ++c) {
+        double Mc[3][3];
+        for (int i = 0; i < 3; ++i)
+          for (int j = 0; j < 3; ++j) Mc[i][j] = j == c ? b[i] : A[i][j];
+        sol[c] = det3(Mc) / D;
+      }
+      const double xc = -sol[0] / 2, yc = -sol[1] / 2;
+      const double R = std::sqrt(std::max(xc * xc + yc * yc - sol[2], 0.0));
+      out->xc = xc + 0.5 * L.nx;
+      out->yc = yc + 0.5 * L.ny;
+      out->R = R;
+      double c;
+      if (spec->cyl_r > 0) {
+        const double D2 = (out->xc - spec->cyl_x) * (out->xc - spec->cyl_x) + (out->yc - spec->cyl_y) * (out->yc - spec->cyl_y);
+        c = (spec->cyl_r * spec->cyl_r + R * R - D2) / (2 * spec->cyl_r * R);
+      } else {
+        c = R > 0 ? (spec->wall_y - out->yc) / R : NAN;
+      }
+      if (c == c) out->theta_deg = std::acos(std::max(-1.0, std::min(1.0, c))) * 180.0 / 3.14159265358979323846;
+    }
+  }
+  if (out->nonfinite) return fail(LBCG_E_DIVERGED, "non-finite density in lattice %d at step %lld", lattice, (long long)h->step);
+  return LBCG_OK;
+}
+
+lbcg_status lbcg_get_populations(lbcg_handle* h, int32_t lattice, double* host_out) {
+  lbcg_status s = check_handle(h);
+  if (s != LBCG_OK) return s;
+  if (!host_out || lattice < 0 || lattice >= int(h->lats.size())) return fail(LBCG_E_ARG, "bad arguments");
+  const LatHost& L = h->lats[lattice];
+  const size_t nn = (size_t)L.nx * L.ny;
+  double* tmp = nullptr;
+  if (cudaMalloc(&tmp, 18 * nn * sizeof(double)) != cudaSuccess) return fail(LBCG_E_NOMEM, "staging allocation");
+  cudaError_t e = launch_from_storage(h->prec, h->d_lats, lattice, (long long)nn, h->pool[h->cur], h->d_flags, tmp, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, tmp, 18 * nn * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  cudaFree(tmp);
+  if (e != cudaSuccess) return cuda_fail(h, e, "get_populations");
+  return LBCG_OK;
+}
+
+lbcg_status lbcg_set_populations(lbcg_handle* h, int32_t lattice, const double* host_in) {
+  lbcg_status s = check_handle(h);
+  if (s != LBCG_OK) return s;
+  if (!host_in || lattice < 0 || lattice >= int(h->lats.size())) return fail(LBCG_E_ARG, "bad arguments");
+  const LatHost& L = h->lats[lattice];
+  const size_t nn = (size_t)L.nx * L.ny;
+  double* tmp = nullptr;
+  if (cudaMalloc(&tmp, 18 * nn * sizeof(double)) != cudaSuccess) return fail(LBCG_E_NOMEM, "staging allocation");
+  cudaError_t e = cudaMemcpyAsync(tmp, host_in, 18 * nn * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = launch_to_storage(h->prec, h->d_lats, lattice, (long long)nn, tmp, h->d_flags, h->pool[h->cur], h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  cudaFree(tmp);
+  if (e != cudaSuccess) return cuda_fail(h, e, "set_populations");
+  return LBCG_OK;
+}
+
+lbcg_status lbcg_get_fields(lbcg_handle* h, int32_t lattice, double* host_out) {
+  lbcg_status s = check_handle(h);
+  if (s != LBCG_OK) return s;
+  if (!host_out || lattice < 0 || lattice >= int(h->lats.size())) return fail(LBCG_E_ARG, "bad arguments");
+  s = run_macro(h, lattice);
+  if (s != LBCG_OK) return s;
+  const LatHost& L = h->lats[lattice];
+  const size_t nn = (size_t)L.nx * L.ny;
+  std::vector<double> buf(4 * (size_t)L.plane);
+  for (int q = 0; q < 4; ++q)
+    CK(h, cudaMemcpyAsync(buf.data() + q * L.plane, h->d_macro + q * h->node_total + L.node_off,
+                          L.plane * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  for (int y = 0; y < L.ny; ++y)
+    for (int x = 0; x < L.nx; ++x) {
+      const size_t k = (size_t)y * L.pitch + x, i = (size_t)y * L.nx + x;
+      const bool solid = L.solid[i] != 0;
+      const double r = buf[k], b = buf[L.plane + k];
+      host_out[i] = solid ? 0.0 : r + b;
+      host_out[nn + i] = solid ? 0.0 : (r - b) / (r + b);
+      host_out[2 * nn + i] = solid ? 0.0 : buf[2 * L.plane + k];
+      host_out[3 * nn + i] = solid ? 0.0 : buf[3 * L.plane + k];
+    }
+  return LBCG_OK;
+}
+
+size_t lbcg_state_bytes(const lbcg_handle* h) {
+  return h ? 18 * (size_t)h->node_total * elem_size(h->prec) : 0;
+}
+
+lbcg_status lbcg_upload_state(lbcg_handle* h, const void* host_in, size_t bytes) {
+  lbcg_status s = check_handle(h);
+  if (s != LBCG_OK) return s;
+  if (!host_in || bytes != lbcg_state_bytes(h)) return fail(LBCG_E_ARG, "state size mismatch");
+  CK(h, cudaMemcpyAsync(h->pool[h->cur], host_in, bytes, cudaMemcpyHostToDevice, h->stream));
+  return LBCG_OK;
+}
+
+lbcg_status lbcg_download_state(lbcg_handle* h, void* host_out, size_t bytes) {
+  lbcg_status s = check_handle(h);
+  if (s != LBCG_OK) return s;
+  if (!host_out || bytes != lbcg_state_bytes(h)) return fail(LBCG_E_ARG, "state size mismatch");
+  CK(h, cudaMemcpyAsync(host_out, h->pool[h->cur], bytes, cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  return LBCG_OK;
+}
+
+lbcg_status lbcg_set_tile(lbcg_handle* h, int32_t ty) {
+  lbcg_status s = check_handle(h);
+  if (s != LBCG_OK) return s;
+  if (ty == 0) ty = kDefaultTY;
+  if (ty != 4 && ty != 8 && ty != 16) return fail(LBCG_E_ARG, "tile height must be 4, 8 or 16");
+  CK(h, cudaStreamSynchronize(h->stream));
+  h->ty = ty;
+  if (h->graph) {
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  return upload_tiles(h);
+}
+
+lbcg_status lbcg_profile(lbcg_handle* h, int32_t enable) {
+  lbcg_status s = check_handle(h);
+  if (s != LBCG_OK) return s;
+  CK(h, cudaStreamSynchronize(h->stream));
+  h->profiling = enable != 0;
+  h->events_used = 0;
+  return LBCG_OK;
+}
+
+lbcg_status lbcg_kernel_times(lbcg_handle* h, double* ms3, int64_t* steps) {
+  lbcg_status s = check_handle(h);
+  if (s != LBCG_OK) return s;
+  if (!ms3 || !steps) return fail(LBCG_E_ARG, "NULL output");
+  CK(h, cudaStreamSynchronize(h->stream));
+  ms3[0] = ms3[1] = ms3[2] = 0.0;
+  for (size_t i = 0; i + 6 <= h->events_used; i += 6)
+    for (int k = 0; k < 3; ++k) {
+      float t = 0.f;
+      CK(h, cudaEventElapsedTime(&t, h->events[i + 2 * k], h->events[i + 2 * k + 1]));
+      ms3[k] += t;
+    }
+  *steps = (int64_t)(h->events_used / 6);
+  h->events_used = 0;
+  return LBCG_OK;
+}
+
+int32_t lbcg_launches_per_step(const lbcg_handle* h) {
+  if (!h) return 0;
+  return (h->nband > 0 ? 1 : 0) + (h->nofb > 0 ? 1 : 0) + (h->ntiles > 0 ? 1 : 0);
+}
+
+int64_t lbcg_total_nodes(const lbcg_handle* h) {
+  if (!h) return 0;
+  int64_t n = 0;
+  for (const LatHost& L : h->lats) n += (int64_t)L.nx * L.ny;
+  return n;
+}
+
+lbcg_status lbcg_destroy(lbcg_handle* h) {
+  if (!h) return LBCG_OK;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  free_handle(h);
+  return LBCG_OK;
+}
+
+}  // extern "C"

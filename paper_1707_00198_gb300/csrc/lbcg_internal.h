@@ -1,0 +1,49 @@
+// Internal interface between the host runtime (lbcg_host.cu) and the kernel launchers
+// (lbcg_kernels.cu, lbcg_obs.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lbcg_device.cuh"
+
+namespace lbcg {
+
+// Everything one launch of the step kernels needs (device pointers).
+struct LaunchStep {
+  const LatDev* lats;
+  const int4* band;       // wall band list (lattice, x, y, -)
+  int nband;
+  const OfbEntry* ofb;    // outermost fluid list
+  int nofb;
+  const int4* tiles;      // tile list (lattice, x0, y0, -)
+  int ntiles;
+  int ty;                 // tile height (tiles are 32 wide)
+  const void* src;
+  void* dst;
+  const uint8_t* flags;
+  void* band_rn;
+  void* wall;
+  long long node_total;
+  double* macro;          // non-null: write macroscopic fields instead of stepping
+  cudaEvent_t* ev;        // non-null: 6 events recorded around k_band, k_wall, k_step
+};
+
+cudaError_t launch_step(int prec, const LaunchStep& p, cudaStream_t st);
+cudaError_t launch_to_storage(int prec, const LatDev* lats, int lat, long long nn, const double* in,
+                              const uint8_t* flags, void* pool, cudaStream_t st);
+cudaError_t launch_from_storage(int prec, const LatDev* lats, int lat, long long nn, const void* pool,
+                                const uint8_t* flags, double* out, cudaStream_t st);
+
+// Observable reductions over one lattice's macroscopic fields (lbcg_obs.cu).
+// `partials` must hold obs_partials_doubles(nx*ny) doubles; `out` receives kObsOut doubles.
+constexpr int kObsQ = 17;     // reduced quantities
+constexpr int kObsRows = 3;   // row-crossing results
+constexpr int kObsOut = kObsQ + kObsRows;
+constexpr int kObsBlocks = 304;  // 2 x 152 SMs
+size_t obs_partials_doubles();
+cudaError_t launch_observables(const LatDev* lats, int lat, int nx, int ny, const double* macro,
+                               long long node_total, const uint8_t* flags, int tip0, int tip1, int cl0, int cl1,
+                               double* partials, double* out, cudaStream_t st);
+
+}  // namespace lbcg

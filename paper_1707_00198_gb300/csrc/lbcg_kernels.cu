@@ -1,0 +1,508 @@
+// Kernels of one time step of the colour-gradient LBM with the improved wetting scheme
+// (arXiv 1707.00198, Sec. II).  Per step, in stream order:
+//   k_band  : rho^N (Eq. 12, 16) on the wall band = outermost fluid nodes and their fluid
+//             neighbours, from the pulled post-streaming populations;
+//   k_wall  : on every outermost fluid node the gradient of Eq. 28 with the virtual values
+//             of Eq. 29 and the contact-angle correction of Eq. 30-36 -> corrected gradient
+//             and unit normal, kept in two small node arrays;
+//   k_step  : the fused bulk step over 32 x TY tiles: pull (streaming + bounce-back folded
+//             into the loads) -> rho^N on the tile plus a 2-node halo (shared memory) ->
+//             n on the tile plus a 1-node halo (outermost-fluid values from k_wall, virtual
+//             n on outermost solid nodes, Eq. 29) -> grad n, kappa, F (Eq. 10, 13, 28) ->
+//             u, nu, MRT collision with Guo forcing (Eq. 1-9, 17, 18) -> recolouring
+//             (Eq. 14) -> store of the post-collision populations at the node.
+#include "lbcg_device.cuh"
+#include "lbcg_internal.h"
+
+namespace lbcg {
+
+struct StepArgs {
+  const LatDev* lats;
+  const int4* tiles;      // (lattice, x0, y0, -)
+  const void* src;        // population pool read this step
+  void* dst;              // population pool written this step
+  const uint8_t* flags;   // node flags
+  const void* band_rn;    // rho^N on the wall band (compute type)
+  void* wall;             // 4 planes of node arrays: g_x, g_y, n_x, n_y (compute type)
+  long long node_total;   // elements per node-array plane
+  double* macro;          // 4 planes of doubles: rho_R, rho_B, u_x, u_y (macro mode)
+};
+
+// ------------------------------------------------------------------ k_band
+template <typename S>
+__global__ void __launch_bounds__(256) k_band(const LatDev* __restrict__ lats, const int4* __restrict__ list,
+                                              int n, const S* __restrict__ src, const uint8_t* __restrict__ flags,
+                                              typename Store<S>::T* __restrict__ band_rn) {
+  using T = typename Store<S>::T;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int4 e = list[i];
+  const LatDev& L = lats[e.x];
+  const int x = e.y, y = e.z;
+  const bool px = L.bcx == BC_PERIODIC, py = L.bcy == BC_PERIODIC;
+  int xm[3], ym[3];
+#pragma unroll
+  for (int d = -1; d <= 1; ++d) {
+    xm[d + 1] = wrap_or_clamp(x + d, L.nx, px);
+    ym[d + 1] = wrap_or_clamp(y + d, L.ny, py);
+  }
+  const uint8_t* fl = flags + L.node_off;
+  auto solid_at = [&](int dx, int dy) { return (fl[(long long)ym[dy + 1] * L.pitch + xm[dx + 1]] & F_SOLID) != 0; };
+  T fr[9], fb[9], rR, rB;
+  pull_node<S>(L, src, x, xm, ym, solid_at, fr, fb);
+  band_rn[L.node_off + (long long)y * L.pitch + x] = colour_indicator(fr, fb, rR, rB);
+}
+
+// ------------------------------------------------------------------ k_wall
+// Eq. 28 with Eq. 29 at solid neighbours, then Eq. 30-36; evaluated with the rounding-exact
+// helpers in the oracle's order (directions 1..8, products w*phi then sign).
+template <typename T>
+__global__ void __launch_bounds__(256) k_wall(const LatDev* __restrict__ lats, const OfbEntry* __restrict__ list,
+                                              int n, const uint8_t* __restrict__ flags,
+                                              const T* __restrict__ band_rn, T* __restrict__ wall,
+                                              long long node_total) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const OfbEntry e = list[i];
+  const LatDev& L = lats[e.lat];
+  const bool px = L.bcx == BC_PERIODIC, py = L.bcy == BC_PERIODIC;
+  const uint8_t* fl = flags + L.node_off;
+  const T* rn = band_rn + L.node_off;
+  T gx = T(0), gy = T(0);
+#pragma unroll
+  for (int a = 1; a < 9; ++a) {
+    const int xx = wrap_or_clamp(e.x + ex(a), L.nx, px);
+    const int yy = wrap_or_clamp(e.y + ey(a), L.ny, py);
+    const long long k = (long long)yy * L.pitch + xx;
+    T v;
+    if (fl[k] & F_SOLID) {
+      // Eq. 29: weighted mean over the fluid neighbours of the outermost solid node
+      T num = T(0), den = T(0);
+#pragma unroll
+      for (int b = 1; b < 9; ++b) {
+        const int x2 = wrap_or_clamp(xx + ex(b), L.nx, px);
+        const int y2 = wrap_or_clamp(yy + ey(b), L.ny, py);
+        const long long k2 = (long long)y2 * L.pitch + x2;
+        if (!(fl[k2] & F_SOLID)) {
+          num = radd(num, rmul(wgt<T>(b), rn[k2]));
+          den = radd(den, wgt<T>(b));
+        }
+      }
+      v = rdiv(num, den);
+    } else {
+      v = rn[k];
+    }
+    const T t = rmul(wgt<T>(a), v);
+    if (ex(a) == 1) gx = radd(gx, t);
+    if (ex(a) == -1) gx = radd(gx, -t);
+    if (ey(a) == 1) gy = radd(gy, t);
+    if (ey(a) == -1) gy = radd(gy, -t);
+  }
+  const T cs2 = T(1.0 / 3.0);
+  gx = rdiv(gx, cs2);
+  gy = rdiv(gy, cs2);
+  const T eps = T(L.grad_eps);
+  const T mag = rsqrt_(radd(rmul(gx, gx), rmul(gy, gy)));
+  T cgx = gx, cgy = gy, nx = T(0), ny = T(0);
+  if (mag > eps) {
+    const T esx = rdiv(gx, mag), esy = rdiv(gy, mag);                 // Eq. 30
+    const T nsx = T(e.nsx), nsy = T(e.nsy), c = T(e.cos_t), s = T(e.sin_t);
+    const T f1x = rsub(rmul(nsx, c), rmul(nsy, s));                   // Eq. 34, +theta
+    const T f1y = radd(rmul(nsx, s), rmul(nsy, c));
+    const T f2x = radd(rmul(nsx, c), rmul(nsy, s));                   // Eq. 34, -theta
+    const T f2y = radd(rmul(-nsx, s), rmul(nsy, c));
+    const T a1 = rsub(f1x, esx), b1 = rsub(f1y, esy);
+    const T a2 = rsub(f2x, esx), b2 = rsub(f2y, esy);
+    const T d1 = rsqrt_(radd(rmul(a1, a1), rmul(b1, b1)));            // Eq. 35
+    const T d2 = rsqrt_(radd(rmul(a2, a2), rmul(b2, b2)));
+    const T nfx = d1 <= d2 ? f1x : f2x;                               // Eq. 36
+    const T nfy = d1 <= d2 ? f1y : f2y;
+    cgx = rmul(mag, nfx);                                             // Eq. 31
+    cgy = rmul(mag, nfy);
+    const T m2 = rsqrt_(radd(rmul(cgx, cgx), rmul(cgy, cgy)));
+    if (m2 > eps) {
+      nx = rdiv(cgx, m2);
+      ny = rdiv(cgy, m2);
+    }
+  }
+  const long long k = L.node_off + (long long)e.y * L.pitch + e.x;
+  wall[k] = cgx;
+  wall[node_total + k] = cgy;
+  wall[2 * node_total + k] = nx;
+  wall[3 * node_total + k] = ny;
+}
+
+// ------------------------------------------------------------------ k_step
+template <typename S, int TY, bool MACRO>
+__global__ void __launch_bounds__(32 * TY) k_step(StepArgs A) {
+  using T = typename Store<S>::T;
+  constexpr int TX = 32;
+  constexpr int NT = TX * TY;
+  constexpr int W3 = TX + 6, H3 = TY + 6;   // flags: tile + 3
+  constexpr int W2 = TX + 4, H2 = TY + 4;   // rho^N: tile + 2
+  constexpr int W1 = TX + 2, H1 = TY + 2;   // n: tile + 1
+  __shared__ uint8_t sfl[H3 * W3];
+  __shared__ T srn[H2 * W2];
+  __shared__ T snx[H1 * W1];
+  __shared__ T sny[H1 * W1];
+  __shared__ int sxm[W3];
+  __shared__ int sym[H3];
+
+  const int4 tl = A.tiles[blockIdx.x];
+  const LatDev& L = A.lats[tl.x];
+  const int x0 = tl.y, y0 = tl.z;
+  const int tid = threadIdx.x;
+  const int nx = L.nx, ny = L.ny, pitch = L.pitch;
+  const bool px = L.bcx == BC_PERIODIC, py = L.bcy == BC_PERIODIC;
+  const uint8_t* __restrict__ fl = A.flags + L.node_off;
+  const S* __restrict__ src = static_cast<const S*>(A.src);
+
+  // mapped lattice coordinates of every halo column / row
+  for (int i = tid; i < W3; i += NT) sxm[i] = wrap_or_clamp(x0 + i - 3, nx, px);
+  for (int i = tid; i < H3; i += NT) sym[i] = wrap_or_clamp(y0 + i - 3, ny, py);
+  __syncthreads();
+  for (int i = tid; i < H3 * W3; i += NT) {
+    const int cx = i % W3, cy = i / W3;
+    sfl[i] = fl[(long long)sym[cy] * pitch + sxm[cx]];
+  }
+  __syncthreads();
+
+  // ---- phase A: rho^N on tile + 2 (own node keeps its populations in registers)
+  const int lx = tid % TX, ly = tid / TX;
+  T fr[9], fb[9], rhoR = T(0), rhoB = T(0), rn = T(0);
+  const uint8_t myfl = sfl[(ly + 3) * W3 + lx + 3];
+  const bool fluid = !(myfl & F_SOLID);
+  {
+    const int c3x = lx + 3, c3y = ly + 3;
+    if (fluid) {
+      const int xm[3] = {sxm[c3x - 1], sxm[c3x], sxm[c3x + 1]};
+      const int ym[3] = {sym[c3y - 1], sym[c3y], sym[c3y + 1]};
+      auto solid_at = [&](int dx, int dy) { return (sfl[(c3y + dy) * W3 + c3x + dx] & F_SOLID) != 0; };
+      pull_node<S>(L, src, sxm[c3x], xm, ym, solid_at, fr, fb);
+      rn = colour_indicator(fr, fb, rhoR, rhoB);
+    } else {
+#pragma unroll
+      for (int a = 0; a < 9; ++a) fr[a] = fb[a] = T(0);
+    }
+    srn[(ly + 2) * W2 + lx + 2] = rn;
+  }
+  for (int i = tid; i < H2 * W2; i += NT) {
+    const int cx = i % W2, cy = i / W2;
+    if (cx >= 2 && cx < TX + 2 && cy >= 2 && cy < TY + 2) continue;
+    const int c3x = cx + 1, c3y = cy + 1;
+    T v = T(0);
+    if (!(sfl[c3y * W3 + c3x] & F_SOLID)) {
+      const int xm[3] = {sxm[c3x - 1], sxm[c3x], sxm[c3x + 1]};
+      const int ym[3] = {sym[c3y - 1], sym[c3y], sym[c3y + 1]};
+      auto solid_at = [&](int dx, int dy) { return (sfl[(c3y + dy) * W3 + c3x + dx] & F_SOLID) != 0; };
+      T hr[9], hb[9], a1, a2;
+      pull_node<S>(L, src, sxm[c3x], xm, ym, solid_at, hr, hb);
+      v = colour_indicator(hr, hb, a1, a2);
+    }
+    srn[i] = v;
+  }
+  __syncthreads();
+
+  // ---- phase B: grad rho^N and n on tile + 1
+  const T eps = T(L.grad_eps);
+  const T* __restrict__ wall = static_cast<const T*>(A.wall);
+  const long long NTOT = A.node_total;
+  T gx = T(0), gy = T(0);
+  for (int i = tid; i < H1 * W1 + NT; i += NT) {
+    // the first NT iterations cover the own tile node, the rest the ring of tile + 1
+    int cx, cy;
+    bool own = i < NT;
+    if (own) {
+      cx = lx + 1;
+      cy = ly + 1;
+    } else {
+      const int j = i - NT;
+      cx = j % W1;
+      cy = j / W1;
+      if (cx >= 1 && cx < TX + 1 && cy >= 1 && cy < TY + 1) continue;
+    }
+    const int c3x = cx + 2, c3y = cy + 2;
+    const uint8_t f = sfl[c3y * W3 + c3x];
+    const long long k = L.node_off + (long long)sym[c3y] * pitch + sxm[c3x];
+    T ax = T(0), ay = T(0), nxv = T(0), nyv = T(0);
+    if (!(f & F_SOLID)) {
+      if (f & F_OFB) {
+        ax = wall[k];
+        ay = wall[NTOT + k];
+        nxv = wall[2 * NTOT + k];
+        nyv = wall[3 * NTOT + k];
+      } else {
+        const int c2x = cx + 1, c2y = cy + 1;
+#pragma unroll
+        for (int a = 1; a < 9; ++a) {
+          const T t = wgt<T>(a) * srn[(c2y + ey(a)) * W2 + c2x + ex(a)];
+          ax += T(ex(a)) * t;
+          ay += T(ey(a)) * t;
+        }
+        ax *= T(3);
+        ay *= T(3);
+        const T m = sqrt(ax * ax + ay * ay);
+        if (m > eps) {
+          nxv = ax / m;
+          nyv = ay / m;
+        }
+      }
+    } else if (f & F_OSOLID) {
+      // virtual n on the outermost solid node (Eq. 29); its fluid neighbours are outermost
+      // fluid nodes, whose n k_wall has stored
+      T sx = T(0), sy = T(0), den = T(0);
+#pragma unroll
+      for (int b = 1; b < 9; ++b) {
+        if (!(sfl[(c3y + ey(b)) * W3 + c3x + ex(b)] & F_SOLID)) {
+          const long long k2 = L.node_off + (long long)sym[c3y + ey(b)] * pitch + sxm[c3x + ex(b)];
+          sx += wgt<T>(b) * wall[2 * NTOT + k2];
+          sy += wgt<T>(b) * wall[3 * NTOT + k2];
+          den += wgt<T>(b);
+        }
+      }
+      nxv = sx / den;
+      nyv = sy / den;
+    }
+    snx[cy * W1 + cx] = nxv;
+    sny[cy * W1 + cx] = nyv;
+    if (own) {
+      gx = ax;
+      gy = ay;
+    }
+  }
+  __syncthreads();
+
+  // ---- phase C: curvature, force, collision, recolouring, store (own node)
+  const int xs = x0 + lx, ys = y0 + ly;
+  if (!fluid || xs >= nx || ys >= ny) return;
+  const int c1x = lx + 1, c1y = ly + 1;
+  T dxx = T(0), dxy = T(0), dyx = T(0), dyy = T(0);  // d_x n_x, d_y n_x, d_x n_y, d_y n_y
+#pragma unroll
+  for (int a = 1; a < 9; ++a) {
+    const int o = (c1y + ey(a)) * W1 + c1x + ex(a);
+    const T tx = wgt<T>(a) * snx[o];
+    const T ty = wgt<T>(a) * sny[o];
+    dxx += T(ex(a)) * tx;
+    dxy += T(ey(a)) * tx;
+    dyx += T(ex(a)) * ty;
+    dyy += T(ey(a)) * ty;
+  }
+  dxx *= T(3);
+  dxy *= T(3);
+  dyx *= T(3);
+  dyy *= T(3);
+  const T nxo = snx[c1y * W1 + c1x], nyo = sny[c1y * W1 + c1x];
+  const T kappa = -nxo * nxo * dyy - nyo * nyo * dxx + nxo * nyo * (dxy + dyx);   // Eq. 13
+  const T Fx = T(0.5) * T(L.sigma) * kappa * gx;                                  // Eq. 10
+  const T Fy = T(0.5) * T(L.sigma) * kappa * gy;
+
+  T f[9];
+#pragma unroll
+  for (int a = 0; a < 9; ++a) f[a] = fr[a] + fb[a];
+  const T rho = rhoR + rhoB;
+  const T jx = f[1] - f[3] + f[5] - f[6] - f[7] + f[8];
+  const T jy = f[2] - f[4] + f[5] + f[6] - f[7] - f[8];
+  const T ux = (jx + T(0.5) * Fx) / rho;                                          // Eq. 17
+  const T uy = (jy + T(0.5) * Fy) / rho;
+  const long long kn = (long long)ys * pitch + xs;
+  if constexpr (MACRO) {
+    const long long k = L.node_off + kn;
+    A.macro[k] = double(rhoR);
+    A.macro[NTOT + k] = double(rhoB);
+    A.macro[2 * NTOT + k] = double(ux);
+    A.macro[3 * NTOT + k] = double(uy);
+    return;
+  } else {
+    // local viscosity (Eq. 18) and shear rate s_v = 1/tau_v (Eq. 5)
+    const T inv_nu = (T(1) + rn) / T(2 * L.nu_R) + (T(1) - rn) / T(2 * L.nu_B);
+    const T sv = T(1) / (T(3) / inv_nu + T(0.5));
+    const T se = T(L.s_e), seps = T(L.s_eps), sq = T(L.s_q);
+    // moments (rows of Eq. 3, the last one read as e_x e_y)
+    const T s14 = f[1] + f[2] + f[3] + f[4];
+    const T s58 = f[5] + f[6] + f[7] + f[8];
+    const T me = T(-4) * f[0] - s14 + T(2) * s58;
+    const T meps = T(4) * f[0] - T(2) * s14 + s58;
+    const T qx = T(-2) * (f[1] - f[3]) + (f[5] - f[6] - f[7] + f[8]);
+    const T qy = T(-2) * (f[2] - f[4]) + (f[5] + f[6] - f[7] - f[8]);
+    const T pxx = f[1] - f[2] + f[3] - f[4];
+    const T pxy = f[5] - f[6] + f[7] - f[8];
+    const T u2 = ux * ux + uy * uy;
+    const T uF = ux * Fx + uy * Fy;
+    // Delta_k = s_k (m_k - m_k^eq) - (1 - s_k/2) (M F~)_k  with M F~ =
+    // (0, 6 u.F, -6 u.F, Fx, -Fx, Fy, -Fy, 2(ux Fx - uy Fy), ux Fy + uy Fx)   (Eq. 8-9)
+    const T De = se * (me - rho * (T(-2) + T(3) * u2)) - (T(1) - T(0.5) * se) * (T(6) * uF);
+    const T Deps = seps * (meps - rho * (T(1) - T(3) * u2)) + (T(1) - T(0.5) * seps) * (T(6) * uF);
+    const T Djx = -Fx, Djy = -Fy;  // s_rho = s_j = 1 (Eq. 6): momentum changes by exactly F
+    const T Dqx = sq * (qx + rho * ux) + (T(1) - T(0.5) * sq) * Fx;
+    const T Dqy = sq * (qy + rho * uy) + (T(1) - T(0.5) * sq) * Fy;
+    const T Dxx = sv * (pxx - rho * (ux * ux - uy * uy)) - (T(1) - T(0.5) * sv) * (T(2) * (ux * Fx - uy * Fy));
+    const T Dxy = sv * (pxy - rho * ux * uy) - (T(1) - T(0.5) * sv) * (ux * Fy + uy * Fx);
+    // M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4)
+    const T ae = De * T(1.0 / 36.0), aeps = Deps * T(1.0 / 36.0);
+    const T ajx = Djx * T(1.0 / 6.0), ajy = Djy * T(1.0 / 6.0);
+    const T aqx = Dqx * T(1.0 / 12.0), aqy = Dqy * T(1.0 / 12.0);
+    const T axx = Dxx * T(0.25), axy = Dxy * T(0.25);
+    T fp[9];
+    fp[0] = f[0] - (T(-4) * ae + T(4) * aeps);
+    const T c14 = -ae - T(2) * aeps;
+    fp[1] = f[1] - (c14 + ajx - T(2) * aqx + axx);
+    fp[2] = f[2] - (c14 + ajy - T(2) * aqy - axx);
+    fp[3] = f[3] - (c14 - ajx + T(2) * aqx + axx);
+    fp[4] = f[4] - (c14 - ajy + T(2) * aqy - axx);
+    const T c58 = T(2) * ae + aeps;
+    fp[5] = f[5] - (c58 + ajx + aqx + ajy + aqy + axy);
+    fp[6] = f[6] - (c58 - ajx - aqx + ajy + aqy - axy);
+    fp[7] = f[7] - (c58 - ajx - aqx - ajy - aqy + axy);
+    fp[8] = f[8] - (c58 + ajx + aqx - ajy - aqy - axy);
+    // recolouring (Eq. 14; the blue line with the minus sign)
+    const T cR = rhoR / rho, cB = rhoB / rho;
+    const T pc = T(L.beta) * rhoR * rhoB / rho;
+    S* __restrict__ dst = static_cast<S*>(A.dst) + L.pop_off + kn;
+    const T r0 = T(L.rho0);
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+      const T en = T(ex(a)) * nxo + T(ey(a)) * nyo;
+      const T pert = pc * wgt<T>(a) * en;
+      const T oR = cR * fp[a] + pert;
+      const T oB = cB * fp[a] - pert;
+      T lo, hi;
+      encode<S, T>(oR, oB, wgt<T>(a) * r0, lo, hi);
+      dst[(long long)a * L.plane] = Store<S>::cv(lo);
+      dst[(long long)(9 + a) * L.plane] = Store<S>::cv(hi);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ layout conversion
+// host layout: double [2][9][ny][nx] (f_R block then f_B block) <-> storage pool
+template <typename S>
+__global__ void k_to_storage(const LatDev* __restrict__ lats, int lat, const double* __restrict__ in,
+                             const uint8_t* __restrict__ flags, S* __restrict__ pool) {
+  using T = typename Store<S>::T;
+  const LatDev& L = lats[lat];
+  const long long nn = (long long)L.nx * L.ny;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 9 * nn) return;
+  const int a = int(i / nn);
+  const long long r = i % nn;
+  const int y = int(r / L.nx), x = int(r % L.nx);
+  const long long k = (long long)y * L.pitch + x;
+  const bool solid = flags[L.node_off + k] & F_SOLID;
+  const T fr = solid ? T(0) : T(in[i]);
+  const T fb = solid ? T(0) : T(in[9 * nn + i]);
+  T lo, hi;
+  encode<S, T>(fr, fb, solid ? T(0) : wgt<T>(a) * T(L.rho0), lo, hi);
+  pool[L.pop_off + (long long)a * L.plane + k] = Store<S>::cv(lo);
+  pool[L.pop_off + (long long)(9 + a) * L.plane + k] = Store<S>::cv(hi);
+}
+
+template <typename S>
+__global__ void k_from_storage(const LatDev* __restrict__ lats, int lat, const S* __restrict__ pool,
+                               const uint8_t* __restrict__ flags, double* __restrict__ out) {
+  using T = typename Store<S>::T;
+  const LatDev& L = lats[lat];
+  const long long nn = (long long)L.nx * L.ny;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 9 * nn) return;
+  const int a = int(i / nn);
+  const long long r = i % nn;
+  const int y = int(r / L.nx), x = int(r % L.nx);
+  const long long k = (long long)y * L.pitch + x;
+  const bool solid = flags[L.node_off + k] & F_SOLID;
+  T fr = T(0), fb = T(0);
+  if (!solid) {
+    const T lo = Store<S>::ld(pool + L.pop_off + (long long)a * L.plane + k);
+    const T hi = Store<S>::ld(pool + L.pop_off + (long long)(9 + a) * L.plane + k);
+    decode<S, T>(lo, hi, wgt<T>(a) * T(L.rho0), fr, fb);
+  }
+  out[i] = double(fr);
+  out[9 * nn + i] = double(fb);
+}
+
+// ------------------------------------------------------------------ launchers
+template <typename S>
+static cudaError_t launch_all(const LaunchStep& p, cudaStream_t st) {
+  using T = typename Store<S>::T;
+  auto rec = [&](int i) {
+    if (p.ev) cudaEventRecord(p.ev[i], st);
+  };
+  rec(0);
+  if (p.nband > 0) {
+    k_band<S><<<(p.nband + 255) / 256, 256, 0, st>>>(p.lats, p.band, p.nband, static_cast<const S*>(p.src),
+                                                     p.flags, static_cast<T*>(p.band_rn));
+  }
+  rec(1);
+  rec(2);
+  if (p.nofb > 0) {
+    k_wall<T><<<(p.nofb + 255) / 256, 256, 0, st>>>(p.lats, p.ofb, p.nofb, p.flags,
+                                                    static_cast<const T*>(p.band_rn), static_cast<T*>(p.wall),
+                                                    p.node_total);
+  }
+  rec(3);
+  rec(4);
+  if (p.ntiles > 0) {
+    StepArgs A{p.lats, p.tiles, p.src, p.dst, p.flags, p.band_rn, p.wall, p.node_total, p.macro};
+    const bool macro = p.macro != nullptr;
+    switch (p.ty) {
+      case 4:
+        if (macro) k_step<S, 4, true><<<p.ntiles, 128, 0, st>>>(A);
+        else k_step<S, 4, false><<<p.ntiles, 128, 0, st>>>(A);
+        break;
+      case 16:
+        if (macro) k_step<S, 16, true><<<p.ntiles, 512, 0, st>>>(A);
+        else k_step<S, 16, false><<<p.ntiles, 512, 0, st>>>(A);
+        break;
+      default:
+        if (macro) k_step<S, 8, true><<<p.ntiles, 256, 0, st>>>(A);
+        else k_step<S, 8, false><<<p.ntiles, 256, 0, st>>>(A);
+        break;
+    }
+  }
+  rec(5);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step(int prec, const LaunchStep& p, cudaStream_t st) {
+  switch (prec) {
+    case 0: return launch_all<double>(p, st);
+    case 1: return launch_all<float>(p, st);
+    case 2: return launch_all<__half>(p, st);
+    case 3: return launch_all<__nv_bfloat16>(p, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_to_storage(int prec, const LatDev* lats, int lat, long long nn, const double* in,
+                              const uint8_t* flags, void* pool, cudaStream_t st) {
+  const long long n = 9 * nn;
+  const int blocks = int((n + 255) / 256);
+  switch (prec) {
+    case 0: k_to_storage<double><<<blocks, 256, 0, st>>>(lats, lat, in, flags, static_cast<double*>(pool)); break;
+    case 1: k_to_storage<float><<<blocks, 256, 0, st>>>(lats, lat, in, flags, static_cast<float*>(pool)); break;
+    case 2: k_to_storage<__half><<<blocks, 256, 0, st>>>(lats, lat, in, flags, static_cast<__half*>(pool)); break;
+    case 3:
+      k_to_storage<__nv_bfloat16><<<blocks, 256, 0, st>>>(lats, lat, in, flags, static_cast<__nv_bfloat16*>(pool));
+      break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_from_storage(int prec, const LatDev* lats, int lat, long long nn, const void* pool,
+                                const uint8_t* flags, double* out, cudaStream_t st) {
+  const long long n = 9 * nn;
+  const int blocks = int((n + 255) / 256);
+  switch (prec) {
+    case 0: k_from_storage<double><<<blocks, 256, 0, st>>>(lats, lat, static_cast<const double*>(pool), flags, out); break;
+    case 1: k_from_storage<float><<<blocks, 256, 0, st>>>(lats, lat, static_cast<const float*>(pool), flags, out); break;
+    case 2: k_from_storage<__half><<<blocks, 256, 0, st>>>(lats, lat, static_cast<const __half*>(pool), flags, out); break;
+    case 3:
+      k_from_storage<__nv_bfloat16><<<blocks, 256, 0, st>>>(lats, lat, static_cast<const __nv_bfloat16*>(pool), flags,
+                                                            out);
+      break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace lbcg

@@ -1,0 +1,281 @@
+"""ctypes binding of liblbcg.so (the C ABI declared in include/lbcg.h).
+
+Module-level functions carry the names of the C entry points and only marshal arguments;
+every step of the method runs in the library's CUDA kernels.  ``Lattice`` is a small
+convenience wrapper around one handle.  There is no fallback: if the library is missing or
+a call fails, an exception is raised.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from .inputs import Geometry, Params
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblbcg.so")
+
+LBCG_FP64, LBCG_FP32, LBCG_FP16_STORE, LBCG_BF16_STORE = 0, 1, 2, 3
+PRECISIONS = {"fp64": LBCG_FP64, "fp32": LBCG_FP32, "fp16": LBCG_FP16_STORE, "bf16": LBCG_BF16_STORE}
+STORE_BYTES = {LBCG_FP64: 8, LBCG_FP32: 4, LBCG_FP16_STORE: 2, LBCG_BF16_STORE: 2}
+_BCX = {"periodic": 0, "closed": 1, "inout": 2}
+_BCY = {"periodic": 0, "closed": 1}
+STATUS = {0: "LBCG_OK", 1: "LBCG_E_ARG", 2: "LBCG_E_GEOMETRY", 3: "LBCG_E_UNSTABLE_PARAM", 4: "LBCG_E_CUDA",
+          5: "LBCG_E_DIVERGED", 6: "LBCG_E_TIMEOUT", 7: "LBCG_E_UNSUPPORTED", 8: "LBCG_E_NOMEM"}
+
+
+class lbcg_geometry(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("bc_x", C.c_int32), ("bc_y", C.c_int32),
+                ("solid", C.POINTER(C.c_uint8)), ("rhoN0", C.POINTER(C.c_double)),
+                ("normal", C.POINTER(C.c_double)), ("theta_node", C.POINTER(C.c_double))]
+
+
+class lbcg_params(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("nu_R", "nu_B", "sigma", "theta", "beta", "s_e", "s_eps", "s_q",
+                                          "rho0", "u_in", "rho_out", "grad_eps")]
+
+
+class lbcg_obs_spec(C.Structure):
+    _fields_ = [("wall_y", C.c_double), ("cyl_x", C.c_double), ("cyl_y", C.c_double), ("cyl_r", C.c_double),
+                ("tip_row0", C.c_int32), ("tip_row1", C.c_int32), ("cl_row0", C.c_int32), ("cl_row1", C.c_int32)]
+
+
+class lbcg_obs(C.Structure):
+    _fields_ = [("step", C.c_int64), ("mass_R", C.c_double), ("mass_B", C.c_double), ("umax", C.c_double),
+                ("n_pts", C.c_double), ("xc", C.c_double), ("yc", C.c_double), ("R", C.c_double),
+                ("theta_deg", C.c_double), ("dp_laplace", C.c_double), ("x_tip", C.c_double),
+                ("x_cl", C.c_double), ("moments", C.c_double * 9), ("nonfinite", C.c_int32)]
+
+
+class LBCGError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def library():
+    """Load liblbcg.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1707_00198_gb300.build.build() "
+                           "(or __graft_entry__.build()); there is no CPU fallback")
+    lib = C.CDLL(LIB_PATH)
+    H = C.c_void_p
+    sigs = {
+        "lbcg_create": (C.c_int, [C.POINTER(lbcg_geometry), C.POINTER(lbcg_params), C.c_int32, C.c_void_p,
+                                  C.POINTER(H)]),
+        "lbcg_create_batch": (C.c_int, [C.c_int32, C.POINTER(lbcg_geometry), C.POINTER(lbcg_params), C.c_int32,
+                                        C.c_void_p, C.POINTER(H)]),
+        "lbcg_step": (C.c_int, [H, C.c_int64]),
+        "lbcg_observables": (C.c_int, [H, C.c_int32, C.POINTER(lbcg_obs_spec), C.POINTER(lbcg_obs)]),
+        "lbcg_get_populations": (C.c_int, [H, C.c_int32, C.c_void_p]),
+        "lbcg_set_populations": (C.c_int, [H, C.c_int32, C.c_void_p]),
+        "lbcg_get_fields": (C.c_int, [H, C.c_int32, C.c_void_p]),
+        "lbcg_state_bytes": (C.c_size_t, [H]),
+        "lbcg_upload_state": (C.c_int, [H, C.c_void_p, C.c_size_t]),
+        "lbcg_download_state": (C.c_int, [H, C.c_void_p, C.c_size_t]),
+        "lbcg_set_tile": (C.c_int, [H, C.c_int32]),
+        "lbcg_profile": (C.c_int, [H, C.c_int32]),
+        "lbcg_kernel_times": (C.c_int, [H, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+        "lbcg_launches_per_step": (C.c_int32, [H]),
+        "lbcg_total_nodes": (C.c_int64, [H]),
+        "lbcg_destroy": (C.c_int, [H]),
+        "lbcg_last_error": (C.c_char_p, []),
+    }
+    for name, (res, args) in sigs.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols() -> list:
+    return ["lbcg_create", "lbcg_create_batch", "lbcg_step", "lbcg_observables", "lbcg_get_populations",
+            "lbcg_set_populations", "lbcg_get_fields", "lbcg_state_bytes", "lbcg_upload_state",
+            "lbcg_download_state", "lbcg_set_tile", "lbcg_profile", "lbcg_kernel_times", "lbcg_launches_per_step", "lbcg_total_nodes", "lbcg_destroy",
+            "lbcg_last_error"]
+
+
+def _check(status: int):
+    if status != 0:
+        raise LBCGError(status, library().lbcg_last_error().decode())
+
+
+def _dptr(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _marshal(geoms: Sequence[Geometry], prms: Sequence[Params]):
+    keep = []
+    G = (lbcg_geometry * len(geoms))()
+    P = (lbcg_params * len(prms))()
+    for i, (g, p) in enumerate(zip(geoms, prms)):
+        solid = np.ascontiguousarray(g.solid, np.uint8)
+        rn = np.ascontiguousarray(g.rhoN0, np.float64)
+        nrm = None if g.normal is None else np.ascontiguousarray(g.normal, np.float64)
+        th = None if g.theta_node is None else np.ascontiguousarray(g.theta_node, np.float64)
+        keep += [solid, rn, nrm, th]
+        G[i] = lbcg_geometry(g.nx, g.ny, _BCX[g.bc_x], _BCY[g.bc_y], solid.ctypes.data_as(C.POINTER(C.c_uint8)),
+                             _dptr(rn), _dptr(nrm), _dptr(th))
+        P[i] = lbcg_params(p.nu_R, p.nu_B, p.sigma, p.theta, p.beta, p.s_e, p.s_eps, p.s_q, p.rho0, p.u_in,
+                           p.rho_out, p.grad_eps)
+    return G, P, keep
+
+
+# ---------------------------------------------------------------- functions with the C names
+def lbcg_create_batch(geoms: Sequence[Geometry], prms: Sequence[Params], precision: int = LBCG_FP32,
+                      stream: int = 0) -> int:
+    G, P, keep = _marshal(geoms, prms)
+    h = C.c_void_p()
+    _check(library().lbcg_create_batch(len(geoms), G, P, precision, C.c_void_p(stream or None), C.byref(h)))
+    return h.value
+
+
+def lbcg_create(geom: Geometry, prm: Params, precision: int = LBCG_FP32, stream: int = 0) -> int:
+    return lbcg_create_batch([geom], [prm], precision, stream)
+
+
+def lbcg_step(h: int, nsteps: int):
+    _check(library().lbcg_step(h, nsteps))
+
+
+def lbcg_observables(h: int, lattice: int = 0, spec: Optional[lbcg_obs_spec] = None, raise_on_diverged=True) -> dict:
+    spec = spec or obs_spec()
+    o = lbcg_obs()
+    st = library().lbcg_observables(h, lattice, C.byref(spec), C.byref(o))
+    if st != 0 and not (st == 5 and not raise_on_diverged):
+        _check(st)
+    d = {k: getattr(o, k) for k, _ in lbcg_obs._fields_ if k != "moments"}
+    d["moments"] = list(o.moments)
+    return d
+
+
+def lbcg_get_populations(h: int, lattice: int, nx: int, ny: int) -> np.ndarray:
+    out = np.empty((2, 9, ny, nx), np.float64)
+    _check(library().lbcg_get_populations(h, lattice, out.ctypes.data))
+    return out
+
+
+def lbcg_set_populations(h: int, lattice: int, f: np.ndarray):
+    f = np.ascontiguousarray(f, np.float64)
+    _check(library().lbcg_set_populations(h, lattice, f.ctypes.data))
+
+
+def lbcg_get_fields(h: int, lattice: int, nx: int, ny: int) -> np.ndarray:
+    out = np.empty((4, ny, nx), np.float64)
+    _check(library().lbcg_get_fields(h, lattice, out.ctypes.data))
+    return out
+
+
+def lbcg_state_bytes(h: int) -> int:
+    return int(library().lbcg_state_bytes(h))
+
+
+def lbcg_upload_state(h: int, ptr: int, nbytes: int):
+    _check(library().lbcg_upload_state(h, ptr, nbytes))
+
+
+def lbcg_download_state(h: int, ptr: int, nbytes: int):
+    _check(library().lbcg_download_state(h, ptr, nbytes))
+
+
+def lbcg_set_tile(h: int, ty: int):
+    _check(library().lbcg_set_tile(h, ty))
+
+
+def lbcg_profile(h: int, enable: bool):
+    _check(library().lbcg_profile(h, 1 if enable else 0))
+
+
+def lbcg_kernel_times(h: int):
+    """(ms of k_band, k_wall, k_step summed, number of profiled steps)."""
+    ms = (C.c_double * 3)()
+    n = C.c_int64()
+    _check(library().lbcg_kernel_times(h, ms, C.byref(n)))
+    return list(ms), n.value
+
+
+def lbcg_launches_per_step(h: int) -> int:
+    return int(library().lbcg_launches_per_step(h))
+
+
+def lbcg_total_nodes(h: int) -> int:
+    return int(library().lbcg_total_nodes(h))
+
+
+def lbcg_destroy(h: int):
+    _check(library().lbcg_destroy(h))
+
+
+def obs_spec(wall_y: float = 0.5, cyl=None, tip_rows=None, cl_rows=None, ny: Optional[int] = None) -> lbcg_obs_spec:
+    if tip_rows is None:
+        tip_rows = ((ny // 2 - 1, ny // 2) if ny % 2 == 0 else (ny // 2, ny // 2)) if ny else (-1, -1)
+    if cl_rows is None:
+        cl_rows = (1, ny - 2) if ny else (-1, -1)
+    cx, cy, cr = cyl if cyl is not None else (0.0, 0.0, 0.0)
+    return lbcg_obs_spec(wall_y, cx, cy, cr, tip_rows[0], tip_rows[1], cl_rows[0], cl_rows[1])
+
+
+class Lattice:
+    """One handle of liblbcg.so holding one or more lattices."""
+
+    def __init__(self, geoms, prms, precision="fp32", stream: int = 0):
+        if isinstance(geoms, Geometry):
+            geoms, prms = [geoms], [prms]
+        self.geoms = list(geoms)
+        self.prms = list(prms)
+        self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self.h = lbcg_create_batch(self.geoms, self.prms, self.precision, stream)
+
+    def step(self, n: int = 1):
+        lbcg_step(self.h, n)
+
+    def observables(self, lattice: int = 0, **kw) -> dict:
+        g = self.geoms[lattice]
+        return lbcg_observables(self.h, lattice, obs_spec(ny=g.ny, **kw))
+
+    def populations(self, lattice: int = 0) -> np.ndarray:
+        g = self.geoms[lattice]
+        return lbcg_get_populations(self.h, lattice, g.nx, g.ny)
+
+    def set_populations(self, f: np.ndarray, lattice: int = 0):
+        lbcg_set_populations(self.h, lattice, f)
+
+    def fields(self, lattice: int = 0) -> np.ndarray:
+        g = self.geoms[lattice]
+        return lbcg_get_fields(self.h, lattice, g.nx, g.ny)
+
+    def set_tile(self, ty: int):
+        lbcg_set_tile(self.h, ty)
+
+    @property
+    def state_bytes(self) -> int:
+        return lbcg_state_bytes(self.h)
+
+    @property
+    def launches_per_step(self) -> int:
+        return lbcg_launches_per_step(self.h)
+
+    @property
+    def total_nodes(self) -> int:
+        return lbcg_total_nodes(self.h)
+
+    def close(self):
+        if self.h:
+            lbcg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,202 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+FP64: every population after 100 steps within 1e-10 (max abs).
+FP32: one step from a common state within 2e-6, and 100 steps within 5e-5.
+Full-size capillary lattice (1200 x 80) in the benchmarked FP32 launch configuration:
+one GPU step checked against oracle steps on sampled windows of the same state.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import lbcg_oracle as O
+from oracle import observables as OB
+from paper_1707_00198_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__ as ge
+    ge.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+
+
+def oracle_run(g, p, n, fR=None, fB=None):
+    lat = O.make_lattice(g, p.theta)
+    if fR is None:
+        fR, fB = O.init_state(lat, g.rhoN0, p.rho0)
+    fR, fB = O.run(lat, p, fR, fB, n)
+    return lat, np.stack([fR.numpy(), fB.numpy()])
+
+
+def gpu_run(g, p, n, prec="fp64", ty=0, state=None):
+    from paper_1707_00198_gb300.lbcg import Lattice
+    L = Lattice(g, p, prec)
+    if ty:
+        L.set_tile(ty)
+    if state is not None:
+        L.set_populations(state)
+    L.step(n)
+    out = L.populations()
+    return L, out
+
+
+def _cases():
+    th = math.radians
+    yield "periodic_droplet_70x50", I.periodic_box_droplet(70, 50, R=12.0, xc=33.1, yc=24.6, noise=1e-3, seed=1), \
+        I.Params(sigma=0.02, nu_R=0.2, nu_B=0.05)
+    yield "flat_wall_100x50_cfg", *I.config_static_droplet()
+    g = I.flat_wall_droplet(77, 29, R=11.0, xc=30.2, noise=1e-3, seed=2, closed_x=True)
+    yield "closed_box_77x29", g, I.Params(theta=th(130), sigma=0.03, nu_R=0.1, nu_B=0.3)
+    g = I.cylinder_droplet(90, 80, Rs=16.0, cx=45.0, cy=28.0, Rd=14.0, theta=th(60), noise=1e-3, seed=3)
+    yield "cylinder_analytic_90x80", g, I.Params(theta=th(60), sigma=0.02)
+    g = I.cylinder_droplet(90, 80, Rs=16.0, cx=45.0, cy=28.0, Rd=14.0, theta=th(120), noise=1e-3, seed=4,
+                           analytic_normal=False)
+    yield "cylinder_e8_90x80", g, I.Params(theta=th(120), sigma=0.02)
+    g = I.capillary_filling(L=96, d=10, reservoir=30, wall=5, red_into=15, noise=1e-3, seed=5)
+    yield "capillary_156x20", g, I.Params(theta=th(30), sigma=0.02)
+    g = I.displacement_channel(W=20, L=110, x_I=25.0, seed=6, noise=1e-3)
+    yield "channel_inout_110x22", g, I.fingering_params(M=5.0, Ca=0.1, theta_deg=60.0)
+    g = I.flat_wall_droplet(45, 21, R=7.0, xc=20.7, noise=1e-3, seed=7)
+    rng = np.random.default_rng(7)
+    g.theta_node = rng.uniform(th(40), th(140), size=(g.ny, g.nx))
+    yield "per_node_theta_45x21", g, I.Params(sigma=0.02)
+    yield "tiny_periodic_7x6", I.periodic_box_droplet(7, 6, R=2.2, xc=3.3, yc=2.8, noise=1e-2, seed=8), \
+        I.Params(sigma=0.03)
+    yield "tiny_walls_5x5", I.flat_wall_droplet(5, 5, R=1.6, xc=2.2, noise=1e-2, seed=9), I.Params(sigma=0.03)
+
+
+CASES = list(_cases())
+
+
+@pytest.mark.parametrize("name,g,p", CASES, ids=[c[0] for c in CASES])
+def test_fp64_matches_oracle_after_100_steps(name, g, p):
+    lat, ref = oracle_run(g, p, 100)
+    L, got = gpu_run(g, p, 100)
+    L.close()
+    err = np.abs(got - ref).max()
+    assert err <= TOL64, f"{name}: max |df| = {err:.3e}"
+
+
+@pytest.mark.parametrize("ty", [4, 16])
+def test_fp64_parity_is_independent_of_the_tile_shape(ty):
+    g, p = I.config_static_droplet()
+    lat, ref = oracle_run(g, p, 40)
+    L, got = gpu_run(g, p, 40, ty=ty)
+    L.close()
+    assert np.abs(got - ref).max() <= TOL64
+
+
+def test_fp64_observables_match_oracle():
+    g, p = I.config_static_droplet()
+    lat, ref = oracle_run(g, p, 100)
+    L, got = gpu_run(g, p, 100)
+    fR = torch.from_numpy(ref[0])
+    fB = torch.from_numpy(ref[1])
+    o_ref = OB.observables(lat, p, fR, fB, wall_y=0.5)
+    o = L.observables(wall_y=0.5)
+    L.close()
+    for k in ("mass_R", "mass_B", "umax", "n_pts", "xc", "yc", "R", "theta_deg", "dp_laplace", "x_cl"):
+        assert abs(o[k] - o_ref[k]) <= 1e-9 * max(1.0, abs(o_ref[k])), (k, o[k], o_ref[k])
+    assert o["nonfinite"] == 0 and o["step"] == 100
+
+
+def test_fp64_fields_match_oracle():
+    g = I.displacement_channel(W=20, L=110, x_I=25.0, seed=6, noise=1e-3)
+    p = I.fingering_params(M=5.0, Ca=0.1, theta_deg=60.0)
+    lat, ref = oracle_run(g, p, 30)
+    L, _ = gpu_run(g, p, 30)
+    F = L.fields()
+    L.close()
+    mac = O.macroscopic(lat, p, torch.from_numpy(ref[0]), torch.from_numpy(ref[1]))
+    fl = lat.fluid.numpy()
+    for i, k in enumerate(("rho", "rhoN", "ux", "uy")):
+        assert np.abs(F[i][fl] - mac[k].numpy()[fl]).max() <= 1e-12, k
+
+
+def test_fp32_one_step_and_100_steps():
+    g, p = I.config_static_droplet()
+    lat, s50 = oracle_run(g, p, 50)
+    # one step from the oracle's state
+    _, ref1 = oracle_run(g, p, 1, torch.from_numpy(s50[0]), torch.from_numpy(s50[1]))
+    L, got1 = gpu_run(g, p, 1, prec="fp32", state=s50)
+    L.close()
+    assert np.abs(got1 - ref1).max() <= 2e-6
+    _, ref = oracle_run(g, p, 100)
+    L, got = gpu_run(g, p, 100, prec="fp32")
+    L.close()
+    assert np.abs(got - ref).max() <= 5e-5
+
+
+def test_batched_lattices_equal_their_single_runs():
+    th = math.radians
+    gs = [I.flat_wall_droplet(45, 21, R=7.0, xc=20.7, noise=1e-3, seed=1),
+          I.displacement_channel(W=20, L=110, x_I=25.0, seed=6, noise=1e-3),
+          I.periodic_box_droplet(33, 40, R=9.0, noise=1e-3, seed=2)]
+    ps = [I.Params(theta=th(70), sigma=0.02), I.fingering_params(5.0, 0.1, 60.0), I.Params(sigma=0.01, nu_B=0.05)]
+    from paper_1707_00198_gb300.lbcg import Lattice
+    for prec in ("fp64", "fp32"):
+        B = Lattice(gs, ps, prec)
+        B.step(37)
+        for i, (g, p) in enumerate(zip(gs, ps)):
+            S, single = gpu_run(g, p, 37, prec=prec)
+            S.close()
+            assert np.array_equal(B.populations(i), single), (prec, i)
+        B.close()
+
+
+def test_graph_replay_matches_direct_steps():
+    # 70 steps use two 32-step graph replays plus direct launches; 70 single calls use none
+    g, p = I.config_static_droplet()
+    from paper_1707_00198_gb300.lbcg import Lattice
+    A = Lattice(g, p, "fp32")
+    A.step(70)
+    Bl = Lattice(g, p, "fp32")
+    for _ in range(70):
+        Bl.step(1)
+    assert np.array_equal(A.populations(), Bl.populations())
+    A.close()
+    Bl.close()
+
+
+def test_full_size_capillary_fp32_sampled_windows():
+    # the 1200 x 80 capillary-filling lattice in the benchmarked configuration (FP32, default
+    # tile): after 300 steps take the state, make one more GPU step, and check it against
+    # oracle steps on windows around sampled nodes (margin 8 nodes, beyond the step's reach)
+    g, p = I.config_capillary()
+    from paper_1707_00198_gb300.lbcg import Lattice
+    L = Lattice(g, p, "fp32")
+    L.step(300)
+    s0 = L.populations()
+    L.step(1)
+    s1 = L.populations()
+    L.close()
+    rng = np.random.default_rng(0)
+    M = 8
+    H = 14
+    centres = [(200, 20), (999, 59), (300, 40), (1199, 0), (0, 79), (600, 21)]
+    centres += [(int(x), int(y)) for x, y in zip(rng.integers(0, g.nx, 6), rng.integers(0, g.ny, 6))]
+    worst = 0.0
+    for cx, cy in centres:
+        xs = [(cx + d) % g.nx for d in range(-H, H + 1)]
+        ys = [(cy + d) % g.ny for d in range(-H, H + 1)]
+        sub_solid = g.solid[np.ix_(ys, xs)]
+        if sub_solid.all():
+            continue
+        wg = I.Geometry(len(xs), len(ys), sub_solid, np.zeros((len(ys), len(xs))), bc_x="periodic", bc_y="periodic")
+        wlat = O.make_lattice(wg, p.theta)
+        fR = torch.from_numpy(s0[0][:, ys][:, :, xs].copy())
+        fB = torch.from_numpy(s0[1][:, ys][:, :, xs].copy())
+        oR, oB = O.step(wlat, p, fR, fB)
+        inner = (slice(None), slice(M, -M), slice(M, -M))
+        gR = s1[0][:, ys][:, :, xs]
+        gB = s1[1][:, ys][:, :, xs]
+        worst = max(worst, np.abs(gR[inner] - oR.numpy()[inner]).max(), np.abs(gB[inner] - oB.numpy()[inner]).max())
+    assert worst <= 2e-6, worst
