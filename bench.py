@@ -171,7 +171,7 @@ def cpu_oracle_rate(geoms, prms, budget_s: float = 15.0, max_steps: int = 100000
     from oracle import lbcg_oracle as O
     g, p = reference_sample(geoms, prms)
     lat = O.make_lattice(g, p.theta)
-    fR, fB = O.init_state(lat, g.rhoN0, p.rho0)
+    fR, fB = O.init_state(lat, g.rhoN0, p.rho0, p)
     nf = int((g.solid == 0).sum())
     t0 = time.perf_counter()
     fR, fB = O.run(lat, p, fR, fB, 2)
@@ -192,7 +192,7 @@ def run_reference(args):
     (geoms, prms), desc = workload(args.workload, seed=0)
     g, p = reference_sample(geoms, prms)
     lat = O.make_lattice(g, p.theta)
-    fR, fB = O.init_state(lat, g.rhoN0, p.rho0)
+    fR, fB = O.init_state(lat, g.rhoN0, p.rho0, p)
     nf = int((g.solid == 0).sum())
     fR, fB = O.run(lat, p, fR, fB, args.warmup)
     t0 = time.perf_counter()

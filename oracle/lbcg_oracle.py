@@ -204,14 +204,22 @@ def make_lattice(geom, theta: float | torch.Tensor) -> OracleLattice:
 
 
 # ------------------------------------------------------------------ initial state
-def init_state(lat: OracleLattice, rhoN0, rho0: float = 1.0):
+def init_state(lat: OracleLattice, rhoN0, rho0: float = 1.0, prm=None):
     """Rest equilibrium with the caller's colour field: f_{a,R} = w_a rho0 (1 + rho^N_0)/2,
-    f_{a,B} = w_a rho0 (1 - rho^N_0)/2 on fluid nodes, zero on solid nodes."""
+    f_{a,B} = w_a rho0 (1 - rho^N_0)/2 on fluid nodes, zero on solid nodes.
+
+    On an inlet/outlet lattice the Zou-He conditions of Sec. III.D constrain the
+    post-streaming populations of the open columns; the initial state is a post-streaming
+    state, so they are imposed on it too (``prm`` supplies u_in and rho_out)."""
     r = torch.as_tensor(np.asarray(rhoN0), dtype=DT)
     fl = lat.fluid.to(DT)
     w = torch.tensor(W, dtype=DT)[:, None, None]
     fR = w * rho0 * (1 + r) / 2 * fl
     fB = w * rho0 * (1 - r) / 2 * fl
+    if lat.inout:
+        if prm is None:
+            raise ValueError("an inlet/outlet lattice needs the parameters to set its initial state")
+        fR, fB = inlet_outlet(lat, prm, fR, fB)
     return fR, fB
 
 

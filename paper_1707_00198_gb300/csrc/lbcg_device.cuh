@@ -6,8 +6,10 @@
 //                 second one.  Direct storage (double, float): f_{a,R} then f_{a,B}.
 //                 Deviation storage (half, bfloat16): d_a = f_a - w_a rho0 then
 //                 g_a = f_{a,R} - f_{a,B} (an exact linear transform of the pair).
-//                 The stored state is post-collision, pre-streaming; streaming is folded
-//                 into the next step's loads (pull), bounce-back into the choice of address.
+//                 The stored state is the post-streaming state at each node: a step loads
+//                 a node's own 18 values and pushes its post-collision values to the
+//                 neighbours (half-way bounce-back: back into the node's own opposite slot;
+//                 across an open edge: dropped).
 //   node arrays : flags (uint8), and in the compute type T the rho^N of the wall band and
 //                 the corrected gradient / normal of the outermost fluid nodes.
 #pragma once
@@ -136,41 +138,25 @@ __device__ __forceinline__ int wrap_or_clamp(int v, int n, bool periodic) {
   return v < 0 ? 0 : (v >= n ? n - 1 : v);
 }
 
-// ------------------------------------------------------------------ pull with boundaries
-// Post-streaming populations of fluid node (x, y): f_a(x) = f''_a(x - e_a) if that node is
-// fluid, else the half-way bounce-back f''_{opp(a)}(x) (Eq. 15).  `solid_at(dx, dy)` tells
-// whether the node at offset (dx, dy) from (x, y) is solid; `xm[dx+1]`, `ym[dy+1]` are the
-// mapped coordinates of the neighbours.  On an inlet/outlet lattice the Zou-He conditions
-// replace the populations entering from outside (Sec. III.D).
-template <typename S, typename SolidFn>
-__device__ __forceinline__ void pull_node(const LatDev& L, const S* __restrict__ src, int x, const int xm[3],
-                                          const int ym[3], SolidFn solid_at,
+// ------------------------------------------------------------------ load with boundaries
+// Post-streaming populations of fluid node (x, y), stored at the node itself (streaming and
+// bounce-back happened in the previous step's push).  On an inlet/outlet lattice the Zou-He
+// conditions (Sec. III.D) replace the populations that enter from outside; applying them on
+// every read is idempotent, so a state that already satisfies them is unchanged.
+template <typename S>
+__device__ __forceinline__ void load_node(const LatDev& L, const S* __restrict__ src, long long k, int x,
                                           typename Store<S>::T fr[9], typename Store<S>::T fb[9]) {
   using T = typename Store<S>::T;
-  const S* base = src + L.pop_off;
+  const S* base = src + L.pop_off + k;
   const T r0 = T(L.rho0);
-  const bool inlet = (L.bcx == BC_INOUT) && (x == 0);
-  const bool outlet = (L.bcx == BC_INOUT) && (x == L.nx - 1);
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
-    const bool entering = (inlet && ex(a) == 1) || (outlet && ex(a) == -1);
-    T lo = T(0), hi = T(0);
-    if (!entering) {
-      long long idx;
-      int p;
-      if (a != 0 && solid_at(-ex(a), -ey(a))) {
-        p = opp(a);
-        idx = (long long)ym[1] * L.pitch + xm[1];
-      } else {
-        p = a;
-        idx = (long long)ym[1 - ey(a)] * L.pitch + xm[1 - ex(a)];
-      }
-      lo = Store<S>::ld(base + (long long)p * L.plane + idx);
-      hi = Store<S>::ld(base + (long long)(9 + p) * L.plane + idx);
-    }
+    const T lo = Store<S>::ld(base + (long long)a * L.plane);
+    const T hi = Store<S>::ld(base + (long long)(9 + a) * L.plane);
     decode<S, T>(lo, hi, wgt<T>(a) * r0, fr[a], fb[a]);
   }
-  if (inlet) {
+  if (L.bcx != BC_INOUT) return;
+  if (x == 0) {
     // Zou-He velocity inlet: u = (u_in, 0), unknown f1, f5, f8; the node carries red only
     T f[9];
 #pragma unroll
@@ -185,7 +171,7 @@ __device__ __forceinline__ void pull_node(const LatDev& L, const S* __restrict__
       fr[a] = f[a];
       fb[a] = T(0);
     }
-  } else if (outlet) {
+  } else if (x == L.nx - 1) {
     // Zou-He pressure outlet: rho = rho_out, u_y = 0, unknown f3, f6, f7, which take the
     // colour fraction of the known populations
     T f[9];

@@ -1,16 +1,17 @@
 // Kernels of one time step of the colour-gradient LBM with the improved wetting scheme
 // (arXiv 1707.00198, Sec. II).  Per step, in stream order:
 //   k_band  : rho^N (Eq. 12, 16) on the wall band = outermost fluid nodes and their fluid
-//             neighbours, from the pulled post-streaming populations;
+//             neighbours, from the post-streaming populations stored at each node;
 //   k_wall  : on every outermost fluid node the gradient of Eq. 28 with the virtual values
 //             of Eq. 29 and the contact-angle correction of Eq. 30-36 -> corrected gradient
 //             and unit normal, kept in two small node arrays;
-//   k_step  : the fused bulk step over 32 x TY tiles: pull (streaming + bounce-back folded
-//             into the loads) -> rho^N on the tile plus a 2-node halo (shared memory) ->
+//   k_step  : the fused bulk step over 32 x TY tiles: loads of each node's own populations
+//             -> rho^N on the tile plus a 2-node halo (shared memory) ->
 //             n on the tile plus a 1-node halo (outermost-fluid values from k_wall, virtual
 //             n on outermost solid nodes, Eq. 29) -> grad n, kappa, F (Eq. 10, 13, 28) ->
 //             u, nu, MRT collision with Guo forcing (Eq. 1-9, 17, 18) -> recolouring
-//             (Eq. 14) -> store of the post-collision populations at the node.
+//             (Eq. 14) -> push of the post-collision populations to the neighbours
+//             (streaming, Eq. 15) with half-way bounce-back at solid neighbours.
 #include "lbcg_device.cuh"
 #include "lbcg_internal.h"
 
@@ -31,7 +32,7 @@ struct StepArgs {
 // ------------------------------------------------------------------ k_band
 template <typename S>
 __global__ void __launch_bounds__(256) k_band(const LatDev* __restrict__ lats, const int4* __restrict__ list,
-                                              int n, const S* __restrict__ src, const uint8_t* __restrict__ flags,
+                                              int n, const S* __restrict__ src,
                                               typename Store<S>::T* __restrict__ band_rn) {
   using T = typename Store<S>::T;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -39,17 +40,8 @@ __global__ void __launch_bounds__(256) k_band(const LatDev* __restrict__ lats, c
   const int4 e = list[i];
   const LatDev& L = lats[e.x];
   const int x = e.y, y = e.z;
-  const bool px = L.bcx == BC_PERIODIC, py = L.bcy == BC_PERIODIC;
-  int xm[3], ym[3];
-#pragma unroll
-  for (int d = -1; d <= 1; ++d) {
-    xm[d + 1] = wrap_or_clamp(x + d, L.nx, px);
-    ym[d + 1] = wrap_or_clamp(y + d, L.ny, py);
-  }
-  const uint8_t* fl = flags + L.node_off;
-  auto solid_at = [&](int dx, int dy) { return (fl[(long long)ym[dy + 1] * L.pitch + xm[dx + 1]] & F_SOLID) != 0; };
   T fr[9], fb[9], rR, rB;
-  pull_node<S>(L, src, x, xm, ym, solid_at, fr, fb);
+  load_node<S>(L, src, (long long)y * L.pitch + x, x, fr, fb);
   band_rn[L.node_off + (long long)y * L.pitch + x] = colour_indicator(fr, fb, rR, rB);
 }
 
@@ -175,10 +167,7 @@ __global__ void __launch_bounds__(32 * TY) k_step(StepArgs A) {
   {
     const int c3x = lx + 3, c3y = ly + 3;
     if (fluid) {
-      const int xm[3] = {sxm[c3x - 1], sxm[c3x], sxm[c3x + 1]};
-      const int ym[3] = {sym[c3y - 1], sym[c3y], sym[c3y + 1]};
-      auto solid_at = [&](int dx, int dy) { return (sfl[(c3y + dy) * W3 + c3x + dx] & F_SOLID) != 0; };
-      pull_node<S>(L, src, sxm[c3x], xm, ym, solid_at, fr, fb);
+      load_node<S>(L, src, (long long)sym[c3y] * pitch + sxm[c3x], sxm[c3x], fr, fb);
       rn = colour_indicator(fr, fb, rhoR, rhoB);
     } else {
 #pragma unroll
@@ -192,11 +181,8 @@ __global__ void __launch_bounds__(32 * TY) k_step(StepArgs A) {
     const int c3x = cx + 1, c3y = cy + 1;
     T v = T(0);
     if (!(sfl[c3y * W3 + c3x] & F_SOLID)) {
-      const int xm[3] = {sxm[c3x - 1], sxm[c3x], sxm[c3x + 1]};
-      const int ym[3] = {sym[c3y - 1], sym[c3y], sym[c3y + 1]};
-      auto solid_at = [&](int dx, int dy) { return (sfl[(c3y + dy) * W3 + c3x + dx] & F_SOLID) != 0; };
       T hr[9], hb[9], a1, a2;
-      pull_node<S>(L, src, sxm[c3x], xm, ym, solid_at, hr, hb);
+      load_node<S>(L, src, (long long)sym[c3y] * pitch + sxm[c3x], sxm[c3x], hr, hb);
       v = colour_indicator(hr, hb, a1, a2);
     }
     srn[i] = v;
@@ -357,8 +343,9 @@ __global__ void __launch_bounds__(32 * TY) k_step(StepArgs A) {
     // recolouring (Eq. 14; the blue line with the minus sign)
     const T cR = rhoR / rho, cB = rhoB / rho;
     const T pc = T(L.beta) * rhoR * rhoB / rho;
-    S* __restrict__ dst = static_cast<S*>(A.dst) + L.pop_off + kn;
+    S* __restrict__ dst = static_cast<S*>(A.dst) + L.pop_off;
     const T r0 = T(L.rho0);
+    const int c3x = lx + 3, c3y = ly + 3;
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
       const T en = T(ex(a)) * nxo + T(ey(a)) * nyo;
@@ -366,9 +353,27 @@ __global__ void __launch_bounds__(32 * TY) k_step(StepArgs A) {
       const T oR = cR * fp[a] + pert;
       const T oB = cB * fp[a] - pert;
       T lo, hi;
+      // streaming (Eq. 15): to x + e_a if that node is fluid; half-way bounce-back into the
+      // opposite slot of this node if it is solid; dropped if it lies beyond an open edge
+      long long k;
+      int slot;
+      if (a == 0) {
+        k = kn;
+        slot = 0;
+      } else {
+        const int xr = xs + ex(a), yr = ys + ey(a);
+        if ((!px && (xr < 0 || xr >= nx)) || (!py && (yr < 0 || yr >= ny))) continue;
+        if (sfl[(c3y + ey(a)) * W3 + c3x + ex(a)] & F_SOLID) {
+          k = kn;
+          slot = opp(a);
+        } else {
+          k = (long long)sym[c3y + ey(a)] * pitch + sxm[c3x + ex(a)];
+          slot = a;
+        }
+      }
       encode<S, T>(oR, oB, wgt<T>(a) * r0, lo, hi);
-      dst[(long long)a * L.plane] = Store<S>::cv(lo);
-      dst[(long long)(9 + a) * L.plane] = Store<S>::cv(hi);
+      dst[(long long)slot * L.plane + k] = Store<S>::cv(lo);
+      dst[(long long)(9 + slot) * L.plane + k] = Store<S>::cv(hi);
     }
   }
 }
@@ -396,6 +401,7 @@ __global__ void k_to_storage(const LatDev* __restrict__ lats, int lat, const dou
   pool[L.pop_off + (long long)(9 + a) * L.plane + k] = Store<S>::cv(hi);
 }
 
+// host layout out <- the post-streaming state as a step reads it (Zou-He applied on open edges)
 template <typename S>
 __global__ void k_from_storage(const LatDev* __restrict__ lats, int lat, const S* __restrict__ pool,
                                const uint8_t* __restrict__ flags, double* __restrict__ out) {
@@ -403,20 +409,21 @@ __global__ void k_from_storage(const LatDev* __restrict__ lats, int lat, const S
   const LatDev& L = lats[lat];
   const long long nn = (long long)L.nx * L.ny;
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= 9 * nn) return;
-  const int a = int(i / nn);
-  const long long r = i % nn;
-  const int y = int(r / L.nx), x = int(r % L.nx);
+  if (i >= nn) return;
+  const int y = int(i / L.nx), x = int(i % L.nx);
   const long long k = (long long)y * L.pitch + x;
-  const bool solid = flags[L.node_off + k] & F_SOLID;
-  T fr = T(0), fb = T(0);
-  if (!solid) {
-    const T lo = Store<S>::ld(pool + L.pop_off + (long long)a * L.plane + k);
-    const T hi = Store<S>::ld(pool + L.pop_off + (long long)(9 + a) * L.plane + k);
-    decode<S, T>(lo, hi, wgt<T>(a) * T(L.rho0), fr, fb);
+  T fr[9], fb[9];
+  if (flags[L.node_off + k] & F_SOLID) {
+#pragma unroll
+    for (int a = 0; a < 9; ++a) fr[a] = fb[a] = T(0);
+  } else {
+    load_node<S>(L, pool, k, x, fr, fb);
   }
-  out[i] = double(fr);
-  out[9 * nn + i] = double(fb);
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    out[a * nn + i] = double(fr[a]);
+    out[(9 + a) * nn + i] = double(fb[a]);
+  }
 }
 
 // ------------------------------------------------------------------ launchers
@@ -429,7 +436,7 @@ static cudaError_t launch_all(const LaunchStep& p, cudaStream_t st) {
   rec(0);
   if (p.nband > 0) {
     k_band<S><<<(p.nband + 255) / 256, 256, 0, st>>>(p.lats, p.band, p.nband, static_cast<const S*>(p.src),
-                                                     p.flags, static_cast<T*>(p.band_rn));
+                                                     static_cast<T*>(p.band_rn));
   }
   rec(1);
   rec(2);
@@ -490,7 +497,7 @@ cudaError_t launch_to_storage(int prec, const LatDev* lats, int lat, long long n
 
 cudaError_t launch_from_storage(int prec, const LatDev* lats, int lat, long long nn, const void* pool,
                                 const uint8_t* flags, double* out, cudaStream_t st) {
-  const long long n = 9 * nn;
+  const long long n = nn;
   const int blocks = int((n + 255) / 256);
   switch (prec) {
     case 0: k_from_storage<double><<<blocks, 256, 0, st>>>(lats, lat, static_cast<const double*>(pool), flags, out); break;

@@ -31,7 +31,7 @@ def _built():
 def oracle_run(g, p, n, fR=None, fB=None):
     lat = O.make_lattice(g, p.theta)
     if fR is None:
-        fR, fB = O.init_state(lat, g.rhoN0, p.rho0)
+        fR, fB = O.init_state(lat, g.rhoN0, p.rho0, p)
     fR, fB = O.run(lat, p, fR, fB, n)
     return lat, np.stack([fR.numpy(), fB.numpy()])
 

@@ -13,7 +13,7 @@ from paper_1707_00198_gb300 import inputs as I
 
 def _state(geom, prm):
     lat = O.make_lattice(geom, prm.theta)
-    fR, fB = O.init_state(lat, geom.rhoN0, prm.rho0)
+    fR, fB = O.init_state(lat, geom.rhoN0, prm.rho0, prm)
     return lat, fR, fB
 
 

@@ -47,7 +47,7 @@ def test_laplace_law_for_a_free_droplet():
         g = I.periodic_box_droplet(40, 40, R=R)
         p = I.Params(sigma=0.01)
         lat = O.make_lattice(g, p.theta)
-        fR, fB = O.init_state(lat, g.rhoN0)
+        fR, fB = O.init_state(lat, g.rhoN0, p.rho0, p)
         fR, fB = O.run(lat, p, fR, fB, 300)
         dps, Rs = [], []
         for _ in range(40):
@@ -69,7 +69,7 @@ def test_static_contact_angle_on_a_flat_wall(theta_deg):
     g = I.flat_wall_droplet(64, 32, R=R, yc=0.5 - R * math.cos(th), noise=1e-3, seed=0)
     p = I.Params(sigma=1e-2, theta=th)
     lat = O.make_lattice(g, p.theta)
-    fR, fB = O.init_state(lat, g.rhoN0)
+    fR, fB = O.init_state(lat, g.rhoN0, p.rho0, p)
     fR, fB = O.run(lat, p, fR, fB, 1000)
     o = OB.observables(lat, p, fR, fB, wall_y=0.5)
     assert abs(o["theta_deg"] - theta_deg) < 3.0, o["theta_deg"]
@@ -84,7 +84,7 @@ def test_capillary_filling_follows_lucas_washburn():
     g = I.capillary_filling(L=L, d=d, reservoir=30, wall=4, red_into=20)
     p = I.Params(sigma=0.05, theta=math.radians(30))
     lat = O.make_lattice(g, p.theta)
-    fR, fB = O.init_state(lat, g.rhoN0)
+    fR, fB = O.init_state(lat, g.rhoN0, p.rho0, p)
     fR, fB = O.run(lat, p, fR, fB, 1000)
     ts, xs = [], []
     for k in range(5):
