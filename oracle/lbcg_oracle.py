@@ -136,7 +136,7 @@ class OracleLattice:
 def solid_normal_e8(solid: torch.Tensor, omega_fb: torch.Tensor, bc_x: str, bc_y: str) -> torch.Tensor:
     """Eq. 32-33: n_s = sum_k w(|c_k|^2) s(x + c_k) c_k / |...| at Omega_Fb nodes.
 
-    The weights of Eq. 33 are k/5040 with integer k (240, 112, 84, 16, 1); the common factor
+    The weights of Eq. 33 are k/5040 with integer k (960, 448, 84, 32, 1); the common factor
     cancels in the normalisation, so the sum is taken over the integers k, which is exact.
     Flat walls then give exactly axis-aligned normals, so the tie D1 == D2 of Eq. 36 is an
     exact tie rather than a rounding accident."""

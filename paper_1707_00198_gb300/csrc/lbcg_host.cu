@@ -182,7 +182,8 @@ void classify(const lbcg_geometry* g, const lbcg_params* p, int lat, std::vector
   for (int y = 0; y < ny; ++y)
     for (int x = 0; x < nx; ++x)
       if (inband[(size_t)y * nx + x]) band.push_back(make_int4(lat, x, y, 0));
-  // E8 stencil (Eq. 33): the weights are k/5040 with integer k, summed exactly as integers
+  // E8 stencil (Eq. 33): the weights are k/5040 with integer k = 960, 448, 84, 32, 1 for
+  // |c|^2 = 1, 2, 4, 5, 8; the sums are taken exactly over the integers k
   struct C8 {
     int cx, cy, k;
   };
@@ -190,7 +191,7 @@ void classify(const lbcg_geometry* g, const lbcg_params* p, int lat, std::vector
   for (int cy = -2; cy <= 2; ++cy)
     for (int cx = -2; cx <= 2; ++cx) {
       const int c2 = cx * cx + cy * cy;
-      const int k = c2 == 1 ? 240 : c2 == 2 ? 112 : c2 == 4 ? 84 : c2 == 5 ? 16 : c2 == 8 ? 1 : 0;
+      const int k = c2 == 1 ? 960 : c2 == 2 ? 448 : c2 == 4 ? 84 : c2 == 5 ? 32 : c2 == 8 ? 1 : 0;
       if (k) st.push_back({cx, cy, k});
     }
   auto s_e8 = [&](int x, int y) -> int {

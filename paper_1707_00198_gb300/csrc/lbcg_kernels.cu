@@ -207,7 +207,12 @@ __global__ void __launch_bounds__(32 * TY) k_step(StepArgs A) {
       cy = j / W1;
       if (cx >= 1 && cx < TX + 1 && cy >= 1 && cy < TY + 1) continue;
     }
-    const int c3x = cx + 2, c3y = cy + 2;
+    // A slot beyond a non-periodic edge is a ghost copy of the edge node (zero normal
+    // gradient): evaluate it at the slot of the node it copies, whose stencil stays inside
+    // the halo.  Periodic slots already hold their wrapped node with its own neighbours.
+    const int sx = px ? cx : min(max(cx + sxm[cx + 2] - (x0 + cx - 1), 0), W1 - 1);
+    const int sy = py ? cy : min(max(cy + sym[cy + 2] - (y0 + cy - 1), 0), H1 - 1);
+    const int c3x = sx + 2, c3y = sy + 2;
     const uint8_t f = sfl[c3y * W3 + c3x];
     const long long k = L.node_off + (long long)sym[c3y] * pitch + sxm[c3x];
     T ax = T(0), ay = T(0), nxv = T(0), nyv = T(0);
@@ -218,7 +223,7 @@ __global__ void __launch_bounds__(32 * TY) k_step(StepArgs A) {
         nxv = wall[2 * NTOT + k];
         nyv = wall[3 * NTOT + k];
       } else {
-        const int c2x = cx + 1, c2y = cy + 1;
+        const int c2x = sx + 1, c2y = sy + 1;
 #pragma unroll
         for (int a = 1; a < 9; ++a) {
           const T t = wgt<T>(a) * srn[(c2y + ey(a)) * W2 + c2x + ex(a)];
@@ -236,18 +241,20 @@ __global__ void __launch_bounds__(32 * TY) k_step(StepArgs A) {
     } else if (f & F_OSOLID) {
       // virtual n on the outermost solid node (Eq. 29); its fluid neighbours are outermost
       // fluid nodes, whose n k_wall has stored
-      T sx = T(0), sy = T(0), den = T(0);
+      T vx = T(0), vy = T(0), den = T(0);
 #pragma unroll
       for (int b = 1; b < 9; ++b) {
         if (!(sfl[(c3y + ey(b)) * W3 + c3x + ex(b)] & F_SOLID)) {
           const long long k2 = L.node_off + (long long)sym[c3y + ey(b)] * pitch + sxm[c3x + ex(b)];
-          sx += wgt<T>(b) * wall[2 * NTOT + k2];
-          sy += wgt<T>(b) * wall[3 * NTOT + k2];
+          vx += wgt<T>(b) * wall[2 * NTOT + k2];
+          vy += wgt<T>(b) * wall[3 * NTOT + k2];
           den += wgt<T>(b);
         }
       }
-      nxv = sx / den;
-      nyv = sy / den;
+      if (den > T(0)) {
+        nxv = vx / den;
+        nyv = vy / den;
+      }
     }
     snx[cy * W1 + cx] = nxv;
     sny[cy * W1 + cx] = nyv;
