@@ -177,6 +177,34 @@ int64_t lbcg_total_nodes(const lbcg_handle* h);
 
 lbcg_status lbcg_destroy(lbcg_handle* h);
 
+/* Observable sums without any device allocation.  The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc -- code that runs under a fixed
+ * device-memory budget or a custom allocator that forbids new allocations, or a thread that
+ * must not take the driver's allocation locks -- and that hold the macroscopic fields of a
+ * lattice in their own device buffers.  It performs the same reduction lbcg_observables
+ * performs internally, with the per-block partial sums kept in a file-scope device array of
+ * 304 x 17 doubles (41,344 bytes) that every GPU loading the library holds until exit.
+ *
+ *   fields : DEVICE pointer, double [4][ny][nx]: rho_R, rho_B, u_x, u_y (caller-owned);
+ *   mask   : DEVICE pointer, uint8 [ny][nx]: LBCG_MASK_SOLID marks solid nodes (skipped),
+ *            LBCG_MASK_NO_FIT marks nodes whose links give no interface point (caller-owned);
+ *   nx, ny : 1 <= nx*ny <= LBCG_NOALLOC_MAX_NODES, else LBCG_E_ARG with a message;
+ *   stream : cudaStream_t the two kernels are enqueued on (asynchronous, no synchronisation);
+ *   out    : DEVICE pointer to 17 doubles (caller-owned): mass_R, mass_B, |u|max, the nine
+ *            interface moments (as lbcg_obs.moments), sum and count of rho/3 over
+ *            rho^N > 0.9, sum and count over rho^N < -0.9, non-finite flag.
+ *
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress,
+ * with that device current); make that first call before any stream capture.  All calls on
+ * a device share the array; calls whose kernels overlap on the GPU race and must be
+ * serialised by the caller.  Each call overwrites every partial before reading it, so no
+ * state carries over between calls.  Errors are reported through lbcg_last_error(). */
+#define LBCG_MASK_SOLID 1
+#define LBCG_MASK_NO_FIT 8
+#define LBCG_NOALLOC_MAX_NODES 2147483647LL
+lbcg_status lbcg_field_moments_noalloc(const double* fields, const uint8_t* mask, int32_t nx, int32_t ny,
+                                       void* stream, double* out);
+
 /* Message of the last error on the calling thread ("" if none). */
 const char* lbcg_last_error(void);
 

@@ -322,6 +322,8 @@ lbcg_status run_macro(lbcg_handle* h, int lat) {
 
 }  // namespace
 
+void lbcg::set_last_error(const char* msg) { g_err = msg; }
+
 extern "C" {
 
 const char* lbcg_last_error(void) { return g_err.c_str(); }

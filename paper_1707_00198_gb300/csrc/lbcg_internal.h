@@ -46,4 +46,7 @@ cudaError_t launch_observables(const LatDev* lats, int lat, int nx, int ny, cons
                                long long node_total, const uint8_t* flags, int tip0, int tip1, int cl0, int cl1,
                                double* partials, double* out, cudaStream_t st);
 
+// Sets the calling thread's message returned by lbcg_last_error() (lbcg_host.cu).
+void set_last_error(const char* msg);
+
 }  // namespace lbcg

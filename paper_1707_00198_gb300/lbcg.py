@@ -89,6 +89,8 @@ def library():
         "lbcg_total_nodes": (C.c_int64, [H]),
         "lbcg_destroy": (C.c_int, [H]),
         "lbcg_last_error": (C.c_char_p, []),
+        "lbcg_field_moments_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
+                                                 C.c_void_p]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -102,7 +104,7 @@ def exported_symbols() -> list:
     return ["lbcg_create", "lbcg_create_batch", "lbcg_step", "lbcg_observables", "lbcg_get_populations",
             "lbcg_set_populations", "lbcg_get_fields", "lbcg_state_bytes", "lbcg_upload_state",
             "lbcg_download_state", "lbcg_set_tile", "lbcg_profile", "lbcg_kernel_times", "lbcg_launches_per_step", "lbcg_total_nodes", "lbcg_destroy",
-            "lbcg_last_error"]
+            "lbcg_last_error", "lbcg_field_moments_noalloc"]
 
 
 def _check(status: int):
@@ -214,6 +216,15 @@ def lbcg_total_nodes(h: int) -> int:
 
 def lbcg_destroy(h: int):
     _check(library().lbcg_destroy(h))
+
+
+LBCG_MASK_SOLID = 1
+LBCG_MASK_NO_FIT = 8
+
+
+def lbcg_field_moments_noalloc(fields_ptr: int, mask_ptr: int, nx: int, ny: int, stream: int, out_ptr: int):
+    """Device pointers in, device pointer out (17 doubles); allocates nothing."""
+    _check(library().lbcg_field_moments_noalloc(fields_ptr, mask_ptr, nx, ny, C.c_void_p(stream or None), out_ptr))
 
 
 def obs_spec(wall_y: float = 0.5, cyl=None, tip_rows=None, cl_rows=None, ny: Optional[int] = None) -> lbcg_obs_spec:
