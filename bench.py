@@ -41,9 +41,10 @@ DTYPE = {"fp64": "f64", "fp32": "f32", "fp16": "f16-store/f32-math", "bf16": "bf
 
 
 # ----------------------------------------------------------------------------- workloads
-def workload(name: str, seed: int = 0):
+def workload(name: str, seed: int = 0, lattices: int = 64):
     if name == "batched_sweep":
-        return I.channel_sweep(64, seed=seed), "64 displacement channels, W~U{40..200}, L=10W, (M,Ca,theta) grids"
+        return I.channel_sweep(lattices, seed=seed), \
+            f"{lattices} displacement channels, W~U{{40..200}}, L=10W, (M,Ca,theta) grids"
     if name == "capillary":
         g, p = I.config_capillary()
         return ([g], [p]), "capillary filling 1200x80, d=40, L=800, theta=30deg, sigma=1e-2"
@@ -189,7 +190,7 @@ def run_reference(args):
     if rank != 0:
         return
     from oracle import lbcg_oracle as O
-    (geoms, prms), desc = workload(args.workload, seed=0)
+    (geoms, prms), desc = workload(args.workload, seed=0, lattices=args.lattices)
     g, p = reference_sample(geoms, prms)
     lat = O.make_lattice(g, p.theta)
     fR, fB = O.init_state(lat, g.rhoN0, p.rho0, p)
@@ -233,9 +234,11 @@ def timed_steps(lat, stream, K, flush_buf):
     return sum(a.elapsed_time(b) for a, b in evs)
 
 
-def measure_form(geoms, prms, precision, K, W, stream, with_profile=False):
+def measure_form(geoms, prms, precision, K, W, stream, with_profile=False, ty=0):
     from paper_1707_00198_gb300 import lbcg
     lat = lbcg.Lattice(geoms, prms, precision, stream=stream.cuda_stream)
+    if ty:
+        lat.set_tile(ty)
     lat.step(W)
     torch.cuda.synchronize()
     flush = None
@@ -261,7 +264,7 @@ def run_ours(args):
     ge.build()
     from paper_1707_00198_gb300 import lbcg
 
-    (geoms, prms), desc = workload(args.workload, seed=rank)
+    (geoms, prms), desc = workload(args.workload, seed=rank, lattices=args.lattices)
     nf = fluid_nodes(geoms)
     nodes = sum(g.nx * g.ny for g in geoms)
     stream = torch.cuda.Stream()
@@ -270,6 +273,8 @@ def run_ours(args):
     # ---- timed region: K steps of the whole batch, kernels timed with events on the stream
     clocks = Clocks(local)
     lat = lbcg.Lattice(geoms, prms, args.precision, stream=stream.cuda_stream)
+    if args.ty:
+        lat.set_tile(args.ty)
     lat.step(args.warmup)
     torch.cuda.synchronize()
     flush = torch.zeros(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda") if lat.state_bytes < 2 * L2_BYTES \
@@ -302,7 +307,7 @@ def run_ours(args):
     achieved = alg_bytes / (step_ms / 1e3) / 1e9
     peaks = measured_peaks()
     peak, peak_src = (peaks["hbm_gbs"], "measured") if peaks and "hbm_gbs" in peaks else (6800.0, "fallback")
-    traffic = recorded_traffic(f"k_step<{args.precision},ty8>", nf)
+    traffic = recorded_traffic(f"k_step<{args.precision},ty{args.ty or 8}>", nf)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "kernel": "k_step", "peak_source": peak_src,
             "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": step_ms,
@@ -335,7 +340,7 @@ def run_ours(args):
                 forms[prec] = {"MLUPS": value / ws, "hbm_gbs_alg": whole_gbs}
                 continue
             Kf = max(10, args.steps // 4)
-            L2, msf, _, _ = measure_form(geoms, prms, prec, Kf, args.warmup, stream)
+            L2, msf, _, _ = measure_form(geoms, prms, prec, Kf, args.warmup, stream, ty=args.ty)
             L2.close()
             forms[prec] = {"MLUPS": nf * Kf / (msf / 1e3) / 1e6,
                            "hbm_gbs_alg": 36 * STORE_BYTES[prec] * nf * Kf / (msf / 1e3) / 1e9}
@@ -352,6 +357,7 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
                 "config": {"workload": args.workload, "description": desc, "lattices": len(geoms), "nodes": nodes,
+                           "tile": f"32x{args.ty or 8}",
                            "fluid_nodes_per_gpu": nf, "precision": args.precision,
                            "state_bytes": sb, "l2": "flushed before every timed step" if flush is not None
                            else "inputs larger than L2", "mlups_counts": "fluid-node updates"},
@@ -372,6 +378,8 @@ def main():
     ap.add_argument("--workload", default="batched_sweep",
                     choices=("batched_sweep", "capillary", "fingering", "static_droplet", "roofline_box"))
     ap.add_argument("--precision", default="fp32", choices=("fp64", "fp32", "fp16", "bf16"))
+    ap.add_argument("--lattices", type=int, default=64, help="channels of the batched sweep")
+    ap.add_argument("--ty", type=int, default=0, help="tile height of k_step (4, 8, 16; 0 = default)")
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
