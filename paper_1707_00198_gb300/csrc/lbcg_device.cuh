@@ -38,6 +38,7 @@ struct LatDev {
   long long plane;     // elements per plane (pitch * ny)
   long long node_off;  // element offset of node (0,0) in the node arrays
   double nu_R, nu_B, sigma, beta, s_e, s_eps, s_q, rho0, u_in, rho_out, grad_eps;
+  double h_inv_nuR, h_inv_nuB;  // 1/(2 nu_R), 1/(2 nu_B): the two weights of Eq. 18
 };
 
 // Entry of the outermost-fluid list: node, its solid normal and contact angle.
@@ -143,26 +144,24 @@ __device__ __forceinline__ int wrap_or_clamp(int v, int n, bool periodic) {
 // bounce-back happened in the previous step's push).  On an inlet/outlet lattice the Zou-He
 // conditions (Sec. III.D) replace the populations that enter from outside; applying them on
 // every read is idempotent, so a state that already satisfies them is unchanged.
-template <typename S>
-__device__ __forceinline__ void load_node(const LatDev& L, const S* __restrict__ src, long long k, int x,
-                                          typename Store<S>::T fr[9], typename Store<S>::T fb[9]) {
-  using T = typename Store<S>::T;
-  const S* base = src + L.pop_off + k;
-  const T r0 = T(L.rho0);
-#pragma unroll
-  for (int a = 0; a < 9; ++a) {
-    const T lo = Store<S>::ld(base + (long long)a * L.plane);
-    const T hi = Store<S>::ld(base + (long long)(9 + a) * L.plane);
-    decode<S, T>(lo, hi, wgt<T>(a) * r0, fr[a], fb[a]);
-  }
-  if (L.bcx != BC_INOUT) return;
+// Zou-He conditions (Sec. III.D) on the populations of a node in column x of an
+// inlet/outlet lattice: velocity inlet (u_in, 0) carrying red only at x = 0 (unknown f1, f5,
+// f8), pressure outlet rho_out at x = nx-1 (unknown f3, f6, f7, which take the colour
+// fraction of the known populations).  Applying them again to a state that already satisfies
+// them changes nothing.
+template <typename T>
+__device__ __forceinline__ T zh_div(T a, T b) {
+  if constexpr (sizeof(T) == 4) return __fdividef(a, b);
+  else return a / b;
+}
+template <typename T>
+__device__ __forceinline__ void zou_he(int x, int nx, T u_in, T rho_out, T fr[9], T fb[9]) {
   if (x == 0) {
-    // Zou-He velocity inlet: u = (u_in, 0), unknown f1, f5, f8; the node carries red only
     T f[9];
 #pragma unroll
     for (int a = 0; a < 9; ++a) f[a] = fr[a] + fb[a];
-    const T u = T(L.u_in);
-    const T rho = (f[0] + f[2] + f[4] + T(2) * (f[3] + f[6] + f[7])) / (T(1) - u);
+    const T u = u_in;
+    const T rho = zh_div(f[0] + f[2] + f[4] + T(2) * (f[3] + f[6] + f[7]), T(1) - u);
     f[1] = f[3] + T(2.0 / 3.0) * rho * u;
     f[5] = f[7] - T(0.5) * (f[2] - f[4]) + rho * u / T(6);
     f[8] = f[6] + T(0.5) * (f[2] - f[4]) + rho * u / T(6);
@@ -171,20 +170,18 @@ __device__ __forceinline__ void load_node(const LatDev& L, const S* __restrict__
       fr[a] = f[a];
       fb[a] = T(0);
     }
-  } else if (x == L.nx - 1) {
-    // Zou-He pressure outlet: rho = rho_out, u_y = 0, unknown f3, f6, f7, which take the
-    // colour fraction of the known populations
+  } else if (x == nx - 1) {
     T f[9];
 #pragma unroll
     for (int a = 0; a < 9; ++a) f[a] = fr[a] + fb[a];
-    const T r = T(L.rho_out);
-    const T ux = T(-1) + (f[0] + f[2] + f[4] + T(2) * (f[1] + f[5] + f[8])) / r;
+    const T r = rho_out;
+    const T ux = T(-1) + zh_div(f[0] + f[2] + f[4] + T(2) * (f[1] + f[5] + f[8]), r);
     const T f3 = f[1] - T(2.0 / 3.0) * r * ux;
     const T f7 = f[5] + T(0.5) * (f[2] - f[4]) - r * ux / T(6);
     const T f6 = f[8] - T(0.5) * (f[2] - f[4]) - r * ux / T(6);
     const T kR = fr[0] + fr[1] + fr[2] + fr[4] + fr[5] + fr[8];
     const T kT = f[0] + f[1] + f[2] + f[4] + f[5] + f[8];
-    const T frac = kT != T(0) ? kR / kT : T(0);
+    const T frac = kT != T(0) ? zh_div(kR, kT) : T(0);
     fr[3] = frac * f3;
     fb[3] = (T(1) - frac) * f3;
     fr[6] = frac * f6;
@@ -192,6 +189,31 @@ __device__ __forceinline__ void load_node(const LatDev& L, const S* __restrict__
     fr[7] = frac * f7;
     fb[7] = (T(1) - frac) * f7;
   }
+}
+
+// The 18 stored values of one node (`base` points at plane 0 of the node, planes `plane`
+// elements apart) decoded to (f_R, f_B).
+template <typename S>
+__device__ __forceinline__ void load_raw(const S* __restrict__ base, int plane, typename Store<S>::T r0,
+                                         typename Store<S>::T fr[9], typename Store<S>::T fb[9]) {
+  using T = typename Store<S>::T;
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    const T lo = Store<S>::ld(base + a * plane);
+    const T hi = Store<S>::ld(base + (9 + a) * plane);
+    decode<S, T>(lo, hi, wgt<T>(a) * r0, fr[a], fb[a]);
+  }
+}
+
+// Post-streaming populations of fluid node k = y*pitch + x, stored at the node itself
+// (streaming and bounce-back happened in the previous step's push), with the Zou-He
+// conditions applied on the open columns of an inlet/outlet lattice.
+template <typename S>
+__device__ __forceinline__ void load_node(const LatDev& L, const S* __restrict__ src, long long k, int x,
+                                          typename Store<S>::T fr[9], typename Store<S>::T fb[9]) {
+  using T = typename Store<S>::T;
+  load_raw<S>(src + L.pop_off + k, int(L.plane), T(L.rho0), fr, fb);
+  if (L.bcx == BC_INOUT) zou_he<T>(x, L.nx, T(L.u_in), T(L.rho_out), fr, fb);
 }
 
 // rho^N of Eq. 12 from the colour densities of Eq. 16 (sequential sums in direction order)

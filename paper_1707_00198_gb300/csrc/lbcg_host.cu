@@ -107,6 +107,9 @@ lbcg_status validate(const lbcg_geometry* g, const lbcg_params* p, int idx) {
   if (g->bc_x < 0 || g->bc_x > 2 || g->bc_y < 0 || g->bc_y > 1)
     return fail(LBCG_E_ARG, "lattice %d: bad boundary codes %d %d", idx, g->bc_x, g->bc_y);
   if (g->bc_x == LBCG_BCX_INOUT && g->nx < 3) return fail(LBCG_E_GEOMETRY, "lattice %d: inlet/outlet needs nx >= 3", idx);
+  if (18LL * ((g->nx + 31) / 32 * 32) * g->ny > 0x7fffffffLL)
+    return fail(LBCG_E_UNSUPPORTED, "lattice %d: %d x %d exceeds 2^31 stored values (split it into a batch)", idx,
+                g->nx, g->ny);
   const int nx = g->nx, ny = g->ny;
   if (g->bc_x == LBCG_BCX_CLOSED)
     for (int y = 0; y < ny; ++y)
@@ -394,6 +397,8 @@ lbcg_status lbcg_create_batch(int32_t n, const lbcg_geometry* geoms, const lbcg_
     d.u_in = p.u_in;
     d.rho_out = p.rho_out;
     d.grad_eps = p.grad_eps;
+    d.h_inv_nuR = 0.5 / p.nu_R;
+    d.h_inv_nuB = 0.5 / p.nu_B;
   }
   h->node_total = node_total;
   h->flags_host.assign((size_t)node_total, F_SOLID);

@@ -125,9 +125,22 @@ __global__ void __launch_bounds__(256) k_wall(const LatDev* __restrict__ lats, c
 }
 
 // ------------------------------------------------------------------ k_step
+// Arithmetic helpers: the FP64 instantiation keeps IEEE divisions and square roots (it is the
+// validation path); the FP32-arithmetic instantiations use the hardware reciprocal and
+// reciprocal square root.
+template <typename T>
+__device__ __forceinline__ T rcp_(T x) {
+  if constexpr (sizeof(T) == 4) return __fdividef(1.0f, x);
+  else return T(1) / x;
+}
+
+// FP32-arithmetic instantiations are held to 64 registers so that 1024 threads fit on an
+// SM (they need no more); the FP64 validation instantiation keeps its registers.
 template <typename S, int TY, bool MACRO>
-__global__ void __launch_bounds__(32 * TY) k_step(StepArgs A) {
+__global__ void __launch_bounds__(32 * TY, sizeof(typename Store<S>::T) == 4 ? 1024 / (32 * TY) : 1)
+    k_step(StepArgs A) {
   using T = typename Store<S>::T;
+  constexpr bool kF32 = sizeof(T) == 4;
   constexpr int TX = 32;
   constexpr int NT = TX * TY;
   constexpr int W3 = TX + 6, H3 = TY + 6;   // flags: tile + 3
@@ -139,15 +152,21 @@ __global__ void __launch_bounds__(32 * TY) k_step(StepArgs A) {
   __shared__ T sny[H1 * W1];
   __shared__ int sxm[W3];
   __shared__ int sym[H3];
+  __shared__ LatDev sL;
 
   const int4 tl = A.tiles[blockIdx.x];
-  const LatDev& L = A.lats[tl.x];
   const int x0 = tl.y, y0 = tl.z;
   const int tid = threadIdx.x;
-  const int nx = L.nx, ny = L.ny, pitch = L.pitch;
-  const bool px = L.bcx == BC_PERIODIC, py = L.bcy == BC_PERIODIC;
-  const uint8_t* __restrict__ fl = A.flags + L.node_off;
-  const S* __restrict__ src = static_cast<const S*>(A.src);
+  if (tid == 0) sL = A.lats[tl.x];
+  __syncthreads();
+  // lattice constants in registers (shared memory cannot alias the global stores below)
+  const int nx = sL.nx, ny = sL.ny, pitch = sL.pitch, plane = int(sL.plane);
+  const bool px = sL.bcx == BC_PERIODIC, py = sL.bcy == BC_PERIODIC, inout = sL.bcx == BC_INOUT;
+  const T r0 = T(sL.rho0), u_in = T(sL.u_in), rho_out = T(sL.rho_out), eps = T(sL.grad_eps);
+  const uint8_t* __restrict__ fl = A.flags + sL.node_off;
+  const S* __restrict__ src = static_cast<const S*>(A.src) + sL.pop_off;
+  const T* __restrict__ wall = static_cast<const T*>(A.wall) + sL.node_off;
+  const long long NTOT = A.node_total;
 
   // mapped lattice coordinates of every halo column / row
   for (int i = tid; i < W3; i += NT) sxm[i] = wrap_or_clamp(x0 + i - 3, nx, px);
@@ -155,49 +174,63 @@ __global__ void __launch_bounds__(32 * TY) k_step(StepArgs A) {
   __syncthreads();
   for (int i = tid; i < H3 * W3; i += NT) {
     const int cx = i % W3, cy = i / W3;
-    sfl[i] = fl[(long long)sym[cy] * pitch + sxm[cx]];
+    sfl[i] = fl[sym[cy] * pitch + sxm[cx]];
   }
   __syncthreads();
+
+  auto load = [&](int c3x, int c3y, T fr_[9], T fb_[9]) {
+    const int x = sxm[c3x];
+    load_raw<S>(src + sym[c3y] * pitch + x, plane, r0, fr_, fb_);
+    if (inout) zou_he<T>(x, nx, u_in, rho_out, fr_, fb_);
+  };
+  // rho^N (Eq. 12): exactly +-1 on single-colour nodes in both arithmetic paths
+  auto indicator = [&](const T fr_[9], const T fb_[9], T& sr, T& sb) -> T {
+    sr = fr_[0];
+    sb = fb_[0];
+#pragma unroll
+    for (int a = 1; a < 9; ++a) {
+      sr += fr_[a];
+      sb += fb_[a];
+    }
+    if constexpr (kF32) {
+      const T v = (sr - sb) * rcp_(sr + sb);
+      return sb == T(0) ? T(1) : (sr == T(0) ? T(-1) : v);
+    } else {
+      return (sr - sb) / (sr + sb);
+    }
+  };
 
   // ---- phase A: rho^N on tile + 2 (own node keeps its populations in registers)
   const int lx = tid % TX, ly = tid / TX;
   T fr[9], fb[9], rhoR = T(0), rhoB = T(0), rn = T(0);
-  const uint8_t myfl = sfl[(ly + 3) * W3 + lx + 3];
-  const bool fluid = !(myfl & F_SOLID);
-  {
-    const int c3x = lx + 3, c3y = ly + 3;
-    if (fluid) {
-      load_node<S>(L, src, (long long)sym[c3y] * pitch + sxm[c3x], sxm[c3x], fr, fb);
-      rn = colour_indicator(fr, fb, rhoR, rhoB);
-    } else {
+  const bool fluid = !(sfl[(ly + 3) * W3 + lx + 3] & F_SOLID);
+  if (fluid) {
+    load(lx + 3, ly + 3, fr, fb);
+    rn = indicator(fr, fb, rhoR, rhoB);
+  } else {
 #pragma unroll
-      for (int a = 0; a < 9; ++a) fr[a] = fb[a] = T(0);
-    }
-    srn[(ly + 2) * W2 + lx + 2] = rn;
+    for (int a = 0; a < 9; ++a) fr[a] = fb[a] = T(0);
   }
+  srn[(ly + 2) * W2 + lx + 2] = rn;
   for (int i = tid; i < H2 * W2; i += NT) {
     const int cx = i % W2, cy = i / W2;
     if (cx >= 2 && cx < TX + 2 && cy >= 2 && cy < TY + 2) continue;
-    const int c3x = cx + 1, c3y = cy + 1;
     T v = T(0);
-    if (!(sfl[c3y * W3 + c3x] & F_SOLID)) {
+    if (!(sfl[(cy + 1) * W3 + cx + 1] & F_SOLID)) {
       T hr[9], hb[9], a1, a2;
-      load_node<S>(L, src, (long long)sym[c3y] * pitch + sxm[c3x], sxm[c3x], hr, hb);
-      v = colour_indicator(hr, hb, a1, a2);
+      load(cx + 1, cy + 1, hr, hb);
+      v = indicator(hr, hb, a1, a2);
     }
     srn[i] = v;
   }
   __syncthreads();
 
   // ---- phase B: grad rho^N and n on tile + 1
-  const T eps = T(L.grad_eps);
-  const T* __restrict__ wall = static_cast<const T*>(A.wall);
-  const long long NTOT = A.node_total;
   T gx = T(0), gy = T(0);
   for (int i = tid; i < H1 * W1 + NT; i += NT) {
     // the first NT iterations cover the own tile node, the rest the ring of tile + 1
     int cx, cy;
-    bool own = i < NT;
+    const bool own = i < NT;
     if (own) {
       cx = lx + 1;
       cy = ly + 1;
@@ -214,7 +247,7 @@ __global__ void __launch_bounds__(32 * TY) k_step(StepArgs A) {
     const int sy = py ? cy : min(max(cy + sym[cy + 2] - (y0 + cy - 1), 0), H1 - 1);
     const int c3x = sx + 2, c3y = sy + 2;
     const uint8_t f = sfl[c3y * W3 + c3x];
-    const long long k = L.node_off + (long long)sym[c3y] * pitch + sxm[c3x];
+    const int k = sym[c3y] * pitch + sxm[c3x];
     T ax = T(0), ay = T(0), nxv = T(0), nyv = T(0);
     if (!(f & F_SOLID)) {
       if (f & F_OFB) {
@@ -227,15 +260,24 @@ __global__ void __launch_bounds__(32 * TY) k_step(StepArgs A) {
 #pragma unroll
         for (int a = 1; a < 9; ++a) {
           const T t = wgt<T>(a) * srn[(c2y + ey(a)) * W2 + c2x + ex(a)];
-          ax += T(ex(a)) * t;
-          ay += T(ey(a)) * t;
+          if (ex(a)) ax += T(ex(a)) * t;
+          if (ey(a)) ay += T(ey(a)) * t;
         }
         ax *= T(3);
         ay *= T(3);
-        const T m = sqrt(ax * ax + ay * ay);
-        if (m > eps) {
-          nxv = ax / m;
-          nyv = ay / m;
+        const T m2 = ax * ax + ay * ay;
+        if constexpr (kF32) {
+          if (m2 > eps * eps) {
+            const T inv = rsqrtf(m2);
+            nxv = ax * inv;
+            nyv = ay * inv;
+          }
+        } else {
+          const T m = sqrt(m2);
+          if (m > eps) {
+            nxv = ax / m;
+            nyv = ay / m;
+          }
         }
       }
     } else if (f & F_OSOLID) {
@@ -245,7 +287,7 @@ __global__ void __launch_bounds__(32 * TY) k_step(StepArgs A) {
 #pragma unroll
       for (int b = 1; b < 9; ++b) {
         if (!(sfl[(c3y + ey(b)) * W3 + c3x + ex(b)] & F_SOLID)) {
-          const long long k2 = L.node_off + (long long)sym[c3y + ey(b)] * pitch + sxm[c3x + ex(b)];
+          const int k2 = sym[c3y + ey(b)] * pitch + sxm[c3x + ex(b)];
           vx += wgt<T>(b) * wall[2 * NTOT + k2];
           vy += wgt<T>(b) * wall[3 * NTOT + k2];
           den += wgt<T>(b);
@@ -265,7 +307,7 @@ __global__ void __launch_bounds__(32 * TY) k_step(StepArgs A) {
   }
   __syncthreads();
 
-  // ---- phase C: curvature, force, collision, recolouring, store (own node)
+  // ---- phase C: curvature, force, collision, recolouring, push (own node)
   const int xs = x0 + lx, ys = y0 + ly;
   if (!fluid || xs >= nx || ys >= ny) return;
   const int c1x = lx + 1, c1y = ly + 1;
@@ -275,41 +317,44 @@ __global__ void __launch_bounds__(32 * TY) k_step(StepArgs A) {
     const int o = (c1y + ey(a)) * W1 + c1x + ex(a);
     const T tx = wgt<T>(a) * snx[o];
     const T ty = wgt<T>(a) * sny[o];
-    dxx += T(ex(a)) * tx;
-    dxy += T(ey(a)) * tx;
-    dyx += T(ex(a)) * ty;
-    dyy += T(ey(a)) * ty;
+    if (ex(a)) {
+      dxx += T(ex(a)) * tx;
+      dyx += T(ex(a)) * ty;
+    }
+    if (ey(a)) {
+      dxy += T(ey(a)) * tx;
+      dyy += T(ey(a)) * ty;
+    }
   }
-  dxx *= T(3);
-  dxy *= T(3);
-  dyx *= T(3);
-  dyy *= T(3);
   const T nxo = snx[c1y * W1 + c1x], nyo = sny[c1y * W1 + c1x];
-  const T kappa = -nxo * nxo * dyy - nyo * nyo * dxx + nxo * nyo * (dxy + dyx);   // Eq. 13
-  const T Fx = T(0.5) * T(L.sigma) * kappa * gx;                                  // Eq. 10
-  const T Fy = T(0.5) * T(L.sigma) * kappa * gy;
+  // Eq. 13 (the factor 3 = 1/c_s^2 of Eq. 28 applied once) and Eq. 10
+  const T kappa = T(3) * (-nxo * nxo * dyy - nyo * nyo * dxx + nxo * nyo * (dxy + dyx));
+  const T hsk = T(0.5) * T(sL.sigma) * kappa;
+  const T Fx = hsk * gx;
+  const T Fy = hsk * gy;
 
   T f[9];
 #pragma unroll
   for (int a = 0; a < 9; ++a) f[a] = fr[a] + fb[a];
   const T rho = rhoR + rhoB;
+  const T irho = rcp_(rho);
   const T jx = f[1] - f[3] + f[5] - f[6] - f[7] + f[8];
   const T jy = f[2] - f[4] + f[5] + f[6] - f[7] - f[8];
-  const T ux = (jx + T(0.5) * Fx) / rho;                                          // Eq. 17
-  const T uy = (jy + T(0.5) * Fy) / rho;
-  const long long kn = (long long)ys * pitch + xs;
+  const T ux = (jx + T(0.5) * Fx) * irho;                                         // Eq. 17
+  const T uy = (jy + T(0.5) * Fy) * irho;
+  const int kn = ys * pitch + xs;
   if constexpr (MACRO) {
-    const long long k = L.node_off + kn;
+    const long long k = sL.node_off + kn;
     A.macro[k] = double(rhoR);
     A.macro[NTOT + k] = double(rhoB);
     A.macro[2 * NTOT + k] = double(ux);
     A.macro[3 * NTOT + k] = double(uy);
     return;
   } else {
-    // local viscosity (Eq. 18) and shear rate s_v = 1/tau_v (Eq. 5)
-    const T inv_nu = (T(1) + rn) / T(2 * L.nu_R) + (T(1) - rn) / T(2 * L.nu_B);
-    const T sv = T(1) / (T(3) / inv_nu + T(0.5));
-    const T se = T(L.s_e), seps = T(L.s_eps), sq = T(L.s_q);
+    // local viscosity (Eq. 18) and s_v = 1/tau_v = 1/(3 nu + 1/2) (Eq. 5)
+    const T inv_nu = (T(1) + rn) * T(sL.h_inv_nuR) + (T(1) - rn) * T(sL.h_inv_nuB);
+    const T sv = inv_nu * rcp_(T(3) + T(0.5) * inv_nu);
+    const T se = T(sL.s_e), seps = T(sL.s_eps), sq = T(sL.s_q);
     // moments (rows of Eq. 3, the last one read as e_x e_y)
     const T s14 = f[1] + f[2] + f[3] + f[4];
     const T s58 = f[5] + f[6] + f[7] + f[8];
@@ -325,14 +370,14 @@ __global__ void __launch_bounds__(32 * TY) k_step(StepArgs A) {
     // (0, 6 u.F, -6 u.F, Fx, -Fx, Fy, -Fy, 2(ux Fx - uy Fy), ux Fy + uy Fx)   (Eq. 8-9)
     const T De = se * (me - rho * (T(-2) + T(3) * u2)) - (T(1) - T(0.5) * se) * (T(6) * uF);
     const T Deps = seps * (meps - rho * (T(1) - T(3) * u2)) + (T(1) - T(0.5) * seps) * (T(6) * uF);
-    const T Djx = -Fx, Djy = -Fy;  // s_rho = s_j = 1 (Eq. 6): momentum changes by exactly F
     const T Dqx = sq * (qx + rho * ux) + (T(1) - T(0.5) * sq) * Fx;
     const T Dqy = sq * (qy + rho * uy) + (T(1) - T(0.5) * sq) * Fy;
     const T Dxx = sv * (pxx - rho * (ux * ux - uy * uy)) - (T(1) - T(0.5) * sv) * (T(2) * (ux * Fx - uy * Fy));
     const T Dxy = sv * (pxy - rho * ux * uy) - (T(1) - T(0.5) * sv) * (ux * Fy + uy * Fx);
-    // M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4)
+    // M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4); s_rho = s_j = 1
+    // (Eq. 6), so the momentum rows give Delta_j = -F: the momentum changes by exactly F
     const T ae = De * T(1.0 / 36.0), aeps = Deps * T(1.0 / 36.0);
-    const T ajx = Djx * T(1.0 / 6.0), ajy = Djy * T(1.0 / 6.0);
+    const T ajx = -Fx * T(1.0 / 6.0), ajy = -Fy * T(1.0 / 6.0);
     const T aqx = Dqx * T(1.0 / 12.0), aqy = Dqy * T(1.0 / 12.0);
     const T axx = Dxx * T(0.25), axy = Dxy * T(0.25);
     T fp[9];
@@ -348,10 +393,9 @@ __global__ void __launch_bounds__(32 * TY) k_step(StepArgs A) {
     fp[7] = f[7] - (c58 - ajx - aqx - ajy - aqy + axy);
     fp[8] = f[8] - (c58 + ajx + aqx - ajy - aqy - axy);
     // recolouring (Eq. 14; the blue line with the minus sign)
-    const T cR = rhoR / rho, cB = rhoB / rho;
-    const T pc = T(L.beta) * rhoR * rhoB / rho;
-    S* __restrict__ dst = static_cast<S*>(A.dst) + L.pop_off;
-    const T r0 = T(L.rho0);
+    const T cR = rhoR * irho, cB = rhoB * irho;
+    const T pc = T(sL.beta) * rhoR * rhoB * irho;
+    S* __restrict__ dst = static_cast<S*>(A.dst) + sL.pop_off;
     const int c3x = lx + 3, c3y = ly + 3;
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
@@ -362,7 +406,7 @@ __global__ void __launch_bounds__(32 * TY) k_step(StepArgs A) {
       T lo, hi;
       // streaming (Eq. 15): to x + e_a if that node is fluid; half-way bounce-back into the
       // opposite slot of this node if it is solid; dropped if it lies beyond an open edge
-      long long k;
+      int k;
       int slot;
       if (a == 0) {
         k = kn;
@@ -374,13 +418,13 @@ __global__ void __launch_bounds__(32 * TY) k_step(StepArgs A) {
           k = kn;
           slot = opp(a);
         } else {
-          k = (long long)sym[c3y + ey(a)] * pitch + sxm[c3x + ex(a)];
+          k = sym[c3y + ey(a)] * pitch + sxm[c3x + ex(a)];
           slot = a;
         }
       }
       encode<S, T>(oR, oB, wgt<T>(a) * r0, lo, hi);
-      dst[(long long)slot * L.plane + k] = Store<S>::cv(lo);
-      dst[(long long)(9 + slot) * L.plane + k] = Store<S>::cv(hi);
+      dst[slot * plane + k] = Store<S>::cv(lo);
+      dst[(9 + slot) * plane + k] = Store<S>::cv(hi);
     }
   }
 }
