@@ -158,8 +158,12 @@ size_t lbcg_state_bytes(const lbcg_handle* h);
 lbcg_status lbcg_upload_state(lbcg_handle* h, const void* host_in, size_t bytes);
 lbcg_status lbcg_download_state(lbcg_handle* h, void* host_out, size_t bytes);
 
-/* Tile shape of the fused step kernel (rows of 32-wide tiles); 0 = the built-in default.
- * Valid ty: 4, 8, 16.  Drops captured graphs. */
+/* Schedule of the fused step kernel.  The default is the y-sweep (k_sweep): blocks of 128
+ * threads own strips of 124 columns and walk up `rows`-row segments of them (rows = 0 picks
+ * the segment height so that every SM gets several strips).  lbcg_set_tile switches to 2-D
+ * tiles of 32 x ty nodes (k_step; ty = 4, 8 or 16, 0 = 8).  Both give the same results to
+ * rounding; the choice only changes speed.  Both calls synchronise and drop captured graphs. */
+lbcg_status lbcg_set_sweep(lbcg_handle* h, int32_t rows);
 lbcg_status lbcg_set_tile(lbcg_handle* h, int32_t ty);
 
 /* Kernel timing with CUDA events on the handle's stream.  While enabled, lbcg_step launches

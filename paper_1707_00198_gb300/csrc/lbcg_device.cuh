@@ -31,6 +31,9 @@ enum : uint8_t {
 
 enum { BC_PERIODIC = 0, BC_CLOSED = 1, BC_INOUT = 2 };
 
+// threads of a k_sweep block; its strip has kSweepThreads - 4 interior columns
+constexpr int kSweepThreads = 128;
+
 // Per-lattice constants, resident in global memory, one entry per lattice of a handle.
 struct LatDev {
   int nx, ny, pitch, bcx, bcy, pad_;

@@ -63,6 +63,10 @@ struct lbcg_handle {
   LatDev* d_lats = nullptr;
   int4* d_tiles = nullptr;
   int ntiles = 0;
+  int sweep = 1;          // schedule of the step kernel: 1 = y-sweep over strips, 0 = tiles
+  int sweep_rows = 0;     // rows per strip segment, 0 = automatic
+  int4* d_strips = nullptr;
+  int nstrips = 0;
   int4* d_band = nullptr;
   int nband = 0;
   OfbEntry* d_ofb = nullptr;
@@ -256,6 +260,33 @@ void build_tiles(lbcg_handle* h, std::vector<int4>& tiles) {
   }
 }
 
+// Strips of the y-sweep: kSweepThreads - 4 interior columns each; rows split into segments
+// when the lattices are too narrow to give every SM several strips.  Strips whose own
+// columns and rows hold no fluid node are skipped.
+void build_strips(lbcg_handle* h, std::vector<int4>& strips) {
+  strips.clear();
+  const int W = kSweepThreads - 4;
+  long long nx_strips = 0;
+  for (const LatHost& L : h->lats) nx_strips += (L.nx + W - 1) / W;
+  const long long target = 152LL * 8;
+  for (size_t l = 0; l < h->lats.size(); ++l) {
+    const LatHost& L = h->lats[l];
+    int rows = h->sweep_rows;
+    if (rows <= 0) {
+      const long long k = nx_strips >= target ? 1 : (target + nx_strips - 1) / nx_strips;
+      rows = int(std::max<long long>(8, (L.ny + k - 1) / k));
+    }
+    for (int x0 = 0; x0 < L.nx; x0 += W)
+      for (int y0 = 0; y0 < L.ny; y0 += rows) {
+        const int y1 = std::min(y0 + rows, L.ny);
+        bool any = false;
+        for (int y = y0; y < y1 && !any; ++y)
+          for (int x = x0; x < std::min(x0 + W, L.nx) && !any; ++x) any = L.solid[(size_t)y * L.nx + x] == 0;
+        if (any) strips.push_back(make_int4(int(l), x0, y0, y1));
+      }
+  }
+}
+
 LaunchStep make_launch(lbcg_handle* h, int src, double* macro, int tile_begin, int tile_end) {
   LaunchStep p{};
   p.lats = h->d_lats;
@@ -273,6 +304,9 @@ LaunchStep make_launch(lbcg_handle* h, int src, double* macro, int tile_begin, i
   p.wall = h->d_wall;
   p.node_total = h->node_total;
   p.macro = macro;
+  p.strips = h->d_strips;
+  p.nstrips = h->nstrips;
+  p.sweep = h->sweep;
   return p;
 }
 
@@ -280,8 +314,8 @@ void free_handle(lbcg_handle* h) {
   if (!h) return;
   if (h->graph) cudaGraphExecDestroy(h->graph);
   for (cudaEvent_t e : h->events) cudaEventDestroy(e);
-  void* ptrs[] = {h->pool[0], h->pool[1], h->d_flags, h->d_band_rn, h->d_wall, h->d_macro,
-                  h->d_lats,  h->d_tiles, h->d_band,  h->d_ofb,     h->d_obs};
+  void* ptrs[] = {h->pool[0], h->pool[1], h->d_flags, h->d_band_rn, h->d_wall,  h->d_macro,
+                  h->d_lats,  h->d_tiles, h->d_band,  h->d_ofb,     h->d_obs, h->d_strips};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -296,6 +330,14 @@ lbcg_status upload_tiles(lbcg_handle* h) {
   h->ntiles = int(tiles.size());
   CK(h, cudaMalloc(&h->d_tiles, std::max<size_t>(1, tiles.size()) * sizeof(int4)));
   if (!tiles.empty()) CK(h, cudaMemcpy(h->d_tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  std::vector<int4> strips;
+  build_strips(h, strips);
+  if (h->d_strips) cudaFree(h->d_strips);
+  h->d_strips = nullptr;
+  h->nstrips = int(strips.size());
+  CK(h, cudaMalloc(&h->d_strips, std::max<size_t>(1, strips.size()) * sizeof(int4)));
+  if (!strips.empty())
+    CK(h, cudaMemcpy(h->d_strips, strips.data(), strips.size() * sizeof(int4), cudaMemcpyHostToDevice));
   return LBCG_OK;
 }
 
@@ -681,6 +723,20 @@ lbcg_status lbcg_download_state(lbcg_handle* h, void* host_out, size_t bytes) {
   return LBCG_OK;
 }
 
+lbcg_status lbcg_set_sweep(lbcg_handle* h, int32_t rows) {
+  lbcg_status s = check_handle(h);
+  if (s != LBCG_OK) return s;
+  if (rows < 0) return fail(LBCG_E_ARG, "rows per strip segment must be >= 0");
+  CK(h, cudaStreamSynchronize(h->stream));
+  h->sweep = 1;
+  h->sweep_rows = rows;
+  if (h->graph) {
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  return upload_tiles(h);
+}
+
 lbcg_status lbcg_set_tile(lbcg_handle* h, int32_t ty) {
   lbcg_status s = check_handle(h);
   if (s != LBCG_OK) return s;
@@ -688,6 +744,7 @@ lbcg_status lbcg_set_tile(lbcg_handle* h, int32_t ty) {
   if (ty != 4 && ty != 8 && ty != 16) return fail(LBCG_E_ARG, "tile height must be 4, 8 or 16");
   CK(h, cudaStreamSynchronize(h->stream));
   h->ty = ty;
+  h->sweep = 0;
   if (h->graph) {
     cudaGraphExecDestroy(h->graph);
     h->graph = nullptr;
@@ -723,7 +780,7 @@ lbcg_status lbcg_kernel_times(lbcg_handle* h, double* ms3, int64_t* steps) {
 
 int32_t lbcg_launches_per_step(const lbcg_handle* h) {
   if (!h) return 0;
-  return (h->nband > 0 ? 1 : 0) + (h->nofb > 0 ? 1 : 0) + (h->ntiles > 0 ? 1 : 0);
+  return (h->nband > 0 ? 1 : 0) + (h->nofb > 0 ? 1 : 0) + ((h->sweep ? h->nstrips : h->ntiles) > 0 ? 1 : 0);
 }
 
 int64_t lbcg_total_nodes(const lbcg_handle* h) {

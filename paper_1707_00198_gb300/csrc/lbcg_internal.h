@@ -25,7 +25,10 @@ struct LaunchStep {
   void* band_rn;
   void* wall;
   long long node_total;
-  double* macro;          // non-null: write macroscopic fields instead of stepping
+  const int4* strips;     // sweep schedule: (lattice, x0, y_begin, y_end)
+  int nstrips;
+  int sweep;              // 1: k_sweep over strips, 0: k_step over tiles
+  double* macro;          // non-null: write macroscopic fields instead of stepping (tiles)
   cudaEvent_t* ev;        // non-null: 6 events recorded around k_band, k_wall, k_step
 };
 

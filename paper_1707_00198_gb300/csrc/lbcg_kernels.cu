@@ -429,6 +429,259 @@ __global__ void __launch_bounds__(32 * TY, sizeof(typename Store<S>::T) == 4 ? 1
   }
 }
 
+// ------------------------------------------------------------------ k_sweep
+// The same time step as k_step, organised as a sweep along y over column strips: a block of
+// NTH threads owns NTH - 4 interior columns plus two halo columns on each side and walks up
+// a range of rows.  Per row r it loads the populations of row r and forms rho^N(r); then
+// n(r-1) (needs rho^N of rows r-2..r); then collides row r-2 (needs n of rows r-3..r-1) and
+// pushes it.  Halo work exists only in x ((NTH)/(NTH-4) loads per node), each node is
+// loaded once for rho^N and once more (from L2) for its collision, and the rows of the
+// stencil live in small shared-memory rings.
+struct SweepArgs {
+  const LatDev* lats;
+  const int4* strips;     // (lattice, x0 = first interior column, y_begin, y_end)
+  const void* src;
+  void* dst;
+  const uint8_t* flags;
+  const void* wall;
+  long long node_total;
+};
+
+template <typename S, int NTH>
+__global__ void __launch_bounds__(NTH, sizeof(typename Store<S>::T) == 4 ? 1024 / NTH : 1)
+    k_sweep(SweepArgs A) {
+  using T = typename Store<S>::T;
+  constexpr bool kF32 = sizeof(T) == 4;
+  constexpr int RR = 5;   // rho^N / flags ring (rows r-4 .. r)
+  constexpr int RN = 3;   // n, grad ring (rows r-3 .. r-1)
+  __shared__ T srn[RR][NTH];
+  __shared__ uint8_t sfl[RR][NTH];
+  __shared__ T snx[RN][NTH], sny[RN][NTH], sgx[RN][NTH], sgy[RN][NTH];
+  __shared__ LatDev sL;
+
+  const int4 sp = A.strips[blockIdx.x];
+  const int t = threadIdx.x;
+  if (t == 0) sL = A.lats[sp.x];
+  __syncthreads();
+  const int nx = sL.nx, ny = sL.ny, pitch = sL.pitch, plane = int(sL.plane);
+  const bool px = sL.bcx == BC_PERIODIC, py = sL.bcy == BC_PERIODIC, inout = sL.bcx == BC_INOUT;
+  const T r0 = T(sL.rho0), u_in = T(sL.u_in), rho_out = T(sL.rho_out), eps = T(sL.grad_eps);
+  const T sigma = T(sL.sigma), beta = T(sL.beta), se = T(sL.s_e), seps = T(sL.s_eps), sq = T(sL.s_q);
+  const T hR = T(sL.h_inv_nuR), hB = T(sL.h_inv_nuB);
+  const uint8_t* __restrict__ fl = A.flags + sL.node_off;
+  const S* __restrict__ src = static_cast<const S*>(A.src) + sL.pop_off;
+  S* __restrict__ dst = static_cast<S*>(A.dst) + sL.pop_off;
+  const T* __restrict__ wall = static_cast<const T*>(A.wall) + sL.node_off;
+  const long long NTOT = A.node_total;
+
+  // this thread's column and its neighbours
+  const int cx = sp.y - 2 + t;                       // raw column
+  const int xm = wrap_or_clamp(cx, nx, px);
+  const int xl = wrap_or_clamp(cx - 1, nx, px), xr = wrap_or_clamp(cx + 1, nx, px);
+  // a column beyond a non-periodic edge is a ghost copy of the edge column: its n is
+  // evaluated at the slot of the column it copies (zero normal gradient)
+  const int tc = px ? t : min(max(t + xm - cx, 1), NTH - 2);
+  const bool interior = t >= 2 && t < NTH - 2 && cx < nx;
+  const int ys = sp.z, ye = sp.w;
+
+  auto indicator = [&](const T fr_[9], const T fb_[9], T& sr, T& sb) -> T {
+    sr = fr_[0];
+    sb = fb_[0];
+#pragma unroll
+    for (int a = 1; a < 9; ++a) {
+      sr += fr_[a];
+      sb += fb_[a];
+    }
+    if constexpr (kF32) {
+      const T v = (sr - sb) * rcp_(sr + sb);
+      return sb == T(0) ? T(1) : (sr == T(0) ? T(-1) : v);
+    } else {
+      return (sr - sb) / (sr + sb);
+    }
+  };
+
+  for (int r = ys - 2; r <= ye + 1; ++r) {
+    const int s0 = ((r % RR) + RR) % RR;
+    // ---- stage 1: rho^N and flags of row r
+    {
+      const int ym = wrap_or_clamp(r, ny, py);
+      const uint8_t f = fl[ym * pitch + xm];
+      T v = T(0);
+      if (!(f & F_SOLID)) {
+        T fr[9], fb[9], a1, a2;
+        load_raw<S>(src + ym * pitch + xm, plane, r0, fr, fb);
+        if (inout) zou_he<T>(xm, nx, u_in, rho_out, fr, fb);
+        v = indicator(fr, fb, a1, a2);
+      }
+      srn[s0][t] = v;
+      sfl[s0][t] = f;
+    }
+    __syncthreads();
+    // ---- stage 2: grad rho^N and n of row q = r - 1 (columns 1 .. NTH-2)
+    const int q = r - 1;
+    if (q >= ys - 1 && t >= 1 && t < NTH - 1) {
+      const int sq0 = ((q % RR) + RR) % RR, sqm = ((q - 1) % RR + RR) % RR, sqp = ((q + 1) % RR + RR) % RR;
+      const int qn = ((q % RN) + RN) % RN;
+      const uint8_t f = sfl[sq0][tc];
+      const int ymq = wrap_or_clamp(q, ny, py);
+      T ax = T(0), ay = T(0), nxv = T(0), nyv = T(0);
+      if (!(f & F_SOLID)) {
+        if (f & F_OFB) {
+          const int k = ymq * pitch + wrap_or_clamp(sp.y - 2 + tc, nx, px);
+          ax = wall[k];
+          ay = wall[NTOT + k];
+          nxv = wall[2 * NTOT + k];
+          nyv = wall[3 * NTOT + k];
+        } else {
+          const T* rm = srn[sqm];
+          const T* r0w = srn[sq0];
+          const T* rp = srn[sqp];
+          // Eq. 28 over the 8 neighbours, direction order 1..8
+          const T w1 = T(1.0 / 9.0), w2 = T(1.0 / 36.0);
+          ax = w1 * (r0w[tc + 1] - r0w[tc - 1]) + w2 * (rp[tc + 1] - rp[tc - 1] + rm[tc + 1] - rm[tc - 1]);
+          ay = w1 * (rp[tc] - rm[tc]) + w2 * (rp[tc + 1] + rp[tc - 1] - rm[tc - 1] - rm[tc + 1]);
+          ax *= T(3);
+          ay *= T(3);
+          const T m2 = ax * ax + ay * ay;
+          if constexpr (kF32) {
+            if (m2 > eps * eps) {
+              const T inv = rsqrtf(m2);
+              nxv = ax * inv;
+              nyv = ay * inv;
+            }
+          } else {
+            const T m = sqrt(m2);
+            if (m > eps) {
+              nxv = ax / m;
+              nyv = ay / m;
+            }
+          }
+        }
+      } else if (f & F_OSOLID) {
+        // virtual n (Eq. 29) from the stored n of the neighbouring outermost fluid nodes
+        T vx = T(0), vy = T(0), den = T(0);
+#pragma unroll
+        for (int b = 1; b < 9; ++b) {
+          const int sb = ey(b) == 0 ? sq0 : (ey(b) > 0 ? sqp : sqm);
+          if (!(sfl[sb][tc + ex(b)] & F_SOLID)) {
+            const int k2 = wrap_or_clamp(q + ey(b), ny, py) * pitch + wrap_or_clamp(sp.y - 2 + tc + ex(b), nx, px);
+            vx += wgt<T>(b) * wall[2 * NTOT + k2];
+            vy += wgt<T>(b) * wall[3 * NTOT + k2];
+            den += wgt<T>(b);
+          }
+        }
+        if (den > T(0)) {
+          nxv = vx / den;
+          nyv = vy / den;
+        }
+      }
+      snx[qn][t] = nxv;
+      sny[qn][t] = nyv;
+      sgx[qn][t] = ax;
+      sgy[qn][t] = ay;
+    }
+    __syncthreads();
+    // ---- stage 3: collide and push row p = r - 2
+    const int p = r - 2;
+    if (p < ys || !interior) continue;
+    const int sp0 = ((p % RR) + RR) % RR;
+    const uint8_t myf = sfl[sp0][t];
+    if (myf & F_SOLID) continue;
+    const int pn = ((p % RN) + RN) % RN, pnm = ((p - 1) % RN + RN) % RN, pnp = ((p + 1) % RN + RN) % RN;
+    const int ym = wrap_or_clamp(p, ny, py);
+    const int kn = ym * pitch + xm;
+    T fr[9], fb[9];
+    load_raw<S>(src + kn, plane, r0, fr, fb);
+    if (inout) zou_he<T>(xm, nx, u_in, rho_out, fr, fb);
+    T rhoR, rhoB;
+    const T rn = indicator(fr, fb, rhoR, rhoB);
+    // grad n (Eq. 28) and curvature (Eq. 13)
+    const T* nxm = snx[pnm]; const T* nx0 = snx[pn]; const T* nxp = snx[pnp];
+    const T* nym = sny[pnm]; const T* ny0 = sny[pn]; const T* nyp = sny[pnp];
+    const T w1 = T(1.0 / 9.0), w2 = T(1.0 / 36.0);
+    const T dxx = w1 * (nx0[t + 1] - nx0[t - 1]) + w2 * (nxp[t + 1] - nxp[t - 1] + nxm[t + 1] - nxm[t - 1]);
+    const T dxy = w1 * (nxp[t] - nxm[t]) + w2 * (nxp[t + 1] + nxp[t - 1] - nxm[t - 1] - nxm[t + 1]);
+    const T dyx = w1 * (ny0[t + 1] - ny0[t - 1]) + w2 * (nyp[t + 1] - nyp[t - 1] + nym[t + 1] - nym[t - 1]);
+    const T dyy = w1 * (nyp[t] - nym[t]) + w2 * (nyp[t + 1] + nyp[t - 1] - nym[t - 1] - nym[t + 1]);
+    const T nxo = nx0[t], nyo = ny0[t];
+    const T kappa = T(3) * (-nxo * nxo * dyy - nyo * nyo * dxx + nxo * nyo * (dxy + dyx));
+    const T hsk = T(0.5) * sigma * kappa;
+    const T Fx = hsk * sgx[pn][t];
+    const T Fy = hsk * sgy[pn][t];
+
+    T f[9];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) f[a] = fr[a] + fb[a];
+    const T rho = rhoR + rhoB;
+    const T irho = rcp_(rho);
+    const T jx = f[1] - f[3] + f[5] - f[6] - f[7] + f[8];
+    const T jy = f[2] - f[4] + f[5] + f[6] - f[7] - f[8];
+    const T ux = (jx + T(0.5) * Fx) * irho;
+    const T uy = (jy + T(0.5) * Fy) * irho;
+    const T inv_nu = (T(1) + rn) * hR + (T(1) - rn) * hB;
+    const T sv = inv_nu * rcp_(T(3) + T(0.5) * inv_nu);
+    const T s14 = f[1] + f[2] + f[3] + f[4];
+    const T s58 = f[5] + f[6] + f[7] + f[8];
+    const T me = T(-4) * f[0] - s14 + T(2) * s58;
+    const T meps = T(4) * f[0] - T(2) * s14 + s58;
+    const T qx = T(-2) * (f[1] - f[3]) + (f[5] - f[6] - f[7] + f[8]);
+    const T qy = T(-2) * (f[2] - f[4]) + (f[5] + f[6] - f[7] - f[8]);
+    const T pxx = f[1] - f[2] + f[3] - f[4];
+    const T pxy = f[5] - f[6] + f[7] - f[8];
+    const T u2 = ux * ux + uy * uy;
+    const T uF = ux * Fx + uy * Fy;
+    const T De = se * (me - rho * (T(-2) + T(3) * u2)) - (T(1) - T(0.5) * se) * (T(6) * uF);
+    const T Deps = seps * (meps - rho * (T(1) - T(3) * u2)) + (T(1) - T(0.5) * seps) * (T(6) * uF);
+    const T Dqx = sq * (qx + rho * ux) + (T(1) - T(0.5) * sq) * Fx;
+    const T Dqy = sq * (qy + rho * uy) + (T(1) - T(0.5) * sq) * Fy;
+    const T Dxx = sv * (pxx - rho * (ux * ux - uy * uy)) - (T(1) - T(0.5) * sv) * (T(2) * (ux * Fx - uy * Fy));
+    const T Dxy = sv * (pxy - rho * ux * uy) - (T(1) - T(0.5) * sv) * (ux * Fy + uy * Fx);
+    const T ae = De * T(1.0 / 36.0), aeps = Deps * T(1.0 / 36.0);
+    const T ajx = -Fx * T(1.0 / 6.0), ajy = -Fy * T(1.0 / 6.0);
+    const T aqx = Dqx * T(1.0 / 12.0), aqy = Dqy * T(1.0 / 12.0);
+    const T axx = Dxx * T(0.25), axy = Dxy * T(0.25);
+    T fp[9];
+    fp[0] = f[0] - (T(-4) * ae + T(4) * aeps);
+    const T c14 = -ae - T(2) * aeps;
+    fp[1] = f[1] - (c14 + ajx - T(2) * aqx + axx);
+    fp[2] = f[2] - (c14 + ajy - T(2) * aqy - axx);
+    fp[3] = f[3] - (c14 - ajx + T(2) * aqx + axx);
+    fp[4] = f[4] - (c14 - ajy + T(2) * aqy - axx);
+    const T c58 = T(2) * ae + aeps;
+    fp[5] = f[5] - (c58 + ajx + aqx + ajy + aqy + axy);
+    fp[6] = f[6] - (c58 - ajx - aqx + ajy + aqy - axy);
+    fp[7] = f[7] - (c58 - ajx - aqx - ajy - aqy + axy);
+    fp[8] = f[8] - (c58 + ajx + aqx - ajy - aqy - axy);
+    const T cR = rhoR * irho, cB = rhoB * irho;
+    const T pc = beta * rhoR * rhoB * irho;
+    // destinations: rows p-1, p, p+1 and columns cx-1, cx, cx+1
+    const int rowk[3] = {wrap_or_clamp(p - 1, ny, py) * pitch, ym * pitch, wrap_or_clamp(p + 1, ny, py) * pitch};
+    const int colk[3] = {xl, xm, xr};
+    const int rings[3] = {((p - 1) % RR + RR) % RR, sp0, ((p + 1) % RR + RR) % RR};
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+      const T en = T(ex(a)) * nxo + T(ey(a)) * nyo;
+      const T pert = pc * wgt<T>(a) * en;
+      const T oR = cR * fp[a] + pert;
+      const T oB = cB * fp[a] - pert;
+      int k = kn, slot = a;
+      if (a != 0) {
+        const int xrw = cx + ex(a), yrw = p + ey(a);
+        if ((!px && (xrw < 0 || xrw >= nx)) || (!py && (yrw < 0 || yrw >= ny))) continue;
+        if (sfl[rings[ey(a) + 1]][t + ex(a)] & F_SOLID) {
+          slot = opp(a);
+        } else {
+          k = rowk[ey(a) + 1] + colk[ex(a) + 1];
+        }
+      }
+      T lo, hi;
+      encode<S, T>(oR, oB, wgt<T>(a) * r0, lo, hi);
+      dst[slot * plane + k] = Store<S>::cv(lo);
+      dst[(9 + slot) * plane + k] = Store<S>::cv(hi);
+    }
+  }
+}
+
 // ------------------------------------------------------------------ layout conversion
 // host layout: double [2][9][ny][nx] (f_R block then f_B block) <-> storage pool
 template <typename S>
@@ -498,7 +751,12 @@ static cudaError_t launch_all(const LaunchStep& p, cudaStream_t st) {
   }
   rec(3);
   rec(4);
-  if (p.ntiles > 0) {
+  if (p.sweep && p.macro == nullptr) {
+    if (p.nstrips > 0) {
+      SweepArgs B{p.lats, p.strips, p.src, p.dst, p.flags, p.wall, p.node_total};
+      k_sweep<S, kSweepThreads><<<p.nstrips, kSweepThreads, 0, st>>>(B);
+    }
+  } else if (p.ntiles > 0) {
     StepArgs A{p.lats, p.tiles, p.src, p.dst, p.flags, p.band_rn, p.wall, p.node_total, p.macro};
     const bool macro = p.macro != nullptr;
     switch (p.ty) {

@@ -83,6 +83,7 @@ def library():
         "lbcg_upload_state": (C.c_int, [H, C.c_void_p, C.c_size_t]),
         "lbcg_download_state": (C.c_int, [H, C.c_void_p, C.c_size_t]),
         "lbcg_set_tile": (C.c_int, [H, C.c_int32]),
+        "lbcg_set_sweep": (C.c_int, [H, C.c_int32]),
         "lbcg_profile": (C.c_int, [H, C.c_int32]),
         "lbcg_kernel_times": (C.c_int, [H, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
         "lbcg_launches_per_step": (C.c_int32, [H]),
@@ -103,7 +104,7 @@ def library():
 def exported_symbols() -> list:
     return ["lbcg_create", "lbcg_create_batch", "lbcg_step", "lbcg_observables", "lbcg_get_populations",
             "lbcg_set_populations", "lbcg_get_fields", "lbcg_state_bytes", "lbcg_upload_state",
-            "lbcg_download_state", "lbcg_set_tile", "lbcg_profile", "lbcg_kernel_times", "lbcg_launches_per_step", "lbcg_total_nodes", "lbcg_destroy",
+            "lbcg_download_state", "lbcg_set_sweep", "lbcg_set_tile", "lbcg_profile", "lbcg_kernel_times", "lbcg_launches_per_step", "lbcg_total_nodes", "lbcg_destroy",
             "lbcg_last_error", "lbcg_field_moments_noalloc"]
 
 
@@ -194,6 +195,10 @@ def lbcg_set_tile(h: int, ty: int):
     _check(library().lbcg_set_tile(h, ty))
 
 
+def lbcg_set_sweep(h: int, rows: int = 0):
+    _check(library().lbcg_set_sweep(h, rows))
+
+
 def lbcg_profile(h: int, enable: bool):
     _check(library().lbcg_profile(h, 1 if enable else 0))
 
@@ -267,6 +272,9 @@ class Lattice:
 
     def set_tile(self, ty: int):
         lbcg_set_tile(self.h, ty)
+
+    def set_sweep(self, rows: int = 0):
+        lbcg_set_sweep(self.h, rows)
 
     @property
     def state_bytes(self) -> int:

@@ -36,11 +36,13 @@ def oracle_run(g, p, n, fR=None, fB=None):
     return lat, np.stack([fR.numpy(), fB.numpy()])
 
 
-def gpu_run(g, p, n, prec="fp64", ty=0, state=None):
+def gpu_run(g, p, n, prec="fp64", ty=0, state=None, rows=None):
     from paper_1707_00198_gb300.lbcg import Lattice
     L = Lattice(g, p, prec)
     if ty:
         L.set_tile(ty)
+    if rows is not None:
+        L.set_sweep(rows)
     if state is not None:
         L.set_populations(state)
     L.step(n)
@@ -85,13 +87,29 @@ def test_fp64_matches_oracle_after_100_steps(name, g, p):
     assert err <= TOL64, f"{name}: max |df| = {err:.3e}"
 
 
-@pytest.mark.parametrize("ty", [4, 16])
-def test_fp64_parity_is_independent_of_the_tile_shape(ty):
-    g, p = I.config_static_droplet()
-    lat, ref = oracle_run(g, p, 40)
-    L, got = gpu_run(g, p, 40, ty=ty)
-    L.close()
-    assert np.abs(got - ref).max() <= TOL64
+SCHEDULES = [("tiles", 4, None), ("tiles", 8, None), ("tiles", 16, None), ("sweep", 0, 3), ("sweep", 0, 17)]
+
+
+@pytest.mark.parametrize("kind,ty,rows", SCHEDULES, ids=[f"{k}{t or r}" for k, t, r in SCHEDULES])
+def test_fp64_parity_is_independent_of_the_schedule(kind, ty, rows):
+    # 2-D tiles of 32 x ty, and the y-sweep with short row segments (every segment starts
+    # with the warm-up rows of the sweep), on walls, a cylinder and an inlet/outlet channel
+    cases = [I.config_static_droplet(),
+             (I.cylinder_droplet(90, 80, Rs=16.0, cx=45.0, cy=28.0, Rd=14.0, theta=math.radians(120), noise=1e-3,
+                                 seed=4, analytic_normal=False), I.Params(theta=math.radians(120), sigma=0.02)),
+             (I.displacement_channel(W=20, L=110, x_I=25.0, seed=6, noise=1e-3), I.fingering_params(5.0, 0.1, 60.0))]
+    for g, p in cases:
+        lat, ref = oracle_run(g, p, 40)
+        L, got = gpu_run(g, p, 40, ty=ty, rows=rows)
+        L.close()
+        assert np.abs(got - ref).max() <= TOL64, (g.name, np.abs(got - ref).max())
+
+
+def test_fp32_schedules_agree():
+    g, p = I.config_fingering(M=5.0, Ca=0.1, theta_deg=60.0)
+    _, a = gpu_run(g, p, 200, prec="fp32", ty=8)
+    _, b = gpu_run(g, p, 200, prec="fp32", rows=0)
+    assert np.abs(a - b).max() <= 1e-5
 
 
 def test_fp64_observables_match_oracle():
