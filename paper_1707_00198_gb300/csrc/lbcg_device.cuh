@@ -1,17 +1,22 @@
 // Device-side building blocks of the colour-gradient LBM step (arXiv 1707.00198, Sec. II).
 //
 // Layout in HBM (one "pool" per kind, lattices of a batch packed one after another):
-//   populations : 18 planes [k][a][y][pitch] of the storage type S, plane-major, x fastest;
-//                 planes 0..8 hold direction a of the first stored quantity, 9..17 of the
-//                 second one.  Direct storage (double, float): f_{a,R} then f_{a,B}.
-//                 Deviation storage (half, bfloat16): d_a = f_a - w_a rho0 then
-//                 g_a = f_{a,R} - f_{a,B} (an exact linear transform of the pair).
+//   populations : 18 stored values per node in the storage type S, laid out in blocks of
+//                 32 nodes along x: [y][x/32][a][x%32][k] (direction a = 0..8, k = 0, 1).
+//                 k = 0 holds the first stored quantity of direction a, k = 1 the second,
+//                 so a direction's pair is one vector access; a node's nine pairs sit at
+//                 fixed distances from one address, and a 32-node row segment is one
+//                 contiguous chunk of 18 x 32 values.
+//                 Direct storage (double, float): (f_{a,R}, f_{a,B}).
+//                 Deviation storage (half, bfloat16): (d_a = f_a - w_a rho0,
+//                 g_a = f_{a,R} - f_{a,B}), an exact linear transform of the pair.
 //                 The stored state is the post-streaming state at each node: a step loads
-//                 a node's own 18 values and pushes its post-collision values to the
+//                 a node's own values and pushes its post-collision values to the
 //                 neighbours (half-way bounce-back: back into the node's own opposite slot;
 //                 across an open edge: dropped).
-//   node arrays : flags (uint8), and in the compute type T the rho^N of the wall band and
-//                 the corrected gradient / normal of the outermost fluid nodes.
+//   node arrays : [y][pitch] per lattice: flags (uint8), the solid-neighbour mask (uint8),
+//                 and in the compute type T the rho^N of the wall band and the corrected
+//                 gradient / normal of the outermost fluid nodes.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -27,6 +32,7 @@ enum : uint8_t {
   F_OFB = 2,      // outermost fluid node (fluid with a solid D2Q9 neighbour), Omega_Fb
   F_OSOLID = 4,   // outermost solid node (solid with a fluid D2Q9 neighbour), Eq. 29
   F_NEAR = 8,     // within Chebyshev distance 3 of a solid node (excluded from the fit)
+  F_EDGE = 16,    // fluid node in an open (inlet/outlet) column: some pushes leave the lattice
 };
 
 enum { BC_PERIODIC = 0, BC_CLOSED = 1, BC_INOUT = 2 };
@@ -37,8 +43,8 @@ constexpr int kSweepThreads = 128;
 // Per-lattice constants, resident in global memory, one entry per lattice of a handle.
 struct LatDev {
   int nx, ny, pitch, bcx, bcy, pad_;
-  long long pop_off;   // element offset of plane 0 of this lattice in the population pool
-  long long plane;     // elements per plane (pitch * ny)
+  long long pop_off;   // element offset of this lattice's block in the population pool
+  long long plane;     // elements of one node-array plane of this lattice (pitch * ny)
   long long node_off;  // element offset of node (0,0) in the node arrays
   double nu_R, nu_B, sigma, beta, s_e, s_eps, s_q, rho0, u_in, rho_out, grad_eps;
   double h_inv_nuR, h_inv_nuB;  // 1/(2 nu_R), 1/(2 nu_B): the two weights of Eq. 18
@@ -65,34 +71,64 @@ __host__ __device__ constexpr T wgt(int a) {
   return a == 0 ? T(4.0 / 9.0) : (a <= 4 ? T(1.0 / 9.0) : T(1.0 / 36.0));
 }
 
+// Element offset of the direction-0 pair of node (x, y) within its lattice's population block
+// (pitch is a multiple of 32); the pair of direction a is kDir * a further.
+constexpr int kDir = 64;          // elements between the pairs of consecutive directions
+constexpr int kSeg = 9 * kDir;    // elements of a 32-node row segment
+__host__ __device__ __forceinline__ int pop_node(int x, int y, int pitch) {
+  return (y * (pitch >> 5) + (x >> 5)) * kSeg + (x & 31) * 2;
+}
+
 // ------------------------------------------------------------------ storage traits
 template <typename S> struct Store;
 template <> struct Store<double> {
   using T = double;
   static constexpr bool kDeviation = false;
-  __device__ static double ld(const double* p) { return __ldg(p); }
-  __device__ static double cv(double v) { return v; }
+  __device__ static void ldp(const double* p, double& lo, double& hi) {
+    const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+    lo = v.x;
+    hi = v.y;
+  }
+  __device__ static void stp(double* p, double lo, double hi) {
+    *reinterpret_cast<double2*>(p) = make_double2(lo, hi);
+  }
 };
 template <> struct Store<float> {
   using T = float;
   static constexpr bool kDeviation = false;
-  __device__ static float ld(const float* p) { return __ldg(p); }
-  __device__ static float cv(float v) { return v; }
+  __device__ static void ldp(const float* p, float& lo, float& hi) {
+    const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+    lo = v.x;
+    hi = v.y;
+  }
+  __device__ static void stp(float* p, float lo, float hi) { *reinterpret_cast<float2*>(p) = make_float2(lo, hi); }
 };
 template <> struct Store<__half> {
   using T = float;
   static constexpr bool kDeviation = true;
-  __device__ static float ld(const __half* p) { return __half2float(__ldg(p)); }
-  __device__ static __half cv(float v) { return __float2half_rn(v); }
+  __device__ static void ldp(const __half* p, float& lo, float& hi) {
+    const float2 v = __half22float2(__ldg(reinterpret_cast<const __half2*>(p)));
+    lo = v.x;
+    hi = v.y;
+  }
+  __device__ static void stp(__half* p, float lo, float hi) {
+    *reinterpret_cast<__half2*>(p) = __floats2half2_rn(lo, hi);
+  }
 };
 template <> struct Store<__nv_bfloat16> {
   using T = float;
   static constexpr bool kDeviation = true;
-  __device__ static float ld(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
-  __device__ static __nv_bfloat16 cv(float v) { return __float2bfloat16_rn(v); }
+  __device__ static void ldp(const __nv_bfloat16* p, float& lo, float& hi) {
+    const float2 v = __bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162*>(p)));
+    lo = v.x;
+    hi = v.y;
+  }
+  __device__ static void stp(__nv_bfloat16* p, float lo, float hi) {
+    *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(lo, hi);
+  }
 };
 
-// stored pair (lo = plane a, hi = plane 9+a) -> (f_R, f_B)
+// stored pair (lo = k 0, hi = k 1) <-> (f_R, f_B)
 template <typename S, typename T>
 __device__ __forceinline__ void decode(T lo, T hi, T wr0, T& fr, T& fb) {
   if constexpr (Store<S>::kDeviation) {
@@ -142,11 +178,7 @@ __device__ __forceinline__ int wrap_or_clamp(int v, int n, bool periodic) {
   return v < 0 ? 0 : (v >= n ? n - 1 : v);
 }
 
-// ------------------------------------------------------------------ load with boundaries
-// Post-streaming populations of fluid node (x, y), stored at the node itself (streaming and
-// bounce-back happened in the previous step's push).  On an inlet/outlet lattice the Zou-He
-// conditions (Sec. III.D) replace the populations that enter from outside; applying them on
-// every read is idempotent, so a state that already satisfies them is unchanged.
+// ------------------------------------------------------------------ Zou-He open columns
 // Zou-He conditions (Sec. III.D) on the populations of a node in column x of an
 // inlet/outlet lattice: velocity inlet (u_in, 0) carrying red only at x = 0 (unknown f1, f5,
 // f8), pressure outlet rho_out at x = nx-1 (unknown f3, f6, f7, which take the colour
@@ -194,28 +226,39 @@ __device__ __forceinline__ void zou_he(int x, int nx, T u_in, T rho_out, T fr[9]
   }
 }
 
-// The 18 stored values of one node (`base` points at plane 0 of the node, planes `plane`
-// elements apart) decoded to (f_R, f_B).
+// ------------------------------------------------------------------ node access
+// The nine stored pairs of one node (`base` points at its direction-0 pair) decoded to
+// (f_R, f_B).
 template <typename S>
-__device__ __forceinline__ void load_raw(const S* __restrict__ base, int plane, typename Store<S>::T r0,
+__device__ __forceinline__ void load_raw(const S* __restrict__ base, typename Store<S>::T r0,
                                          typename Store<S>::T fr[9], typename Store<S>::T fb[9]) {
   using T = typename Store<S>::T;
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
-    const T lo = Store<S>::ld(base + a * plane);
-    const T hi = Store<S>::ld(base + (9 + a) * plane);
+    T lo, hi;
+    Store<S>::ldp(base + a * kDir, lo, hi);
     decode<S, T>(lo, hi, wgt<T>(a) * r0, fr[a], fb[a]);
   }
 }
 
-// Post-streaming populations of fluid node k = y*pitch + x, stored at the node itself
-// (streaming and bounce-back happened in the previous step's push), with the Zou-He
-// conditions applied on the open columns of an inlet/outlet lattice.
+// Encode (f_R, f_B) of one direction (rest weight wr0 = w_a rho0) and store the pair at p.
 template <typename S>
-__device__ __forceinline__ void load_node(const LatDev& L, const S* __restrict__ src, long long k, int x,
+__device__ __forceinline__ void store_pair(S* p, typename Store<S>::T fr, typename Store<S>::T fb,
+                                           typename Store<S>::T wr0) {
+  using T = typename Store<S>::T;
+  T lo, hi;
+  encode<S, T>(fr, fb, wr0, lo, hi);
+  Store<S>::stp(p, lo, hi);
+}
+
+// Post-streaming populations of fluid node (x, y), stored at the node itself (streaming and
+// bounce-back happened in the previous step's push), with the Zou-He conditions applied on
+// the open columns of an inlet/outlet lattice.
+template <typename S>
+__device__ __forceinline__ void load_node(const LatDev& L, const S* __restrict__ src, int x, int y,
                                           typename Store<S>::T fr[9], typename Store<S>::T fb[9]) {
   using T = typename Store<S>::T;
-  load_raw<S>(src + L.pop_off + k, int(L.plane), T(L.rho0), fr, fb);
+  load_raw<S>(src + L.pop_off + pop_node(x, y, L.pitch), T(L.rho0), fr, fb);
   if (L.bcx == BC_INOUT) zou_he<T>(x, L.nx, T(L.u_in), T(L.rho_out), fr, fb);
 }
 

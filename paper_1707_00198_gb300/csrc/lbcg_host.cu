@@ -57,6 +57,7 @@ struct lbcg_handle {
   void* pool[2] = {nullptr, nullptr};
   int cur = 0;
   uint8_t* d_flags = nullptr;
+  uint8_t* d_nbmask = nullptr;
   void* d_band_rn = nullptr;
   void* d_wall = nullptr;
   double* d_macro = nullptr;
@@ -147,21 +148,26 @@ lbcg_status validate(const lbcg_geometry* g, const lbcg_params* p, int idx) {
 
 // Classification of one lattice (Sec. II.C): flags, wall band, outermost-fluid entries.
 void classify(const lbcg_geometry* g, const lbcg_params* p, int lat, std::vector<uint8_t>& flags_local,
-              std::vector<int4>& band, std::vector<OfbEntry>& ofb) {
+              std::vector<uint8_t>& mask_local, std::vector<int4>& band, std::vector<OfbEntry>& ofb) {
   const int nx = g->nx, ny = g->ny;
   const bool px = g->bc_x == LBCG_BCX_PERIODIC, py = g->bc_y == LBCG_BCY_PERIODIC;
   auto S = [&](int x, int y) { return g->solid[(size_t)y * nx + x] != 0; };
   flags_local.assign((size_t)nx * ny, 0);
+  mask_local.assign((size_t)nx * ny, 0);
   for (int y = 0; y < ny; ++y)
     for (int x = 0; x < nx; ++x) {
       uint8_t f = 0;
       const bool s = S(x, y);
       bool any_s = false, any_f = false;
+      uint8_t m = 0;
       for (int a = 1; a < 9; ++a) {
         const bool sn = S(wrap_clamp(x + EXH[a], nx, px), wrap_clamp(y + EYH[a], ny, py));
         any_s |= sn;
         any_f |= !sn;
+        if (sn) m |= uint8_t(1u << (a - 1));
       }
+      if (!s) mask_local[(size_t)y * nx + x] = m;
+      if (!s && g->bc_x == LBCG_BCX_INOUT && (x == 0 || x == nx - 1)) f |= F_EDGE;
       if (s) {
         f |= F_SOLID;
         if (any_f) f |= F_OSOLID;
@@ -300,6 +306,7 @@ LaunchStep make_launch(lbcg_handle* h, int src, double* macro, int tile_begin, i
   p.src = h->pool[src];
   p.dst = h->pool[src ^ 1];
   p.flags = h->d_flags;
+  p.nbmask = h->d_nbmask;
   p.band_rn = h->d_band_rn;
   p.wall = h->d_wall;
   p.node_total = h->node_total;
@@ -314,8 +321,9 @@ void free_handle(lbcg_handle* h) {
   if (!h) return;
   if (h->graph) cudaGraphExecDestroy(h->graph);
   for (cudaEvent_t e : h->events) cudaEventDestroy(e);
-  void* ptrs[] = {h->pool[0], h->pool[1], h->d_flags, h->d_band_rn, h->d_wall,  h->d_macro,
-                  h->d_lats,  h->d_tiles, h->d_band,  h->d_ofb,     h->d_obs, h->d_strips};
+  void* ptrs[] = {h->pool[0], h->pool[1], h->d_flags, h->d_band_rn, h->d_wall,   h->d_macro,
+                  h->d_lats,  h->d_tiles, h->d_band,  h->d_ofb,     h->d_obs,    h->d_strips,
+                  h->d_nbmask};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -444,19 +452,23 @@ lbcg_status lbcg_create_batch(int32_t n, const lbcg_geometry* geoms, const lbcg_
   }
   h->node_total = node_total;
   h->flags_host.assign((size_t)node_total, F_SOLID);
+  std::vector<uint8_t> mask_host((size_t)node_total, 0);
   for (int l = 0; l < n; ++l) {
-    std::vector<uint8_t> fl;
-    classify(&geoms[l], &prms[l], l, fl, band, ofb);
+    std::vector<uint8_t> fl, mk;
+    classify(&geoms[l], &prms[l], l, fl, mk, band, ofb);
     const LatHost& L = h->lats[l];
-    for (int y = 0; y < L.ny; ++y)
+    for (int y = 0; y < L.ny; ++y) {
       memcpy(&h->flags_host[L.node_off + (size_t)y * L.pitch], &fl[(size_t)y * L.nx], L.nx);
+      memcpy(&mask_host[L.node_off + (size_t)y * L.pitch], &mk[(size_t)y * L.nx], L.nx);
+    }
   }
   h->nband = int(band.size());
   h->nofb = int(ofb.size());
   const size_t es = elem_size(precision), cs = compute_size(precision);
   auto alloc = [&](void** p, size_t bytes) { return cudaMalloc(p, std::max<size_t>(bytes, 16)) == cudaSuccess; };
   bool ok = alloc(&h->pool[0], 18 * (size_t)node_total * es) && alloc(&h->pool[1], 18 * (size_t)node_total * es) &&
-            alloc((void**)&h->d_flags, (size_t)node_total) && alloc(&h->d_band_rn, (size_t)node_total * cs) &&
+            alloc((void**)&h->d_flags, (size_t)node_total) && alloc((void**)&h->d_nbmask, (size_t)node_total) &&
+            alloc(&h->d_band_rn, (size_t)node_total * cs) &&
             alloc(&h->d_wall, 4 * (size_t)node_total * cs) && alloc((void**)&h->d_lats, n * sizeof(LatDev)) &&
             alloc((void**)&h->d_band, band.size() * sizeof(int4)) &&
             alloc((void**)&h->d_ofb, ofb.size() * sizeof(OfbEntry)) &&
@@ -475,6 +487,7 @@ lbcg_status lbcg_create_batch(int32_t n, const lbcg_geometry* geoms, const lbcg_
     }                                                     \
   } while (0)
   CKC(cudaMemcpy(h->d_flags, h->flags_host.data(), (size_t)node_total, cudaMemcpyHostToDevice));
+  CKC(cudaMemcpy(h->d_nbmask, mask_host.data(), (size_t)node_total, cudaMemcpyHostToDevice));
   CKC(cudaMemcpy(h->d_lats, ld.data(), n * sizeof(LatDev), cudaMemcpyHostToDevice));
   if (!band.empty()) CKC(cudaMemcpy(h->d_band, band.data(), band.size() * sizeof(int4), cudaMemcpyHostToDevice));
   if (!ofb.empty()) CKC(cudaMemcpy(h->d_ofb, ofb.data(), ofb.size() * sizeof(OfbEntry), cudaMemcpyHostToDevice));

@@ -22,6 +22,7 @@ struct LaunchStep {
   const void* src;
   void* dst;
   const uint8_t* flags;
+  const uint8_t* nbmask;  // per node: bit a-1 set if the neighbour in direction a is solid
   void* band_rn;
   void* wall;
   long long node_total;

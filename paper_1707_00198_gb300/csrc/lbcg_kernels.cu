@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(256) k_band(const LatDev* __restrict__ lats, c
   const LatDev& L = lats[e.x];
   const int x = e.y, y = e.z;
   T fr[9], fb[9], rR, rB;
-  load_node<S>(L, src, (long long)y * L.pitch + x, x, fr, fb);
+  load_node<S>(L, src, x, y, fr, fb);
   band_rn[L.node_off + (long long)y * L.pitch + x] = colour_indicator(fr, fb, rR, rB);
 }
 
@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(32 * TY, sizeof(typename Store<S>::T) == 4 ? 1
   if (tid == 0) sL = A.lats[tl.x];
   __syncthreads();
   // lattice constants in registers (shared memory cannot alias the global stores below)
-  const int nx = sL.nx, ny = sL.ny, pitch = sL.pitch, plane = int(sL.plane);
+  const int nx = sL.nx, ny = sL.ny, pitch = sL.pitch;
   const bool px = sL.bcx == BC_PERIODIC, py = sL.bcy == BC_PERIODIC, inout = sL.bcx == BC_INOUT;
   const T r0 = T(sL.rho0), u_in = T(sL.u_in), rho_out = T(sL.rho_out), eps = T(sL.grad_eps);
   const uint8_t* __restrict__ fl = A.flags + sL.node_off;
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(32 * TY, sizeof(typename Store<S>::T) == 4 ? 1
 
   auto load = [&](int c3x, int c3y, T fr_[9], T fb_[9]) {
     const int x = sxm[c3x];
-    load_raw<S>(src + sym[c3y] * pitch + x, plane, r0, fr_, fb_);
+    load_raw<S>(src + pop_node(x, sym[c3y], pitch), r0, fr_, fb_);
     if (inout) zou_he<T>(x, nx, u_in, rho_out, fr_, fb_);
   };
   // rho^N (Eq. 12): exactly +-1 on single-colour nodes in both arithmetic paths
@@ -397,34 +397,26 @@ __global__ void __launch_bounds__(32 * TY, sizeof(typename Store<S>::T) == 4 ? 1
     const T pc = T(sL.beta) * rhoR * rhoB * irho;
     S* __restrict__ dst = static_cast<S*>(A.dst) + sL.pop_off;
     const int c3x = lx + 3, c3y = ly + 3;
+    const int pn_own = pop_node(xs, ys, pitch);
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
       const T en = T(ex(a)) * nxo + T(ey(a)) * nyo;
       const T pert = pc * wgt<T>(a) * en;
       const T oR = cR * fp[a] + pert;
       const T oB = cB * fp[a] - pert;
-      T lo, hi;
       // streaming (Eq. 15): to x + e_a if that node is fluid; half-way bounce-back into the
       // opposite slot of this node if it is solid; dropped if it lies beyond an open edge
-      int k;
-      int slot;
-      if (a == 0) {
-        k = kn;
-        slot = 0;
-      } else {
+      int k = pn_own, slot = a;
+      if (a != 0) {
         const int xr = xs + ex(a), yr = ys + ey(a);
         if ((!px && (xr < 0 || xr >= nx)) || (!py && (yr < 0 || yr >= ny))) continue;
         if (sfl[(c3y + ey(a)) * W3 + c3x + ex(a)] & F_SOLID) {
-          k = kn;
           slot = opp(a);
         } else {
-          k = sym[c3y + ey(a)] * pitch + sxm[c3x + ex(a)];
-          slot = a;
+          k = pop_node(sxm[c3x + ex(a)], sym[c3y + ey(a)], pitch);
         }
       }
-      encode<S, T>(oR, oB, wgt<T>(a) * r0, lo, hi);
-      dst[slot * plane + k] = Store<S>::cv(lo);
-      dst[(9 + slot) * plane + k] = Store<S>::cv(hi);
+      store_pair<S>(dst + k + slot * kDir, oR, oB, wgt<T>(a) * r0);
     }
   }
 }
@@ -434,15 +426,16 @@ __global__ void __launch_bounds__(32 * TY, sizeof(typename Store<S>::T) == 4 ? 1
 // NTH threads owns NTH - 4 interior columns plus two halo columns on each side and walks up
 // a range of rows.  Per row r it loads the populations of row r and forms rho^N(r); then
 // n(r-1) (needs rho^N of rows r-2..r); then collides row r-2 (needs n of rows r-3..r-1) and
-// pushes it.  Halo work exists only in x ((NTH)/(NTH-4) loads per node), each node is
-// loaded once for rho^N and once more (from L2) for its collision, and the rows of the
-// stencil live in small shared-memory rings.
+// pushes it.  Halo work exists only in x (NTH / (NTH-4) loads per node); each node is loaded
+// once for rho^N and once more (from L2) for its collision; the rows of the stencil live in
+// small shared-memory rings whose slots, like the wrapped row indices, advance by one per row.
 struct SweepArgs {
   const LatDev* lats;
   const int4* strips;     // (lattice, x0 = first interior column, y_begin, y_end)
   const void* src;
   void* dst;
   const uint8_t* flags;
+  const uint8_t* nbmask;  // bit a-1 set: the neighbour in direction a (1..8) is solid
   const void* wall;
   long long node_total;
 };
@@ -463,12 +456,13 @@ __global__ void __launch_bounds__(NTH, sizeof(typename Store<S>::T) == 4 ? 1024 
   const int t = threadIdx.x;
   if (t == 0) sL = A.lats[sp.x];
   __syncthreads();
-  const int nx = sL.nx, ny = sL.ny, pitch = sL.pitch, plane = int(sL.plane);
+  const int nx = sL.nx, ny = sL.ny, pitch = sL.pitch;
   const bool px = sL.bcx == BC_PERIODIC, py = sL.bcy == BC_PERIODIC, inout = sL.bcx == BC_INOUT;
   const T r0 = T(sL.rho0), u_in = T(sL.u_in), rho_out = T(sL.rho_out), eps = T(sL.grad_eps);
   const T sigma = T(sL.sigma), beta = T(sL.beta), se = T(sL.s_e), seps = T(sL.s_eps), sq = T(sL.s_q);
   const T hR = T(sL.h_inv_nuR), hB = T(sL.h_inv_nuB);
   const uint8_t* __restrict__ fl = A.flags + sL.node_off;
+  const uint8_t* __restrict__ nbm = A.nbmask + sL.node_off;
   const S* __restrict__ src = static_cast<const S*>(A.src) + sL.pop_off;
   S* __restrict__ dst = static_cast<S*>(A.dst) + sL.pop_off;
   const T* __restrict__ wall = static_cast<const T*>(A.wall) + sL.node_off;
@@ -481,9 +475,22 @@ __global__ void __launch_bounds__(NTH, sizeof(typename Store<S>::T) == 4 ? 1024 
   // a column beyond a non-periodic edge is a ghost copy of the edge column: its n is
   // evaluated at the slot of the column it copies (zero normal gradient)
   const int tc = px ? t : min(max(t + xm - cx, 1), NTH - 2);
+  const int kxs = wrap_or_clamp(sp.y - 2 + tc, nx, px);  // column of the stage-2 slot
   const bool interior = t >= 2 && t < NTH - 2 && cx < nx;
   const int ys = sp.z, ye = sp.w;
+  // element offsets of the neighbouring columns within a row of 32-node segments
+  const int colk[3] = {(xl >> 5) * kSeg + (xl & 31) * 2, (xm >> 5) * kSeg + (xm & 31) * 2,
+                       (xr >> 5) * kSeg + (xr & 31) * 2};
+  const int rowseg = (pitch >> 5) * kSeg;            // elements of one lattice row
 
+  auto map_row = [&](int v) {
+    if (py) {
+      while (v < 0) v += ny;
+      while (v >= ny) v -= ny;
+      return v;
+    }
+    return v < 0 ? 0 : (v >= ny ? ny - 1 : v);
+  };
   auto indicator = [&](const T fr_[9], const T fb_[9], T& sr, T& sb) -> T {
     sr = fr_[0];
     sb = fb_[0];
@@ -500,16 +507,36 @@ __global__ void __launch_bounds__(NTH, sizeof(typename Store<S>::T) == 4 ? 1024 
     }
   };
 
+  int ym3 = 0, ym2 = 0, ym1 = 0, ym0 = 0;       // mapped rows r-3 .. r
+  int s4 = 0, s3 = 1, s2 = 2, s1 = 3, s0 = 4;   // rho^N/flag ring slots of rows r-4 .. r
+  int n2 = 0, n1 = 1, n0 = 2;                   // n ring slots of rows r-3, r-2, r-1
+
   for (int r = ys - 2; r <= ye + 1; ++r) {
-    const int s0 = ((r % RR) + RR) % RR;
+    {
+      const int t4 = s4;
+      s4 = s3;
+      s3 = s2;
+      s2 = s1;
+      s1 = s0;
+      s0 = t4;
+      if (r == ys - 2) {
+        ym3 = map_row(r - 3);
+        ym2 = map_row(r - 2);
+        ym1 = map_row(r - 1);
+      } else {
+        ym3 = ym2;
+        ym2 = ym1;
+        ym1 = ym0;
+      }
+      ym0 = map_row(r);
+    }
     // ---- stage 1: rho^N and flags of row r
     {
-      const int ym = wrap_or_clamp(r, ny, py);
-      const uint8_t f = fl[ym * pitch + xm];
+      const uint8_t f = fl[ym0 * pitch + xm];
       T v = T(0);
       if (!(f & F_SOLID)) {
         T fr[9], fb[9], a1, a2;
-        load_raw<S>(src + ym * pitch + xm, plane, r0, fr, fb);
+        load_raw<S>(src + ym0 * rowseg + colk[1], r0, fr, fb);
         if (inout) zou_he<T>(xm, nx, u_in, rho_out, fr, fb);
         v = indicator(fr, fb, a1, a2);
       }
@@ -518,27 +545,29 @@ __global__ void __launch_bounds__(NTH, sizeof(typename Store<S>::T) == 4 ? 1024 
     }
     __syncthreads();
     // ---- stage 2: grad rho^N and n of row q = r - 1 (columns 1 .. NTH-2)
-    const int q = r - 1;
-    if (q >= ys - 1 && t >= 1 && t < NTH - 1) {
-      const int sq0 = ((q % RR) + RR) % RR, sqm = ((q - 1) % RR + RR) % RR, sqp = ((q + 1) % RR + RR) % RR;
-      const int qn = ((q % RN) + RN) % RN;
-      const uint8_t f = sfl[sq0][tc];
-      const int ymq = wrap_or_clamp(q, ny, py);
+    {
+      const int tn = n2;  // the slot of row r-4 is reused for row r-1
+      n2 = n1;
+      n1 = n0;
+      n0 = tn;
+    }
+    if (r - 1 >= ys - 1 && t >= 1 && t < NTH - 1) {
+      const uint8_t f = sfl[s1][tc];
       T ax = T(0), ay = T(0), nxv = T(0), nyv = T(0);
       if (!(f & F_SOLID)) {
         if (f & F_OFB) {
-          const int k = ymq * pitch + wrap_or_clamp(sp.y - 2 + tc, nx, px);
+          const int k = ym1 * pitch + kxs;
           ax = wall[k];
           ay = wall[NTOT + k];
           nxv = wall[2 * NTOT + k];
           nyv = wall[3 * NTOT + k];
         } else {
-          const T* rm = srn[sqm];
-          const T* r0w = srn[sq0];
-          const T* rp = srn[sqp];
-          // Eq. 28 over the 8 neighbours, direction order 1..8
+          const T* rm = srn[s2];
+          const T* rc = srn[s1];
+          const T* rp = srn[s0];
+          // Eq. 28 over the 8 neighbours
           const T w1 = T(1.0 / 9.0), w2 = T(1.0 / 36.0);
-          ax = w1 * (r0w[tc + 1] - r0w[tc - 1]) + w2 * (rp[tc + 1] - rp[tc - 1] + rm[tc + 1] - rm[tc - 1]);
+          ax = w1 * (rc[tc + 1] - rc[tc - 1]) + w2 * (rp[tc + 1] - rp[tc - 1] + rm[tc + 1] - rm[tc - 1]);
           ay = w1 * (rp[tc] - rm[tc]) + w2 * (rp[tc + 1] + rp[tc - 1] - rm[tc - 1] - rm[tc + 1]);
           ax *= T(3);
           ay *= T(3);
@@ -560,11 +589,12 @@ __global__ void __launch_bounds__(NTH, sizeof(typename Store<S>::T) == 4 ? 1024 
       } else if (f & F_OSOLID) {
         // virtual n (Eq. 29) from the stored n of the neighbouring outermost fluid nodes
         T vx = T(0), vy = T(0), den = T(0);
+        const int yr[3] = {ym2, ym1, ym0};
+        const int sr[3] = {s2, s1, s0};
 #pragma unroll
         for (int b = 1; b < 9; ++b) {
-          const int sb = ey(b) == 0 ? sq0 : (ey(b) > 0 ? sqp : sqm);
-          if (!(sfl[sb][tc + ex(b)] & F_SOLID)) {
-            const int k2 = wrap_or_clamp(q + ey(b), ny, py) * pitch + wrap_or_clamp(sp.y - 2 + tc + ex(b), nx, px);
+          if (!(sfl[sr[ey(b) + 1]][tc + ex(b)] & F_SOLID)) {
+            const int k2 = yr[ey(b) + 1] * pitch + wrap_or_clamp(sp.y - 2 + tc + ex(b), nx, px);
             vx += wgt<T>(b) * wall[2 * NTOT + k2];
             vy += wgt<T>(b) * wall[3 * NTOT + k2];
             den += wgt<T>(b);
@@ -575,29 +605,27 @@ __global__ void __launch_bounds__(NTH, sizeof(typename Store<S>::T) == 4 ? 1024 
           nyv = vy / den;
         }
       }
-      snx[qn][t] = nxv;
-      sny[qn][t] = nyv;
-      sgx[qn][t] = ax;
-      sgy[qn][t] = ay;
+      snx[n0][t] = nxv;
+      sny[n0][t] = nyv;
+      sgx[n0][t] = ax;
+      sgy[n0][t] = ay;
     }
     __syncthreads();
-    // ---- stage 3: collide and push row p = r - 2
+    // ---- stage 3: collide and push row p = r - 2 (flags slot s2, n rows in n2, n1, n0)
     const int p = r - 2;
     if (p < ys || !interior) continue;
-    const int sp0 = ((p % RR) + RR) % RR;
-    const uint8_t myf = sfl[sp0][t];
+    const uint8_t myf = sfl[s2][t];
     if (myf & F_SOLID) continue;
-    const int pn = ((p % RN) + RN) % RN, pnm = ((p - 1) % RN + RN) % RN, pnp = ((p + 1) % RN + RN) % RN;
-    const int ym = wrap_or_clamp(p, ny, py);
-    const int kn = ym * pitch + xm;
+    const int kn = ym2 * rowseg + colk[1];
+    const uint8_t mask = nbm[ym2 * pitch + xm];
     T fr[9], fb[9];
-    load_raw<S>(src + kn, plane, r0, fr, fb);
+    load_raw<S>(src + kn, r0, fr, fb);
     if (inout) zou_he<T>(xm, nx, u_in, rho_out, fr, fb);
     T rhoR, rhoB;
     const T rn = indicator(fr, fb, rhoR, rhoB);
     // grad n (Eq. 28) and curvature (Eq. 13)
-    const T* nxm = snx[pnm]; const T* nx0 = snx[pn]; const T* nxp = snx[pnp];
-    const T* nym = sny[pnm]; const T* ny0 = sny[pn]; const T* nyp = sny[pnp];
+    const T* nxm = snx[n2]; const T* nx0 = snx[n1]; const T* nxp = snx[n0];
+    const T* nym = sny[n2]; const T* ny0 = sny[n1]; const T* nyp = sny[n0];
     const T w1 = T(1.0 / 9.0), w2 = T(1.0 / 36.0);
     const T dxx = w1 * (nx0[t + 1] - nx0[t - 1]) + w2 * (nxp[t + 1] - nxp[t - 1] + nxm[t + 1] - nxm[t - 1]);
     const T dxy = w1 * (nxp[t] - nxm[t]) + w2 * (nxp[t + 1] + nxp[t - 1] - nxm[t - 1] - nxm[t + 1]);
@@ -606,8 +634,8 @@ __global__ void __launch_bounds__(NTH, sizeof(typename Store<S>::T) == 4 ? 1024 
     const T nxo = nx0[t], nyo = ny0[t];
     const T kappa = T(3) * (-nxo * nxo * dyy - nyo * nyo * dxx + nxo * nyo * (dxy + dyx));
     const T hsk = T(0.5) * sigma * kappa;
-    const T Fx = hsk * sgx[pn][t];
-    const T Fy = hsk * sgy[pn][t];
+    const T Fx = hsk * sgx[n1][t];
+    const T Fy = hsk * sgy[n1][t];
 
     T f[9];
 #pragma unroll
@@ -654,30 +682,34 @@ __global__ void __launch_bounds__(NTH, sizeof(typename Store<S>::T) == 4 ? 1024 
     fp[8] = f[8] - (c58 + ajx + aqx - ajy - aqy - axy);
     const T cR = rhoR * irho, cB = rhoB * irho;
     const T pc = beta * rhoR * rhoB * irho;
-    // destinations: rows p-1, p, p+1 and columns cx-1, cx, cx+1
-    const int rowk[3] = {wrap_or_clamp(p - 1, ny, py) * pitch, ym * pitch, wrap_or_clamp(p + 1, ny, py) * pitch};
-    const int colk[3] = {xl, xm, xr};
-    const int rings[3] = {((p - 1) % RR + RR) % RR, sp0, ((p + 1) % RR + RR) % RR};
+    // streaming (Eq. 15) to rows p-1, p, p+1 and columns cx-1, cx, cx+1
+    const int rowk[3] = {ym3 * rowseg, ym2 * rowseg, ym1 * rowseg};
+    if (mask == 0 && !(myf & F_EDGE)) {
+      // bulk node: every neighbour is a fluid node of the lattice
 #pragma unroll
-    for (int a = 0; a < 9; ++a) {
-      const T en = T(ex(a)) * nxo + T(ey(a)) * nyo;
-      const T pert = pc * wgt<T>(a) * en;
-      const T oR = cR * fp[a] + pert;
-      const T oB = cB * fp[a] - pert;
-      int k = kn, slot = a;
-      if (a != 0) {
-        const int xrw = cx + ex(a), yrw = p + ey(a);
-        if ((!px && (xrw < 0 || xrw >= nx)) || (!py && (yrw < 0 || yrw >= ny))) continue;
-        if (sfl[rings[ey(a) + 1]][t + ex(a)] & F_SOLID) {
-          slot = opp(a);
-        } else {
-          k = rowk[ey(a) + 1] + colk[ex(a) + 1];
-        }
+      for (int a = 0; a < 9; ++a) {
+        const T pert = pc * wgt<T>(a) * (T(ex(a)) * nxo + T(ey(a)) * nyo);
+        store_pair<S>(dst + rowk[ey(a) + 1] + colk[ex(a) + 1] + a * kDir, cR * fp[a] + pert, cB * fp[a] - pert,
+                      wgt<T>(a) * r0);
       }
-      T lo, hi;
-      encode<S, T>(oR, oB, wgt<T>(a) * r0, lo, hi);
-      dst[slot * plane + k] = Store<S>::cv(lo);
-      dst[(9 + slot) * plane + k] = Store<S>::cv(hi);
+    } else {
+      // half-way bounce-back into the opposite slot where the neighbour is solid; dropped
+      // where it lies beyond an open edge
+      const bool okx[3] = {px || cx - 1 >= 0, true, px || cx + 1 < nx};
+      const bool oky[3] = {py || p - 1 >= 0, true, py || p + 1 < ny};
+#pragma unroll
+      for (int a = 0; a < 9; ++a) {
+        const T pert = pc * wgt<T>(a) * (T(ex(a)) * nxo + T(ey(a)) * nyo);
+        const T oR = cR * fp[a] + pert;
+        const T oB = cB * fp[a] - pert;
+        int k = kn + a * kDir;
+        if (a != 0) {
+          if (!(okx[ex(a) + 1] && oky[ey(a) + 1])) continue;
+          if (mask & (1u << (a - 1))) k = kn + opp(a) * kDir;
+          else k = rowk[ey(a) + 1] + colk[ex(a) + 1] + a * kDir;
+        }
+        store_pair<S>(dst + k, oR, oB, wgt<T>(a) * r0);
+      }
     }
   }
 }
@@ -699,10 +731,7 @@ __global__ void k_to_storage(const LatDev* __restrict__ lats, int lat, const dou
   const bool solid = flags[L.node_off + k] & F_SOLID;
   const T fr = solid ? T(0) : T(in[i]);
   const T fb = solid ? T(0) : T(in[9 * nn + i]);
-  T lo, hi;
-  encode<S, T>(fr, fb, solid ? T(0) : wgt<T>(a) * T(L.rho0), lo, hi);
-  pool[L.pop_off + (long long)a * L.plane + k] = Store<S>::cv(lo);
-  pool[L.pop_off + (long long)(9 + a) * L.plane + k] = Store<S>::cv(hi);
+  store_pair<S>(pool + L.pop_off + pop_node(x, y, L.pitch) + a * kDir, fr, fb, solid ? T(0) : wgt<T>(a) * T(L.rho0));
 }
 
 // host layout out <- the post-streaming state as a step reads it (Zou-He applied on open edges)
@@ -721,7 +750,7 @@ __global__ void k_from_storage(const LatDev* __restrict__ lats, int lat, const S
 #pragma unroll
     for (int a = 0; a < 9; ++a) fr[a] = fb[a] = T(0);
   } else {
-    load_node<S>(L, pool, k, x, fr, fb);
+    load_node<S>(L, pool, x, y, fr, fb);
   }
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
@@ -753,7 +782,7 @@ static cudaError_t launch_all(const LaunchStep& p, cudaStream_t st) {
   rec(4);
   if (p.sweep && p.macro == nullptr) {
     if (p.nstrips > 0) {
-      SweepArgs B{p.lats, p.strips, p.src, p.dst, p.flags, p.wall, p.node_total};
+      SweepArgs B{p.lats, p.strips, p.src, p.dst, p.flags, p.nbmask, p.wall, p.node_total};
       k_sweep<S, kSweepThreads><<<p.nstrips, kSweepThreads, 0, st>>>(B);
     }
   } else if (p.ntiles > 0) {
