@@ -530,15 +530,26 @@ __global__ void __launch_bounds__(NTH, sizeof(typename Store<S>::T) == 4 ? 1024 
       }
       ym0 = map_row(r);
     }
+    // the collision of row p = r - 2 (stage 3) needs that row's populations: issue their loads
+    // now, so that they travel while stages 1 and 2 run
+    const int p = r - 2;
+    const bool collide = p >= ys && interior && !(sfl[s2][t] & F_SOLID);
+    const int kn = ym2 * rowseg + colk[1];
+    T fr[9], fb[9];
+    uint8_t mask = 0;
+    if (collide) {
+      load_raw<S>(src + kn, r0, fr, fb);
+      mask = nbm[ym2 * pitch + xm];
+    }
     // ---- stage 1: rho^N and flags of row r
     {
       const uint8_t f = fl[ym0 * pitch + xm];
       T v = T(0);
       if (!(f & F_SOLID)) {
-        T fr[9], fb[9], a1, a2;
-        load_raw<S>(src + ym0 * rowseg + colk[1], r0, fr, fb);
-        if (inout) zou_he<T>(xm, nx, u_in, rho_out, fr, fb);
-        v = indicator(fr, fb, a1, a2);
+        T hr[9], hb[9], a1, a2;
+        load_raw<S>(src + ym0 * rowseg + colk[1], r0, hr, hb);
+        if (inout) zou_he<T>(xm, nx, u_in, rho_out, hr, hb);
+        v = indicator(hr, hb, a1, a2);
       }
       srn[s0][t] = v;
       sfl[s0][t] = f;
@@ -612,14 +623,8 @@ __global__ void __launch_bounds__(NTH, sizeof(typename Store<S>::T) == 4 ? 1024 
     }
     __syncthreads();
     // ---- stage 3: collide and push row p = r - 2 (flags slot s2, n rows in n2, n1, n0)
-    const int p = r - 2;
-    if (p < ys || !interior) continue;
+    if (!collide) continue;
     const uint8_t myf = sfl[s2][t];
-    if (myf & F_SOLID) continue;
-    const int kn = ym2 * rowseg + colk[1];
-    const uint8_t mask = nbm[ym2 * pitch + xm];
-    T fr[9], fb[9];
-    load_raw<S>(src + kn, r0, fr, fb);
     if (inout) zou_he<T>(xm, nx, u_in, rho_out, fr, fb);
     T rhoR, rhoB;
     const T rn = indicator(fr, fb, rhoR, rhoB);
