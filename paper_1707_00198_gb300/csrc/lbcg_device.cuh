@@ -24,6 +24,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cstring>
+
 namespace lbcg {
 
 // node flags
@@ -114,6 +116,13 @@ template <> struct Store<__half> {
   __device__ static void stp(__half* p, float lo, float hi) {
     *reinterpret_cast<__half2*>(p) = __floats2half2_rn(lo, hi);
   }
+  __device__ static void unpack(uint32_t w, float& lo, float& hi) {
+    __half2 h;
+    memcpy(&h, &w, 4);
+    const float2 v = __half22float2(h);
+    lo = v.x;
+    hi = v.y;
+  }
 };
 template <> struct Store<__nv_bfloat16> {
   using T = float;
@@ -125,6 +134,13 @@ template <> struct Store<__nv_bfloat16> {
   }
   __device__ static void stp(__nv_bfloat16* p, float lo, float hi) {
     *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(lo, hi);
+  }
+  __device__ static void unpack(uint32_t w, float& lo, float& hi) {
+    __nv_bfloat162 h;
+    memcpy(&h, &w, 4);
+    const float2 v = __bfloat1622float2(h);
+    lo = v.x;
+    hi = v.y;
   }
 };
 
@@ -250,6 +266,41 @@ __device__ __forceinline__ void store_pair(S* p, typename Store<S>::T fr, typena
   encode<S, T>(fr, fb, wr0, lo, hi);
   Store<S>::stp(p, lo, hi);
 }
+
+// A node's nine stored pairs as loaded, before decoding: for 16-bit storage each pair is one
+// 32-bit word, so a prefetched node costs nine registers instead of eighteen.
+template <typename S>
+struct RawNode {
+  typename Store<S>::T lo[9], hi[9];
+  __device__ __forceinline__ void load(const S* __restrict__ base) {
+#pragma unroll
+    for (int a = 0; a < 9; ++a) Store<S>::ldp(base + a * kDir, lo[a], hi[a]);
+  }
+  __device__ __forceinline__ void decode_to(typename Store<S>::T r0, typename Store<S>::T fr[9],
+                                            typename Store<S>::T fb[9]) const {
+    using T = typename Store<S>::T;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) decode<S, T>(lo[a], hi[a], wgt<T>(a) * r0, fr[a], fb[a]);
+  }
+};
+template <typename S>
+struct RawNode16 {
+  uint32_t w[9];
+  __device__ __forceinline__ void load(const S* __restrict__ base) {
+#pragma unroll
+    for (int a = 0; a < 9; ++a) w[a] = __ldg(reinterpret_cast<const unsigned int*>(base + a * kDir));
+  }
+  __device__ __forceinline__ void decode_to(float r0, float fr[9], float fb[9]) const {
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+      float lo, hi;
+      Store<S>::unpack(w[a], lo, hi);
+      decode<S, float>(lo, hi, wgt<float>(a) * r0, fr[a], fb[a]);
+    }
+  }
+};
+template <> struct RawNode<__half> : RawNode16<__half> {};
+template <> struct RawNode<__nv_bfloat16> : RawNode16<__nv_bfloat16> {};
 
 // Post-streaming populations of fluid node (x, y), stored at the node itself (streaming and
 // bounce-back happened in the previous step's push), with the Zou-He conditions applied on

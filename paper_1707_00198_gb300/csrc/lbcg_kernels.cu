@@ -535,10 +535,10 @@ __global__ void __launch_bounds__(NTH, sizeof(typename Store<S>::T) == 4 ? 1024 
     const int p = r - 2;
     const bool collide = p >= ys && interior && !(sfl[s2][t] & F_SOLID);
     const int kn = ym2 * rowseg + colk[1];
-    T fr[9], fb[9];
+    RawNode<S> pre;
     uint8_t mask = 0;
     if (collide) {
-      load_raw<S>(src + kn, r0, fr, fb);
+      pre.load(src + kn);
       mask = nbm[ym2 * pitch + xm];
     }
     // ---- stage 1: rho^N and flags of row r
@@ -625,6 +625,8 @@ __global__ void __launch_bounds__(NTH, sizeof(typename Store<S>::T) == 4 ? 1024 
     // ---- stage 3: collide and push row p = r - 2 (flags slot s2, n rows in n2, n1, n0)
     if (!collide) continue;
     const uint8_t myf = sfl[s2][t];
+    T fr[9], fb[9];
+    pre.decode_to(r0, fr, fb);
     if (inout) zou_he<T>(xm, nx, u_in, rho_out, fr, fb);
     T rhoR, rhoB;
     const T rn = indicator(fr, fb, rhoR, rhoB);
