@@ -421,6 +421,27 @@ __global__ void __launch_bounds__(32 * TY, sizeof(typename Store<S>::T) == 4 ? 1
   }
 }
 
+// ------------------------------------------------------------------ pair arithmetic
+// (x, y) pairs; on the FP32 path they map onto the packed two-lane FP32 instructions of
+// sm_100+ (__ffma2_rn and friends), on the FP64 path onto two scalar operations.
+template <typename T> struct Pair;
+template <> struct Pair<float> {
+  using V = float2;
+  __device__ static V mk(float a, float b) { return make_float2(a, b); }
+  __device__ static V add(V a, V b) { return __fadd2_rn(a, b); }
+  __device__ static V sub(V a, V b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+  __device__ static V mul(V a, V b) { return __fmul2_rn(a, b); }
+  __device__ static V fma(V a, V b, V c) { return __ffma2_rn(a, b, c); }
+};
+template <> struct Pair<double> {
+  using V = double2;
+  __device__ static V mk(double a, double b) { return make_double2(a, b); }
+  __device__ static V add(V a, V b) { return make_double2(a.x + b.x, a.y + b.y); }
+  __device__ static V sub(V a, V b) { return make_double2(a.x - b.x, a.y - b.y); }
+  __device__ static V mul(V a, V b) { return make_double2(a.x * b.x, a.y * b.y); }
+  __device__ static V fma(V a, V b, V c) { return make_double2(::fma(a.x, b.x, c.x), ::fma(a.y, b.y, c.y)); }
+};
+
 // ------------------------------------------------------------------ k_sweep
 // The same time step as k_step, organised as a sweep along y over column strips: a block of
 // NTH threads owns NTH - 4 interior columns plus two halo columns on each side and walks up
@@ -447,9 +468,11 @@ __global__ void __launch_bounds__(NTH, sizeof(typename Store<S>::T) == 4 ? 1024 
   constexpr bool kF32 = sizeof(T) == 4;
   constexpr int RR = 5;   // rho^N / flags ring (rows r-4 .. r)
   constexpr int RN = 3;   // n, grad ring (rows r-3 .. r-1)
+  using P = Pair<T>;
+  using V = typename P::V;
   __shared__ T srn[RR][NTH];
   __shared__ uint8_t sfl[RR][NTH];
-  __shared__ T snx[RN][NTH], sny[RN][NTH], sgx[RN][NTH], sgy[RN][NTH];
+  __shared__ V sn[RN][NTH], sg[RN][NTH];   // (n_x, n_y) and (d_x rho^N, d_y rho^N)
   __shared__ LatDev sL;
 
   const int4 sp = A.strips[blockIdx.x];
@@ -616,10 +639,8 @@ __global__ void __launch_bounds__(NTH, sizeof(typename Store<S>::T) == 4 ? 1024 
           nyv = vy / den;
         }
       }
-      snx[n0][t] = nxv;
-      sny[n0][t] = nyv;
-      sgx[n0][t] = ax;
-      sgy[n0][t] = ay;
+      sn[n0][t] = P::mk(nxv, nyv);
+      sg[n0][t] = P::mk(ax, ay);
     }
     __syncthreads();
     // ---- stage 3: collide and push row p = r - 2 (flags slot s2, n rows in n2, n1, n0)
@@ -630,19 +651,24 @@ __global__ void __launch_bounds__(NTH, sizeof(typename Store<S>::T) == 4 ? 1024 
     if (inout) zou_he<T>(xm, nx, u_in, rho_out, fr, fb);
     T rhoR, rhoB;
     const T rn = indicator(fr, fb, rhoR, rhoB);
-    // grad n (Eq. 28) and curvature (Eq. 13)
-    const T* nxm = snx[n2]; const T* nx0 = snx[n1]; const T* nxp = snx[n0];
-    const T* nym = sny[n2]; const T* ny0 = sny[n1]; const T* nyp = sny[n0];
-    const T w1 = T(1.0 / 9.0), w2 = T(1.0 / 36.0);
-    const T dxx = w1 * (nx0[t + 1] - nx0[t - 1]) + w2 * (nxp[t + 1] - nxp[t - 1] + nxm[t + 1] - nxm[t - 1]);
-    const T dxy = w1 * (nxp[t] - nxm[t]) + w2 * (nxp[t + 1] + nxp[t - 1] - nxm[t - 1] - nxm[t + 1]);
-    const T dyx = w1 * (ny0[t + 1] - ny0[t - 1]) + w2 * (nyp[t + 1] - nyp[t - 1] + nym[t + 1] - nym[t - 1]);
-    const T dyy = w1 * (nyp[t] - nym[t]) + w2 * (nyp[t + 1] + nyp[t - 1] - nym[t - 1] - nym[t + 1]);
-    const T nxo = nx0[t], nyo = ny0[t];
+    // grad n (Eq. 28) on (n_x, n_y) pairs, then the curvature (Eq. 13)
+    const V* nm = sn[n2];
+    const V* n0v = sn[n1];
+    const V* np = sn[n0];
+    const V W1 = P::mk(T(1.0 / 9.0), T(1.0 / 9.0)), W2 = P::mk(T(1.0 / 36.0), T(1.0 / 36.0));
+    const V nm_l = nm[t - 1], nm_c = nm[t], nm_r = nm[t + 1];
+    const V n0_l = n0v[t - 1], n0_c = n0v[t], n0_r = n0v[t + 1];
+    const V np_l = np[t - 1], np_c = np[t], np_r = np[t + 1];
+    // d_x (n_x, n_y) and d_y (n_x, n_y)
+    const V dX = P::fma(W1, P::sub(n0_r, n0_l), P::mul(W2, P::add(P::sub(np_r, np_l), P::sub(nm_r, nm_l))));
+    const V dY = P::fma(W1, P::sub(np_c, nm_c), P::mul(W2, P::sub(P::add(np_r, np_l), P::add(nm_l, nm_r))));
+    const T dxx = dX.x, dyx = dX.y, dxy = dY.x, dyy = dY.y;
+    const T nxo = n0_c.x, nyo = n0_c.y;
     const T kappa = T(3) * (-nxo * nxo * dyy - nyo * nyo * dxx + nxo * nyo * (dxy + dyx));
     const T hsk = T(0.5) * sigma * kappa;
-    const T Fx = hsk * sgx[n1][t];
-    const T Fy = hsk * sgy[n1][t];
+    const V gv = sg[n1][t];
+    const T Fx = hsk * gv.x;
+    const T Fy = hsk * gv.y;
 
     T f[9];
 #pragma unroll
@@ -687,7 +713,7 @@ __global__ void __launch_bounds__(NTH, sizeof(typename Store<S>::T) == 4 ? 1024 
     fp[6] = f[6] - (c58 - ajx - aqx + ajy + aqy - axy);
     fp[7] = f[7] - (c58 - ajx - aqx - ajy - aqy + axy);
     fp[8] = f[8] - (c58 + ajx + aqx - ajy - aqy - axy);
-    const T cR = rhoR * irho, cB = rhoB * irho;
+    const T cR = rhoR * irho;
     const T pc = beta * rhoR * rhoB * irho;
     // streaming (Eq. 15) to rows p-1, p, p+1 and columns cx-1, cx, cx+1
     const int rowk[3] = {ym3 * rowseg, ym2 * rowseg, ym1 * rowseg};
@@ -696,8 +722,8 @@ __global__ void __launch_bounds__(NTH, sizeof(typename Store<S>::T) == 4 ? 1024 
 #pragma unroll
       for (int a = 0; a < 9; ++a) {
         const T pert = pc * wgt<T>(a) * (T(ex(a)) * nxo + T(ey(a)) * nyo);
-        store_pair<S>(dst + rowk[ey(a) + 1] + colk[ex(a) + 1] + a * kDir, cR * fp[a] + pert, cB * fp[a] - pert,
-                      wgt<T>(a) * r0);
+        const T oR = cR * fp[a] + pert;   // Eq. 14; the blue share is the rest of f'_a
+        store_pair<S>(dst + rowk[ey(a) + 1] + colk[ex(a) + 1] + a * kDir, oR, fp[a] - oR, wgt<T>(a) * r0);
       }
     } else {
       // half-way bounce-back into the opposite slot where the neighbour is solid; dropped
@@ -708,7 +734,7 @@ __global__ void __launch_bounds__(NTH, sizeof(typename Store<S>::T) == 4 ? 1024 
       for (int a = 0; a < 9; ++a) {
         const T pert = pc * wgt<T>(a) * (T(ex(a)) * nxo + T(ey(a)) * nyo);
         const T oR = cR * fp[a] + pert;
-        const T oB = cB * fp[a] - pert;
+        const T oB = fp[a] - oR;
         int k = kn + a * kDir;
         if (a != 0) {
           if (!(okx[ex(a) + 1] && oky[ey(a) + 1])) continue;
