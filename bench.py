@@ -307,11 +307,12 @@ def run_ours(args):
     achieved = alg_bytes / (step_ms / 1e3) / 1e9
     peaks = measured_peaks()
     peak, peak_src = (peaks["hbm_gbs"], "measured") if peaks and "hbm_gbs" in peaks else (6800.0, "fallback")
-    traffic = recorded_traffic(f"k_step<{args.precision},ty{args.ty or 8}>", nf)
+    kname = f"k_step<{args.precision},ty{args.ty}>" if args.ty else f"k_sweep<{args.precision}>"
+    traffic = recorded_traffic(kname, nf)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": traffic, "kernel": "k_step", "peak_source": peak_src,
+            "traffic": traffic, "kernel": kname, "peak_source": peak_src,
             "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": step_ms,
-            "kernel_ms_share": {"k_band": kms[0] / ms, "k_wall": kms[1] / ms, "k_step": kms[2] / ms}}
+            "kernel_ms_share": {"k_band": kms[0] / ms, "k_wall": kms[1] / ms, "step kernel": kms[2] / ms}}
     whole_gbs = alg_bytes * args.steps / (ms / 1e3) / 1e9
 
     # ---- end to end through the C ABI with host buffers (pinned): upload state, step, download
@@ -357,7 +358,7 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
                 "config": {"workload": args.workload, "description": desc, "lattices": len(geoms), "nodes": nodes,
-                           "tile": f"32x{args.ty or 8}",
+                           "schedule": f"tiles 32x{args.ty}" if args.ty else "y-sweep, 124-column strips",
                            "fluid_nodes_per_gpu": nf, "precision": args.precision,
                            "state_bytes": sb, "l2": "flushed before every timed step" if flush is not None
                            else "inputs larger than L2", "mlups_counts": "fluid-node updates"},
