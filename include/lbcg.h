@@ -166,6 +166,31 @@ lbcg_status lbcg_download_state(lbcg_handle* h, void* host_out, size_t bytes);
 lbcg_status lbcg_set_sweep(lbcg_handle* h, int32_t rows);
 lbcg_status lbcg_set_tile(lbcg_handle* h, int32_t ty);
 
+/* Gradients by the discrete adjoint (reverse mode) of the step.  From the handle's current
+ * state, lbcg_adjoint runs `nsteps` steps forward (storing the state every `checkpoint`
+ * steps; the handle ends at step T = nsteps), evaluates the objective J of the state at
+ * T, then runs hand-written reverse kernels back to the start, recomputing each segment of
+ * states from its checkpoint.  It returns J and dJ/d sigma, dJ/d nu_R, dJ/d nu_B and
+ * dJ/d theta: the sum over outermost fluid nodes (a change of the global contact angle) and,
+ * if dJ_dtheta_node is not NULL, per node [ny*nx] (zero off the outermost fluid nodes).
+ * Objectives: LBCG_OBJ_WEIGHTED, J = sum_x weight(x) rho^N(x) (weight: host [ny*nx]);
+ * LBCG_OBJ_FINGER_LENGTH, J = x_tip - x_cl (Sec. III.D; rows as in lbcg_obs_spec), whose
+ * derivative is taken at the crossing cells found at T.  FP64 single-lattice handles only
+ * (else LBCG_E_UNSUPPORTED); device memory for nsteps/checkpoint + checkpoint + 2 states
+ * is allocated for the call and freed before it returns. */
+enum { LBCG_OBJ_WEIGHTED = 0, LBCG_OBJ_FINGER_LENGTH = 1 };
+typedef struct {
+  int64_t nsteps, checkpoint;
+  int32_t objective;
+  const double* weight;
+  int32_t tip_row0, tip_row1, cl_row0, cl_row1;
+} lbcg_adjoint_spec;
+typedef struct {
+  double J, dJ_dsigma, dJ_dnu_R, dJ_dnu_B, dJ_dtheta;
+  double* dJ_dtheta_node;
+} lbcg_grads;
+lbcg_status lbcg_adjoint(lbcg_handle* h, const lbcg_adjoint_spec* spec, lbcg_grads* out);
+
 /* Kernel timing with CUDA events on the handle's stream.  While enabled, lbcg_step launches
  * the kernels of each step directly (no graph) with an event recorded before and after each
  * of k_band, k_wall and k_step.  lbcg_kernel_times synchronises, returns in ms3[0..2] the

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblbcg.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ("lbcg_host.cu", "lbcg_kernels.cu", "lbcg_obs.cu", "lbcg_noalloc.cu")
+SOURCES = ("lbcg_host.cu", "lbcg_kernels.cu", "lbcg_obs.cu", "lbcg_noalloc.cu", "lbcg_adjoint.cu")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

@@ -75,6 +75,7 @@ struct lbcg_handle {
   double* d_obs = nullptr;   // partials then outputs
   cudaGraphExec_t graph = nullptr;
   std::vector<uint8_t> flags_host;
+  std::vector<OfbEntry> ofb_host;
   bool profiling = false;
   std::vector<cudaEvent_t> events;   // 6 per profiled step
   size_t events_used = 0;
@@ -464,6 +465,7 @@ lbcg_status lbcg_create_batch(int32_t n, const lbcg_geometry* geoms, const lbcg_
   }
   h->nband = int(band.size());
   h->nofb = int(ofb.size());
+  h->ofb_host = ofb;
   const size_t es = elem_size(precision), cs = compute_size(precision);
   auto alloc = [&](void** p, size_t bytes) { return cudaMalloc(p, std::max<size_t>(bytes, 16)) == cudaSuccess; };
   bool ok = alloc(&h->pool[0], 18 * (size_t)node_total * es) && alloc(&h->pool[1], 18 * (size_t)node_total * es) &&
@@ -733,6 +735,239 @@ lbcg_status lbcg_download_state(lbcg_handle* h, void* host_out, size_t bytes) {
   if (!host_out || bytes != lbcg_state_bytes(h)) return fail(LBCG_E_ARG, "state size mismatch");
   CK(h, cudaMemcpyAsync(host_out, h->pool[h->cur], bytes, cudaMemcpyDeviceToHost, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
+  return LBCG_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// device buffers of one adjoint run, freed on every exit path
+struct AdjBuffers {
+  std::vector<void*> ptrs;
+  ~AdjBuffers() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+  template <typename P>
+  bool get(P** p, size_t bytes) {
+    void* q = nullptr;
+    if (cudaMalloc(&q, std::max<size_t>(bytes, 16)) != cudaSuccess) return false;
+    ptrs.push_back(q);
+    *p = static_cast<P*>(q);
+    return true;
+  }
+};
+
+// d(first rho^N >= 0 -> < 0 change along profile p)/d p at the two nodes of the crossing
+bool crossing_derivative(const std::vector<double>& prof, int& i0, double& x, double& d0, double& d1) {
+  for (int i = 0; i + 1 < int(prof.size()); ++i)
+    if (prof[i] >= 0 && prof[i + 1] < 0) {
+      const double a = prof[i], b = prof[i + 1], den = a - b;
+      i0 = i;
+      x = i + a / den;
+      d0 = -b / (den * den);
+      d1 = a / (den * den);
+      return true;
+    }
+  return false;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbcg_status lbcg_adjoint(lbcg_handle* h, const lbcg_adjoint_spec* spec, lbcg_grads* out) {
+  lbcg_status s = check_handle(h);
+  if (s != LBCG_OK) return s;
+  if (!spec || !out) return fail(LBCG_E_ARG, "NULL spec or output");
+  if (h->prec != 0) return fail(LBCG_E_UNSUPPORTED, "the adjoint runs on FP64 handles");
+  if (h->lats.size() != 1) return fail(LBCG_E_UNSUPPORTED, "the adjoint runs on single-lattice handles");
+  if (spec->nsteps < 1 || spec->checkpoint < 1) return fail(LBCG_E_ARG, "nsteps and checkpoint must be >= 1");
+  if (spec->objective == LBCG_OBJ_WEIGHTED && !spec->weight) return fail(LBCG_E_ARG, "weighted objective needs weight");
+  if (spec->objective != LBCG_OBJ_WEIGHTED && spec->objective != LBCG_OBJ_FINGER_LENGTH)
+    return fail(LBCG_E_ARG, "unknown objective %d", spec->objective);
+  const LatHost& L = h->lats[0];
+  const int nx = L.nx, ny = L.ny, N = nx * ny;
+  const int64_t T = spec->nsteps, K = spec->checkpoint;
+  const int64_t nseg = (T + K - 1) / K;
+  const size_t sb = lbcg_state_bytes(h);
+  AdjBuffers B;
+  double *ckpt, *seg, *lamA, *lamB, *work, *c_dev;
+  double *nsx, *nsy, *ct, *st;
+  int* pick;
+  const int kWork = 9 + 9 + 3 + 2 + 2 + 2 + 4 + 9 + 9 + 2 + 2 + 2 + 2 + 2 + 2 + 4 + 4;  // N-sized arrays
+  if (!B.get(&ckpt, sb * (size_t)nseg) || !B.get(&seg, sb * (size_t)K) || !B.get(&lamA, 18 * (size_t)N * 8) ||
+      !B.get(&lamB, 18 * (size_t)N * 8) || !B.get(&work, (size_t)kWork * N * 8) || !B.get(&c_dev, (size_t)N * 8) ||
+      !B.get(&nsx, (size_t)N * 8) || !B.get(&nsy, (size_t)N * 8) || !B.get(&ct, (size_t)N * 8) ||
+      !B.get(&st, (size_t)N * 8) || !B.get(&pick, (size_t)N * 4))
+    return fail(LBCG_E_NOMEM, "adjoint buffers (%lld checkpoints of %zu bytes)", (long long)nseg, sb);
+  // compact normals and angles of the outermost fluid nodes
+  {
+    std::vector<double> a(N, 0.0), b(N, 0.0), c(N, 1.0), d(N, 0.0);
+    for (const OfbEntry& e : h->ofb_host) {
+      const int i = e.y * nx + e.x;
+      a[i] = e.nsx;
+      b[i] = e.nsy;
+      c[i] = e.cos_t;
+      d[i] = e.sin_t;
+    }
+    CK(h, cudaMemcpy(nsx, a.data(), N * 8, cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(nsy, b.data(), N * 8, cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(ct, c.data(), N * 8, cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(st, d.data(), N * 8, cudaMemcpyHostToDevice));
+  }
+  CK(h, cudaMemsetAsync(work, 0, (size_t)kWork * N * 8, h->stream));
+  AdjDev A{};
+  {
+    LatDev ld;
+    CK(h, cudaMemcpy(&ld, h->d_lats, sizeof(LatDev), cudaMemcpyDeviceToHost));
+    ld.pop_off = 0;  // the adjoint reads states from its own buffers
+    A.L = ld;
+  }
+  A.N = N;
+  A.flags = h->d_flags;
+  A.nsx = nsx;
+  A.nsy = nsy;
+  A.cos_t = ct;
+  A.sin_t = st;
+  A.pick = pick;
+  double* w = work;
+  auto take = [&](int n) {
+    double* p = w;
+    w += (size_t)n * N;
+    return p;
+  };
+  A.fr = take(9);
+  A.fb = take(9);
+  A.rr = take(1);
+  A.rb = take(1);
+  A.rn = take(1);
+  A.grx = take(1);
+  A.gry = take(1);
+  A.gcx = take(1);
+  A.gcy = take(1);
+  A.nxv = take(1);
+  A.nyv = take(1);
+  A.dn = take(4);
+  A.lf_r = take(9);
+  A.lf_b = take(9);
+  A.ln_x = take(1);
+  A.ln_y = take(1);
+  A.lnt_x = take(1);
+  A.lnt_y = take(1);
+  A.lg_x = take(1);
+  A.lg_y = take(1);
+  A.lgr_x = take(1);
+  A.lgr_y = take(1);
+  A.lrn = take(1);
+  A.lrnt = take(1);
+  A.ldn = take(4);
+  A.p_sigma = take(1);
+  A.p_hR = take(1);
+  A.p_hB = take(1);
+  A.p_theta = take(1);
+  // ---- forward with checkpoints (the handle ends at step T)
+  for (int64_t k = 0; k < nseg; ++k) {
+    CK(h, cudaMemcpyAsync(reinterpret_cast<char*>(ckpt) + sb * k, h->pool[h->cur], sb, cudaMemcpyDeviceToDevice,
+                          h->stream));
+    s = lbcg_step(h, std::min<int64_t>(K, T - k * K));
+    if (s != LBCG_OK) return s;
+  }
+  // ---- objective and its seed dJ/d(rho^N) at step T
+  std::vector<double> fields(4 * (size_t)N), cw(N, 0.0);
+  s = lbcg_get_fields(h, 0, fields.data());
+  if (s != LBCG_OK) return s;
+  const double* rhoN = fields.data() + N;
+  double J = 0.0;
+  if (spec->objective == LBCG_OBJ_WEIGHTED) {
+    for (int i = 0; i < N; ++i)
+      if (!L.solid[i]) {
+        cw[i] = spec->weight[i];
+        J += cw[i] * rhoN[i];
+      }
+  } else {
+    auto row_ok = [&](int r) { return r >= 0 && r < ny; };
+    const int r0 = spec->tip_row0, r1 = spec->tip_row1;
+    if (!row_ok(r0) || !row_ok(r1)) return fail(LBCG_E_ARG, "tip rows outside the lattice");
+    std::vector<double> prof(nx);
+    for (int x = 0; x < nx; ++x) prof[x] = 0.5 * (rhoN[r0 * nx + x] + rhoN[r1 * nx + x]);
+    int i0;
+    double xt, d0, d1;
+    if (!crossing_derivative(prof, i0, xt, d0, d1)) return fail(LBCG_E_ARG, "no finger tip at step T");
+    J = xt;
+    cw[r0 * nx + i0] += 0.5 * d0;
+    cw[r1 * nx + i0] += 0.5 * d0;
+    cw[r0 * nx + i0 + 1] += 0.5 * d1;
+    cw[r1 * nx + i0 + 1] += 0.5 * d1;
+    const int rows[2] = {spec->cl_row0, spec->cl_row1};
+    std::vector<std::pair<int, double>> cl;
+    double xsum = 0;
+    int found = 0;
+    std::vector<int> ii(2);
+    std::vector<double> dd0(2), dd1(2);
+    for (int q = 0; q < 2; ++q) {
+      if (!row_ok(rows[q])) continue;
+      for (int x = 0; x < nx; ++x) prof[x] = rhoN[rows[q] * nx + x];
+      double xc;
+      if (crossing_derivative(prof, ii[found], xc, dd0[found], dd1[found])) {
+        xsum += xc;
+        ii[found] = ii[found] + rows[q] * nx;  // node index of the crossing
+        ++found;
+      }
+    }
+    if (found == 0) return fail(LBCG_E_ARG, "no contact line at step T");
+    J -= xsum / found;
+    for (int q = 0; q < found; ++q) {
+      cw[ii[q]] -= dd0[q] / found;
+      cw[ii[q] + 1] -= dd1[q] / found;
+    }
+  }
+  CK(h, cudaMemcpyAsync(c_dev, cw.data(), N * 8, cudaMemcpyHostToDevice, h->stream));
+  A.src = static_cast<const double*>(h->pool[h->cur]);
+  A.lam = lamA;
+  CK(h, adjoint_seed(A, c_dev, h->stream));
+  // ---- reverse, one checkpoint segment at a time
+  double* lam_cur = lamA;   // adjoint of the state after the step being reversed
+  double* lam_new = lamB;
+  for (int64_t k = nseg - 1; k >= 0; --k) {
+    const int64_t ns = std::min<int64_t>(K, T - k * K);
+    // recompute the states of the segment: seg[j] = state before step k*K + j
+    CK(h, cudaMemcpyAsync(seg, reinterpret_cast<char*>(ckpt) + sb * k, sb, cudaMemcpyDeviceToDevice, h->stream));
+    for (int64_t j = 1; j < ns; ++j) {
+      LaunchStep p = make_launch(h, 0, nullptr, 0, h->ntiles);
+      p.src = reinterpret_cast<char*>(seg) + sb * (j - 1);
+      p.dst = reinterpret_cast<char*>(seg) + sb * j;
+      CK(h, cudaMemcpyAsync(p.dst, p.src, sb, cudaMemcpyDeviceToDevice, h->stream));  // solid slots and padding
+      CK(h, launch_step(h->prec, p, h->stream));
+    }
+    for (int64_t j = ns - 1; j >= 0; --j) {
+      A.src = reinterpret_cast<const double*>(reinterpret_cast<char*>(seg) + sb * j);
+      A.lam_next = lam_cur;
+      A.lam = lam_new;
+      CK(h, adjoint_step(A, h->stream));
+      std::swap(lam_cur, lam_new);
+    }
+  }
+  // ---- parameter adjoints
+  std::vector<double> ps(N), phR(N), phB(N), pth(N);
+  CK(h, cudaMemcpyAsync(ps.data(), A.p_sigma, N * 8, cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaMemcpyAsync(phR.data(), A.p_hR, N * 8, cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaMemcpyAsync(phB.data(), A.p_hB, N * 8, cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaMemcpyAsync(pth.data(), A.p_theta, N * 8, cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  double gs = 0, ghR = 0, ghB = 0, gth = 0;
+  for (int i = 0; i < N; ++i) {
+    gs += ps[i];
+    ghR += phR[i];
+    ghB += phB[i];
+    gth += pth[i];
+  }
+  out->J = J;
+  out->dJ_dsigma = gs;
+  out->dJ_dnu_R = ghR * (-0.5 / (L.prm.nu_R * L.prm.nu_R));
+  out->dJ_dnu_B = ghB * (-0.5 / (L.prm.nu_B * L.prm.nu_B));
+  out->dJ_dtheta = gth;
+  if (out->dJ_dtheta_node) memcpy(out->dJ_dtheta_node, pth.data(), N * 8);
   return LBCG_OK;
 }
 

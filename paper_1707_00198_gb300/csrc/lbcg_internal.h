@@ -50,6 +50,41 @@ cudaError_t launch_observables(const LatDev* lats, int lat, int nx, int ny, cons
                                long long node_total, const uint8_t* flags, int tip0, int tip1, int cl0, int cl1,
                                double* partials, double* out, cudaStream_t st);
 
+// Device pointers of one reverse step of the adjoint (lbcg_adjoint.cu); node arrays are
+// compact [ny][nx], FP64.
+struct AdjDev {
+  LatDev L;
+  int N;
+  const double* src;     // stored state (population pool of the lattice)
+  const uint8_t* flags;  // node flags (pitch layout)
+  const double* nsx;     // solid normal at outermost fluid nodes (compact, 0 elsewhere)
+  const double* nsy;
+  const double* cos_t;   // cos and sin of the contact angle per node (compact)
+  const double* sin_t;
+  // forward intermediates (compact)
+  double *fr, *fb;       // [9][N] post-streaming populations after the Zou-He columns
+  double *rr, *rb, *rn;  // colour densities, rho^N (virtual value on outermost solid nodes)
+  double *grx, *gry;     // raw gradient (Eq. 28)
+  double *gcx, *gcy;     // corrected gradient (Eq. 31; = raw off Omega_Fb)
+  double *nxv, *nyv;     // n on fluid nodes, virtual n on outermost solid nodes
+  double *dn;            // [4][N] d_x n_x, d_y n_x, d_x n_y, d_y n_y
+  int *pick;             // 1 or 2: the candidate Eq. 36 chose (0 off Omega_Fb / below guard)
+  // adjoints
+  const double* lam_next;  // [18][N] adjoint of the stored state after the step: (fr, fb) pairs
+  double* lam;             // [18][N] adjoint of the stored state before the step
+  double *lf_r, *lf_b;     // [9][N] adjoint of the post-Zou-He populations
+  double *ln_x, *ln_y;     // adjoint of n (local part)
+  double *lnt_x, *lnt_y;   // adjoint of the virtual-filled n (scatter target)
+  double *lg_x, *lg_y;     // adjoint of the corrected gradient
+  double *lgr_x, *lgr_y;   // adjoint of the raw gradient
+  double *lrn, *lrnt;      // adjoint of rho^N (local part) and of the virtual-filled rho^N
+  double *ldn;             // [4][N]
+  double *p_sigma, *p_hR, *p_hB, *p_theta;  // per-node parameter adjoints (accumulated)
+};
+
+cudaError_t adjoint_step(const AdjDev& A, cudaStream_t st);
+cudaError_t adjoint_seed(const AdjDev& A, const double* weight, cudaStream_t st);
+
 // Sets the calling thread's message returned by lbcg_last_error() (lbcg_host.cu).
 void set_last_error(const char* msg);
 

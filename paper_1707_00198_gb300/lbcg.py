@@ -50,6 +50,20 @@ class lbcg_obs(C.Structure):
                 ("x_cl", C.c_double), ("moments", C.c_double * 9), ("nonfinite", C.c_int32)]
 
 
+class lbcg_adjoint_spec(C.Structure):
+    _fields_ = [("nsteps", C.c_int64), ("checkpoint", C.c_int64), ("objective", C.c_int32),
+                ("weight", C.POINTER(C.c_double)), ("tip_row0", C.c_int32), ("tip_row1", C.c_int32),
+                ("cl_row0", C.c_int32), ("cl_row1", C.c_int32)]
+
+
+class lbcg_grads(C.Structure):
+    _fields_ = [("J", C.c_double), ("dJ_dsigma", C.c_double), ("dJ_dnu_R", C.c_double), ("dJ_dnu_B", C.c_double),
+                ("dJ_dtheta", C.c_double), ("dJ_dtheta_node", C.POINTER(C.c_double))]
+
+
+LBCG_OBJ_WEIGHTED, LBCG_OBJ_FINGER_LENGTH = 0, 1
+
+
 class LBCGError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -92,6 +106,7 @@ def library():
         "lbcg_last_error": (C.c_char_p, []),
         "lbcg_field_moments_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
                                                  C.c_void_p]),
+        "lbcg_adjoint": (C.c_int, [H, C.POINTER(lbcg_adjoint_spec), C.POINTER(lbcg_grads)]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -105,7 +120,7 @@ def exported_symbols() -> list:
     return ["lbcg_create", "lbcg_create_batch", "lbcg_step", "lbcg_observables", "lbcg_get_populations",
             "lbcg_set_populations", "lbcg_get_fields", "lbcg_state_bytes", "lbcg_upload_state",
             "lbcg_download_state", "lbcg_set_sweep", "lbcg_set_tile", "lbcg_profile", "lbcg_kernel_times", "lbcg_launches_per_step", "lbcg_total_nodes", "lbcg_destroy",
-            "lbcg_last_error", "lbcg_field_moments_noalloc"]
+            "lbcg_last_error", "lbcg_field_moments_noalloc", "lbcg_adjoint"]
 
 
 def _check(status: int):
@@ -232,6 +247,24 @@ def lbcg_field_moments_noalloc(fields_ptr: int, mask_ptr: int, nx: int, ny: int,
     _check(library().lbcg_field_moments_noalloc(fields_ptr, mask_ptr, nx, ny, C.c_void_p(stream or None), out_ptr))
 
 
+def lbcg_adjoint(h: int, nx: int, ny: int, nsteps: int, checkpoint: int, weight: Optional[np.ndarray] = None,
+                 tip_rows=None, cl_rows=None) -> dict:
+    """Run nsteps forward, then the reverse sweep; returns J and its gradients.  With `weight`
+    ([ny, nx]) J = sum weight * rho^N at the last step; without it J is the finger length."""
+    if weight is not None:
+        w = np.ascontiguousarray(weight, dtype=np.float64).reshape(ny, nx)
+        obj, wp = LBCG_OBJ_WEIGHTED, _dptr(w)
+    else:
+        w, obj, wp = None, LBCG_OBJ_FINGER_LENGTH, None
+    o = obs_spec(ny=ny, tip_rows=tip_rows, cl_rows=cl_rows)
+    spec = lbcg_adjoint_spec(nsteps, checkpoint, obj, wp, o.tip_row0, o.tip_row1, o.cl_row0, o.cl_row1)
+    dth = np.zeros((ny, nx), dtype=np.float64)
+    out = lbcg_grads(0, 0, 0, 0, 0, _dptr(dth))
+    _check(library().lbcg_adjoint(h, C.byref(spec), C.byref(out)))
+    return {"J": out.J, "dsigma": out.dJ_dsigma, "dnu_R": out.dJ_dnu_R, "dnu_B": out.dJ_dnu_B,
+            "dtheta": out.dJ_dtheta, "dtheta_node": dth}
+
+
 def obs_spec(wall_y: float = 0.5, cyl=None, tip_rows=None, cl_rows=None, ny: Optional[int] = None) -> lbcg_obs_spec:
     if tip_rows is None:
         tip_rows = ((ny // 2 - 1, ny // 2) if ny % 2 == 0 else (ny // 2, ny // 2)) if ny else (-1, -1)
@@ -269,6 +302,11 @@ class Lattice:
     def fields(self, lattice: int = 0) -> np.ndarray:
         g = self.geoms[lattice]
         return lbcg_get_fields(self.h, lattice, g.nx, g.ny)
+
+    def adjoint(self, nsteps: int, checkpoint: int, weight: Optional[np.ndarray] = None, **kw) -> dict:
+        """Gradients of J at step (current + nsteps); see lbcg_adjoint.  FP64, one lattice."""
+        g = self.geoms[0]
+        return lbcg_adjoint(self.h, g.nx, g.ny, nsteps, checkpoint, weight, **kw)
 
     def set_tile(self, ty: int):
         lbcg_set_tile(self.h, ty)
