@@ -254,6 +254,32 @@ def measure_form(geoms, prms, precision, K, W, stream, with_profile=False, ty=0)
     return lat, ms, kt, flush is not None
 
 
+def adjoint_rate(lbcg, stream, T: int, K: int):
+    """Wall time of lbcg_adjoint (forward with checkpoints + reverse sweep) for the finger
+    length of a 400x42 displacement channel, M=10, Ca=0.05, theta=60 deg, in FP64."""
+    g, p = I.config_adjoint()
+    L = lbcg.Lattice(g, p, "fp64", stream=stream.cuda_stream)
+    try:
+        L.adjoint(2 * K, K)          # warm-up: first launches, allocations
+        L.close()
+        L = lbcg.Lattice(g, p, "fp64", stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = L.adjoint(T, K)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+    except Exception as e:  # noqa: BLE001 -- reported, not hidden
+        return {"error": str(e)}
+    finally:
+        L.close()
+    nf = int((g.solid == 0).sum())
+    return {"workload": f"displacement channel {g.nx}x{g.ny}, M=10, Ca=0.05, theta=60deg, J = finger length",
+            "precision": "fp64", "steps": T, "checkpoint": K, "seconds": t, "s_per_step": t / T,
+            "mlups_forward_plus_reverse": nf * T / t / 1e6, "J": out["J"], "dJ_dtheta": out["dtheta"],
+            "dJ_dsigma": out["dsigma"], "dJ_dnu_R": out["dnu_R"], "dJ_dnu_B": out["dnu_B"],
+            "timing": "host clock around the whole call (it synchronises)"}
+
+
 def run_ours(args):
     ws, rank, local = dist_env()
     if ws > 1:
@@ -346,6 +372,11 @@ def run_ours(args):
             forms[prec] = {"MLUPS": nf * Kf / (msf / 1e3) / 1e6,
                            "hbm_gbs_alg": 36 * STORE_BYTES[prec] * nf * Kf / (msf / 1e3) / 1e9}
 
+    # ---- the discrete adjoint on the 400x42 channel (FP64, rank 0)
+    adj = None
+    if rank == 0 and not args.no_adjoint:
+        adj = adjoint_rate(lbcg, stream, args.adjoint_steps, args.adjoint_checkpoint)
+
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N=1 only)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -364,7 +395,7 @@ def run_ours(args):
                            else "inputs larger than L2", "mlups_counts": "fluid-node updates"},
                 "hbm_gbs_alg": whole_gbs, "hbm_frac_alg": whole_gbs / peak,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-                "forms": forms, "nonfinite_lattice0": obs.get("nonfinite", None)}
+                "forms": forms, "adjoint": adj, "nonfinite_lattice0": obs.get("nonfinite", None)}
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -383,6 +414,9 @@ def main():
     ap.add_argument("--ty", type=int, default=0, help="tile height of k_step (4, 8, 16; 0 = default)")
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adjoint-steps", type=int, default=4000)
+    ap.add_argument("--adjoint-checkpoint", type=int, default=200)
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -3,21 +3,24 @@
 // node), the interfacial tension sigma and the two viscosities (Sec. II; Eq. 1-18, 28-36).
 //
 // One reverse step, from the adjoint lambda' of the stored post-streaming state after the
-// step to the adjoint lambda of the state before it, runs these kernels in order:
-//   forward intermediates, recomputed from the stored state (fwd_*): post-Zou-He
-//     populations, colour densities and rho^N, Eq. 29 virtual rho^N, raw and corrected
-//     gradient (Eq. 28, 30-36), n, Eq. 29 virtual n, grad n;
-//   adj_collide   : transpose of streaming + bounce-back (a gather of lambda'), then the
-//                   hand-derived reverse of Eq. 17, 18, 5, 1-9, 13, 10 and 14 per node;
-//   adj_dn        : transpose of Eq. 28 applied to n (a scatter onto the n stencil);
-//   adj_vn        : transpose of Eq. 29 for n on outermost solid nodes;
-//   adj_n         : reverse of n = g / |g| (zero below the guard);
-//   adj_wet       : reverse of Eq. 30-36 on outermost fluid nodes (d|g| and d theta);
-//   adj_grad      : transpose of Eq. 28 applied to rho^N;
-//   adj_vrn       : transpose of Eq. 29 for rho^N;
-//   adj_rho       : reverse of Eq. 12 and 16, then of the Zou-He columns -> lambda.
-// Scatters accumulate with FP64 atomics.  Everything is FP64; node arrays are compact
-// [ny][nx] (index y * nx + x).
+// step to the adjoint lambda of the state before it, runs six kernels:
+//   fwd_local   : forward intermediates recomputed from the stored state: post-Zou-He
+//                 populations, colour densities and rho^N (Eq. 12, 16); clears the scatter
+//                 targets of this step;
+//   fwd_grad    : raw gradient (Eq. 28, Eq. 29 virtual values evaluated on the fly), the
+//                 wetting correction (Eq. 30-36) and n;
+//   fwd_dn      : grad n (Eq. 28 on n with Eq. 29 virtual values);
+//   adj_collide : transpose of streaming + bounce-back (a gather of lambda'), the
+//                 hand-derived reverse of Eq. 14, 1-9, 17, 18, 10 and 13 per node, and the
+//                 transpose of Eq. 28/29 applied to n (a scatter onto the n stencil);
+//   adj_normal  : reverse of n = g/|g|, of Eq. 30-36 (d|g| and d theta), and the transpose of
+//                 Eq. 28/29 applied to rho^N (a scatter);
+//   adj_rho     : reverse of Eq. 12 and 16, then of the Zou-He columns -> lambda.
+// A value that a stencil reads on a solid neighbour is that node's Eq. 29 virtual value, a
+// weighted mean of its own fluid neighbours; the transpose scatters straight through that
+// mean onto those fluid nodes.  Scatters accumulate with FP64 atomics.  Everything is FP64;
+// node arrays are compact [ny][nx] (index y * nx + x).  FP64 throughput per SM is low on
+// this GPU, so blocks are small (64 threads) to spread a lattice over every SM.
 #include <vector>
 
 #include "../../include/lbcg.h"
@@ -26,6 +29,8 @@
 namespace lbcg {
 
 namespace {
+
+constexpr int kAdjThreads = 64;
 
 __device__ __forceinline__ bool is_solid(const AdjDev& A, int x, int y) {
   return (A.flags[A.L.node_off + (long long)y * A.L.pitch + x] & F_SOLID) != 0;
@@ -37,11 +42,12 @@ __device__ __forceinline__ int mapx(const AdjDev& A, int v) { return wrap_or_cla
 __device__ __forceinline__ int mapy(const AdjDev& A, int v) { return wrap_or_clamp(v, A.L.ny, A.L.bcy == BC_PERIODIC); }
 
 // ------------------------------------------------------------------ forward intermediates
-__global__ void fwd_local(AdjDev A) {
+__global__ void __launch_bounds__(kAdjThreads) fwd_local(AdjDev A) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= A.N) return;
   const int x = i % A.L.nx, y = i / A.L.nx;
   const int N = A.N;
+  A.lnt_x[i] = A.lnt_y[i] = A.lrnt[i] = 0.0;
   if (is_solid(A, x, y)) {
     for (int a = 0; a < 9; ++a) A.fr[a * N + i] = A.fb[a * N + i] = 0.0;
     A.rr[i] = A.rb[i] = A.rn[i] = 0.0;
@@ -58,8 +64,18 @@ __global__ void fwd_local(AdjDev A) {
   A.rb[i] = rB;
 }
 
-// Eq. 29 on outermost solid nodes for a field v (fluid values already in v)
-__device__ double virtual_value(const AdjDev& A, const double* v, int x, int y) {
+// Sum of the D2Q9 weights toward the fluid neighbours of a solid node (Eq. 29 denominator)
+__device__ double weight_sum(const AdjDev& A, int x, int y) {
+  double den = 0.0;
+  for (int b = 1; b < 9; ++b)
+    if (!is_solid(A, mapx(A, x + ex(b)), mapy(A, y + ey(b)))) den = radd(den, wgt<double>(b));
+  return den;
+}
+
+// Value of field v that a stencil reads at (x, y): v itself on a fluid node, the Eq. 29
+// virtual value (the same sums in the same order as the step kernels) on a solid node
+__device__ double read_field(const AdjDev& A, const double* v, int x, int y) {
+  if (!is_solid(A, x, y)) return v[y * A.L.nx + x];
   double num = 0.0, den = 0.0;
   for (int b = 1; b < 9; ++b) {
     const int x2 = mapx(A, x + ex(b)), y2 = mapy(A, y + ey(b));
@@ -70,24 +86,29 @@ __device__ double virtual_value(const AdjDev& A, const double* v, int x, int y) 
   }
   return den > 0.0 ? rdiv(num, den) : 0.0;
 }
-__device__ double weight_sum(const AdjDev& A, int x, int y) {
-  double den = 0.0;
-  for (int b = 1; b < 9; ++b)
-    if (!is_solid(A, mapx(A, x + ex(b)), mapy(A, y + ey(b)))) den = radd(den, wgt<double>(b));
-  return den;
+
+// Transpose of read_field for one or two fields: add `val` to the adjoint of what was read
+__device__ void scatter_field(const AdjDev& A, double* acc0, double* acc1, int x, int y, double v0, double v1) {
+  if (!is_solid(A, x, y)) {
+    const int j = y * A.L.nx + x;
+    atomicAdd(&acc0[j], v0);
+    if (acc1) atomicAdd(&acc1[j], v1);
+    return;
+  }
+  const double den = weight_sum(A, x, y);
+  if (!(den > 0.0)) return;
+  const double r = 1.0 / den;
+  for (int b = 1; b < 9; ++b) {
+    const int x2 = mapx(A, x + ex(b)), y2 = mapy(A, y + ey(b));
+    if (is_solid(A, x2, y2)) continue;
+    const int j = y2 * A.L.nx + x2;
+    const double c = wgt<double>(b) * r;
+    atomicAdd(&acc0[j], c * v0);
+    if (acc1) atomicAdd(&acc1[j], c * v1);
+  }
 }
 
-__global__ void fwd_virtual(AdjDev A, double* v0, double* v1) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= A.N) return;
-  const int x = i % A.L.nx, y = i / A.L.nx;
-  if (!(flag_at(A, x, y) & F_OSOLID)) return;
-  // reads fluid entries only, writes solid entries only: no race
-  v0[i] = virtual_value(A, v0, x, y);
-  if (v1) v1[i] = virtual_value(A, v1, x, y);
-}
-
-__global__ void fwd_grad(AdjDev A) {
+__global__ void __launch_bounds__(kAdjThreads) fwd_grad(AdjDev A) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= A.N) return;
   const int x = i % A.L.nx, y = i / A.L.nx;
@@ -100,7 +121,7 @@ __global__ void fwd_grad(AdjDev A) {
   }
   double gx = 0.0, gy = 0.0;
   for (int a = 1; a < 9; ++a) {
-    const double t = rmul(wgt<double>(a), A.rn[mapy(A, y + ey(a)) * A.L.nx + mapx(A, x + ex(a))]);
+    const double t = rmul(wgt<double>(a), read_field(A, A.rn, mapx(A, x + ex(a)), mapy(A, y + ey(a))));
     if (ex(a) == 1) gx = radd(gx, t);
     if (ex(a) == -1) gx = radd(gx, -t);
     if (ey(a) == 1) gy = radd(gy, t);
@@ -134,7 +155,7 @@ __global__ void fwd_grad(AdjDev A) {
   A.nyv[i] = m2 > eps ? cgy / m2 : 0.0;
 }
 
-__global__ void fwd_dn(AdjDev A) {
+__global__ void __launch_bounds__(kAdjThreads) fwd_dn(AdjDev A) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= A.N) return;
   const int x = i % A.L.nx, y = i / A.L.nx;
@@ -142,8 +163,9 @@ __global__ void fwd_dn(AdjDev A) {
   double d[4] = {0, 0, 0, 0};
   if (!is_solid(A, x, y)) {
     for (int a = 1; a < 9; ++a) {
-      const int j = mapy(A, y + ey(a)) * A.L.nx + mapx(A, x + ex(a));
-      const double tx = wgt<double>(a) * A.nxv[j], ty = wgt<double>(a) * A.nyv[j];
+      const int x2 = mapx(A, x + ex(a)), y2 = mapy(A, y + ey(a));
+      const double tx = wgt<double>(a) * read_field(A, A.nxv, x2, y2);
+      const double ty = wgt<double>(a) * read_field(A, A.nyv, x2, y2);
       d[0] += ex(a) * tx;
       d[1] += ey(a) * tx;
       d[2] += ex(a) * ty;
@@ -156,7 +178,7 @@ __global__ void fwd_dn(AdjDev A) {
 // ------------------------------------------------------------------ reverse kernels
 // Transpose of the push (Eq. 15, half-way bounce-back, open edges) and the reverse of the
 // node-local part of the step.
-__global__ void adj_collide(AdjDev A) {
+__global__ void __launch_bounds__(kAdjThreads) adj_collide(AdjDev A) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= A.N) return;
   const int x = i % A.L.nx, y = i / A.L.nx;
@@ -164,7 +186,6 @@ __global__ void adj_collide(AdjDev A) {
   const LatDev& L = A.L;
   for (int a = 0; a < 9; ++a) A.lf_r[a * N + i] = A.lf_b[a * N + i] = 0.0;
   A.ln_x[i] = A.ln_y[i] = A.lg_x[i] = A.lg_y[i] = A.lrn[i] = 0.0;
-  for (int q = 0; q < 4; ++q) A.ldn[q * N + i] = 0.0;
   if (is_solid(A, x, y)) return;
   const bool px = L.bcx == BC_PERIODIC, py = L.bcy == BC_PERIODIC;
   // adjoint of the post-collision, recoloured values (oR_a, oB_a) leaving this node
@@ -190,7 +211,7 @@ __global__ void adj_collide(AdjDev A) {
     f[a] = fr[a] + fb[a];
   }
   const double rhoR = A.rr[i], rhoB = A.rb[i], rn = A.rn[i];
-  const double rho = rhoR + rhoB;
+  const double rho = rhoR + rhoB, ir = 1.0 / rho;
   const double nxo = A.nxv[i], nyo = A.nyv[i];
   const double gx = A.gcx[i], gy = A.gcy[i];
   const double dxx = A.dn[i], dxy = A.dn[N + i], dyx = A.dn[2 * N + i], dyy = A.dn[3 * N + i];
@@ -199,7 +220,7 @@ __global__ void adj_collide(AdjDev A) {
   const double Fx = hsk * gx, Fy = hsk * gy;
   const double jx = f[1] - f[3] + f[5] - f[6] - f[7] + f[8];
   const double jy = f[2] - f[4] + f[5] + f[6] - f[7] - f[8];
-  const double ux = (jx + 0.5 * Fx) / rho, uy = (jy + 0.5 * Fy) / rho;
+  const double ux = (jx + 0.5 * Fx) * ir, uy = (jy + 0.5 * Fy) * ir;
   const double inv_nu = (1 + rn) * L.h_inv_nuR + (1 - rn) * L.h_inv_nuB;
   const double den_sv = 3.0 + 0.5 * inv_nu;
   const double sv = inv_nu / den_sv;
@@ -220,8 +241,9 @@ __global__ void adj_collide(AdjDev A) {
   const double Dxx = sv * Axx - (1 - 0.5 * sv) * Bxx;
   const double Axy = pxy - rho * ux * uy, Bxy = ux * Fy + uy * Fx;
   const double Dxy = sv * Axy - (1 - 0.5 * sv) * Bxy;
-  const double ae = De / 36, aeps = Deps / 36, ajx = -Fx / 6, ajy = -Fy / 6;
-  const double aqx = Dqx / 12, aqy = Dqy / 12, axx = Dxx / 4, axy = Dxy / 4;
+  constexpr double k36 = 1.0 / 36, k12 = 1.0 / 12, k6 = 1.0 / 6;
+  const double ae = De * k36, aeps = Deps * k36, ajx = -Fx * k6, ajy = -Fy * k6;
+  const double aqx = Dqx * k12, aqy = Dqy * k12, axx = Dxx * 0.25, axy = Dxy * 0.25;
   double fp[9];
   fp[0] = f[0] - (-4 * ae + 4 * aeps);
   const double c14 = -ae - 2 * aeps;
@@ -234,8 +256,8 @@ __global__ void adj_collide(AdjDev A) {
   fp[6] = f[6] - (c58 - ajx - aqx + ajy + aqy - axy);
   fp[7] = f[7] - (c58 - ajx - aqx - ajy - aqy + axy);
   fp[8] = f[8] - (c58 + ajx + aqx - ajy - aqy - axy);
-  const double cR = rhoR / rho;
-  const double pc = beta * rhoR * rhoB / rho;
+  const double cR = rhoR * ir;
+  const double pc = beta * rhoR * rhoB * ir;
   // ---- reverse of Eq. 14: oR = cR fp + pc w (e.n), oB = fp - oR
   double lfp[9], lcR = 0, lpc = 0, lnx = 0, lny = 0;
   for (int a = 0; a < 9; ++a) {
@@ -247,9 +269,9 @@ __global__ void adj_collide(AdjDev A) {
     lnx += mu * pc * wgt<double>(a) * ex(a);
     lny += mu * pc * wgt<double>(a) * ey(a);
   }
-  double lrhoR = lcR / rho + lpc * beta * rhoB / rho;
-  double lrhoB = lpc * beta * rhoR / rho;
-  double lrho = -lcR * rhoR / (rho * rho) - lpc * beta * rhoR * rhoB / (rho * rho);
+  double lrhoR = (lcR + lpc * beta * rhoB) * ir;
+  double lrhoB = lpc * beta * rhoR * ir;
+  double lrho = -(lcR * rhoR + lpc * beta * rhoR * rhoB) * ir * ir;
   // ---- reverse of fp = f - M^T diag(...) Delta
   double lf[9];
   for (int a = 0; a < 9; ++a) lf[a] = lfp[a];
@@ -262,9 +284,9 @@ __global__ void adj_collide(AdjDev A) {
   const double laqy = -(-2 * lfp[2] + 2 * lfp[4] + lfp[5] + lfp[6] - lfp[7] - lfp[8]);
   const double laxx = -(lfp[1] - lfp[2] + lfp[3] - lfp[4]);
   const double laxy = -(lfp[5] - lfp[6] + lfp[7] - lfp[8]);
-  const double lDe = lae / 36, lDeps = laeps / 36, lDqx = laqx / 12, lDqy = laqy / 12;
-  const double lDxx = laxx / 4, lDxy = laxy / 4;
-  double lFx = -lajx / 6, lFy = -lajy / 6;
+  const double lDe = lae * k36, lDeps = laeps * k36, lDqx = laqx * k12, lDqy = laqy * k12;
+  const double lDxx = laxx * 0.25, lDxy = laxy * 0.25;
+  double lFx = -lajx * k6, lFy = -lajy * k6;
   double lux = 0, luy = 0, lu2 = 0, luF = 0, lsv = 0;
   double lme = 0, lmeps = 0, lqx = 0, lqy = 0, lpxx = 0, lpxy = 0;
   // De
@@ -323,10 +345,10 @@ __global__ void adj_collide(AdjDev A) {
   A.p_hR[i] += (1 + rn) * linv;
   A.p_hB[i] += (1 - rn) * linv;
   // u = (j + F/2) / rho
-  const double ljx = lux / rho, ljy = luy / rho;
-  lFx += 0.5 * lux / rho;
-  lFy += 0.5 * luy / rho;
-  lrho += -(ux * lux + uy * luy) / rho;
+  const double ljx = lux * ir, ljy = luy * ir;
+  lFx += 0.5 * ljx;
+  lFy += 0.5 * ljy;
+  lrho += -(ux * lux + uy * luy) * ir;
   for (int a = 0; a < 9; ++a) lf[a] += ex(a) * ljx + ey(a) * ljy;
   // F = (sigma kappa / 2) g
   const double lhsk = gx * lFx + gy * lFy;
@@ -336,10 +358,18 @@ __global__ void adj_collide(AdjDev A) {
   // kappa = -nx^2 dyy - ny^2 dxx + nx ny (dxy + dyx)
   lnx += (-2 * nxo * dyy + nyo * (dxy + dyx)) * lk;
   lny += (-2 * nyo * dxx + nxo * (dxy + dyx)) * lk;
-  A.ldn[i] = -nyo * nyo * lk;             // d_x n_x
-  A.ldn[N + i] = nxo * nyo * lk;          // d_y n_x
-  A.ldn[2 * N + i] = nxo * nyo * lk;      // d_x n_y
-  A.ldn[3 * N + i] = -nxo * nxo * lk;     // d_y n_y
+  // transpose of grad n = 3 sum_a w_a e_a n~(x + e_a) (Eq. 28 on the Eq. 29-filled n)
+  if (lk != 0.0) {
+    const double lxx = -nyo * nyo * lk;   // adjoint of d_x n_x
+    const double lxy = nxo * nyo * lk;    // d_y n_x
+    const double lyx = nxo * nyo * lk;    // d_x n_y
+    const double lyy = -nxo * nxo * lk;   // d_y n_y
+    for (int a = 1; a < 9; ++a) {
+      const double w = 3.0 * wgt<double>(a);
+      scatter_field(A, A.lnt_x, A.lnt_y, mapx(A, x + ex(a)), mapy(A, y + ey(a)), w * (ex(a) * lxx + ey(a) * lxy),
+                    w * (ex(a) * lyx + ey(a) * lyy));
+    }
+  }
   // rho = rhoR + rhoB; f = fr + fb
   lrhoR += lrho;
   lrhoB += lrho;
@@ -354,105 +384,58 @@ __global__ void adj_collide(AdjDev A) {
   A.lg_y[i] = lgy;
 }
 
-// transpose of grad n = 3 sum_a w_a e_a n~(x + e_a): scatter onto the virtual-filled n
-__global__ void adj_dn(AdjDev A) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= A.N) return;
-  const int x = i % A.L.nx, y = i / A.L.nx;
-  if (is_solid(A, x, y)) return;
-  const int N = A.N;
-  const double lxx = A.ldn[i], lxy = A.ldn[N + i], lyx = A.ldn[2 * N + i], lyy = A.ldn[3 * N + i];
-  for (int a = 1; a < 9; ++a) {
-    const int j = mapy(A, y + ey(a)) * A.L.nx + mapx(A, x + ex(a));
-    const double w = 3.0 * wgt<double>(a);
-    atomicAdd(&A.lnt_x[j], w * (ex(a) * lxx + ey(a) * lxy));
-    atomicAdd(&A.lnt_y[j], w * (ex(a) * lyx + ey(a) * lyy));
-  }
-}
-
-// transpose of Eq. 29 (virtual value of an outermost solid node from its fluid neighbours)
-__global__ void adj_virtual(AdjDev A, double* t0, double* t1, double* d0, double* d1) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= A.N) return;
-  const int x = i % A.L.nx, y = i / A.L.nx;
-  if (!(flag_at(A, x, y) & F_OSOLID)) return;
-  const double den = weight_sum(A, x, y);
-  if (!(den > 0.0)) return;
-  for (int b = 1; b < 9; ++b) {
-    const int x2 = mapx(A, x + ex(b)), y2 = mapy(A, y + ey(b));
-    if (is_solid(A, x2, y2)) continue;
-    const int j = y2 * A.L.nx + x2;
-    const double c = wgt<double>(b) / den;
-    atomicAdd(&d0[j], c * t0[i]);
-    if (t1) atomicAdd(&d1[j], c * t1[i]);
-  }
-}
-
-// reverse of n = g / |g| on fluid nodes
-__global__ void adj_n(AdjDev A) {
+// Reverse of n = g_c / |g_c| (zero below the guard), of Eq. 30-36 (g_c = |g_r| n_f(theta) on
+// Omega_Fb, g_c = g_r elsewhere), and the transpose of the raw gradient (Eq. 28 on the
+// Eq. 29-filled rho^N), scattered onto rho^N.
+__global__ void __launch_bounds__(kAdjThreads) adj_normal(AdjDev A) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= A.N) return;
   const int x = i % A.L.nx, y = i / A.L.nx;
   if (is_solid(A, x, y)) return;
   const double lnx = A.ln_x[i] + A.lnt_x[i], lny = A.ln_y[i] + A.lnt_y[i];
-  const double gx = A.gcx[i], gy = A.gcy[i];
-  const double m = sqrt(gx * gx + gy * gy);
-  if (!(m > A.L.grad_eps)) return;
-  const double nx = gx / m, ny = gy / m;
-  const double dot = nx * lnx + ny * lny;
-  A.lg_x[i] += (lnx - nx * dot) / m;
-  A.lg_y[i] += (lny - ny * dot) / m;
-}
-
-// reverse of Eq. 30-36: g_c = |g_r| n_f(theta) on Omega_Fb, the identity elsewhere
-__global__ void adj_wet(AdjDev A) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= A.N) return;
-  const int x = i % A.L.nx, y = i / A.L.nx;
-  if (is_solid(A, x, y)) return;
-  const double lgx = A.lg_x[i], lgy = A.lg_y[i];
-  if (A.pick[i] == 0) {
-    A.lgr_x[i] = lgx;
-    A.lgr_y[i] = lgy;
-    return;
+  double lgx = A.lg_x[i], lgy = A.lg_y[i];
+  {
+    const double gx = A.gcx[i], gy = A.gcy[i];
+    const double m = sqrt(gx * gx + gy * gy);
+    if (m > A.L.grad_eps) {
+      const double im = 1.0 / m, nx = gx * im, ny = gy * im;
+      const double dot = nx * lnx + ny * lny;
+      lgx += (lnx - nx * dot) * im;
+      lgy += (lny - ny * dot) * im;
+    }
   }
-  const double gx = A.grx[i], gy = A.gry[i];
-  const double m = sqrt(gx * gx + gy * gy);
-  const double nsx = A.nsx[i], nsy = A.nsy[i];
-  const double c = A.cos_t[i], s = A.sin_t[i];
-  double nfx, nfy, dfx, dfy;
-  if (A.pick[i] == 1) {   // rotation by +theta
-    nfx = nsx * c - nsy * s;
-    nfy = nsx * s + nsy * c;
-    dfx = -nfy;
-    dfy = nfx;
-  } else {                // rotation by -theta
-    nfx = nsx * c + nsy * s;
-    nfy = -nsx * s + nsy * c;
-    dfx = nfy;
-    dfy = -nfx;
+  double lrx = lgx, lry = lgy;
+  const int pick = A.pick[i];
+  if (pick != 0) {
+    const double gx = A.grx[i], gy = A.gry[i];
+    const double m = sqrt(gx * gx + gy * gy);
+    const double nsx = A.nsx[i], nsy = A.nsy[i];
+    const double c = A.cos_t[i], s = A.sin_t[i];
+    double nfx, nfy, dfx, dfy;
+    if (pick == 1) {   // rotation by +theta; d n_f / d theta = (-n_fy, n_fx)
+      nfx = nsx * c - nsy * s;
+      nfy = nsx * s + nsy * c;
+      dfx = -nfy;
+      dfy = nfx;
+    } else {           // rotation by -theta; d n_f / d theta = (n_fy, -n_fx)
+      nfx = nsx * c + nsy * s;
+      nfy = -nsx * s + nsy * c;
+      dfx = nfy;
+      dfy = -nfx;
+    }
+    const double proj = (nfx * lgx + nfy * lgy) / m;
+    lrx = gx * proj;
+    lry = gy * proj;
+    A.p_theta[i] += m * (dfx * lgx + dfy * lgy);
   }
-  const double proj = nfx * lgx + nfy * lgy;
-  A.lgr_x[i] = gx / m * proj;
-  A.lgr_y[i] = gy / m * proj;
-  A.p_theta[i] += m * (dfx * lgx + dfy * lgy);
-}
-
-// transpose of the raw gradient (Eq. 28 on the virtual-filled rho^N): scatter
-__global__ void adj_grad(AdjDev A) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= A.N) return;
-  const int x = i % A.L.nx, y = i / A.L.nx;
-  if (is_solid(A, x, y)) return;
-  const double lx = A.lgr_x[i], ly = A.lgr_y[i];
-  for (int a = 1; a < 9; ++a) {
-    const int j = mapy(A, y + ey(a)) * A.L.nx + mapx(A, x + ex(a));
-    atomicAdd(&A.lrnt[j], 3.0 * wgt<double>(a) * (ex(a) * lx + ey(a) * ly));
-  }
+  if (lrx != 0.0 || lry != 0.0)
+    for (int a = 1; a < 9; ++a)
+      scatter_field(A, A.lrnt, nullptr, mapx(A, x + ex(a)), mapy(A, y + ey(a)),
+                    3.0 * wgt<double>(a) * (ex(a) * lrx + ey(a) * lry), 0.0);
 }
 
 // reverse of rho^N = (rhoR - rhoB)/(rhoR + rhoB) and of the Zou-He columns
-__global__ void adj_rho(AdjDev A) {
+__global__ void __launch_bounds__(kAdjThreads) adj_rho(AdjDev A) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= A.N) return;
   const int x = i % A.L.nx, y = i / A.L.nx;
@@ -461,7 +444,8 @@ __global__ void adj_rho(AdjDev A) {
   if (is_solid(A, x, y)) return;
   const double lrn = A.lrn[i] + A.lrnt[i];
   const double rR = A.rr[i], rB = A.rb[i], rho = rR + rB;
-  const double cR = 2 * rB / (rho * rho) * lrn, cB = -2 * rR / (rho * rho) * lrn;
+  const double ir2 = 1.0 / (rho * rho);
+  const double cR = 2 * rB * ir2 * lrn, cB = -2 * rR * ir2 * lrn;
   double lr[9], lb[9];
   for (int a = 0; a < 9; ++a) {
     lr[a] = A.lf_r[a * N + i] + cR;
@@ -537,7 +521,17 @@ __global__ void adj_rho(AdjDev A) {
   }
 }
 
-inline int nblk(int n) { return (n + 255) / 256; }
+inline int nblk(int n) { return (n + kAdjThreads - 1) / kAdjThreads; }
+
+// Seed for an objective J = sum_x c(x) rho^N(x) of the stored state: lam = dJ/d(state).
+__global__ void __launch_bounds__(kAdjThreads) k_seed_weighted(AdjDev A, const double* c) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.N) return;
+  const int N = A.N;
+  for (int a = 0; a < 9; ++a) A.lf_r[a * N + i] = A.lf_b[a * N + i] = 0.0;
+  const int x = i % A.L.nx, y = i / A.L.nx;
+  A.lrn[i] = is_solid(A, x, y) ? 0.0 : c[i];
+}
 
 }  // namespace
 
@@ -545,43 +539,20 @@ inline int nblk(int n) { return (n + 255) / 256; }
 // `A` carries device pointers; the forward intermediates are recomputed from A.src.
 cudaError_t adjoint_step(const AdjDev& A, cudaStream_t st) {
   const int b = nblk(A.N);
-  fwd_local<<<b, 256, 0, st>>>(A);
-  fwd_virtual<<<b, 256, 0, st>>>(A, A.rn, nullptr);
-  fwd_grad<<<b, 256, 0, st>>>(A);
-  fwd_virtual<<<b, 256, 0, st>>>(A, A.nxv, A.nyv);
-  fwd_dn<<<b, 256, 0, st>>>(A);
-  cudaMemsetAsync(A.lnt_x, 0, A.N * sizeof(double), st);
-  cudaMemsetAsync(A.lnt_y, 0, A.N * sizeof(double), st);
-  cudaMemsetAsync(A.lrnt, 0, A.N * sizeof(double), st);
-  adj_collide<<<b, 256, 0, st>>>(A);
-  adj_dn<<<b, 256, 0, st>>>(A);
-  // lnt on outermost solid nodes goes to their fluid neighbours' n
-  adj_virtual<<<b, 256, 0, st>>>(A, A.lnt_x, A.lnt_y, A.ln_x, A.ln_y);
-  adj_n<<<b, 256, 0, st>>>(A);
-  adj_wet<<<b, 256, 0, st>>>(A);
-  adj_grad<<<b, 256, 0, st>>>(A);
-  adj_virtual<<<b, 256, 0, st>>>(A, A.lrnt, nullptr, A.lrn, nullptr);
-  adj_rho<<<b, 256, 0, st>>>(A);
+  fwd_local<<<b, kAdjThreads, 0, st>>>(A);
+  fwd_grad<<<b, kAdjThreads, 0, st>>>(A);
+  fwd_dn<<<b, kAdjThreads, 0, st>>>(A);
+  adj_collide<<<b, kAdjThreads, 0, st>>>(A);
+  adj_normal<<<b, kAdjThreads, 0, st>>>(A);
+  adj_rho<<<b, kAdjThreads, 0, st>>>(A);
   return cudaGetLastError();
-}
-
-// Seed for an objective J = sum_x c(x) rho^N(x) of the stored state: lam = dJ/d(state).
-__global__ void k_seed_weighted(AdjDev A, const double* c) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= A.N) return;
-  const int N = A.N;
-  for (int a = 0; a < 9; ++a) A.lf_r[a * N + i] = A.lf_b[a * N + i] = 0.0;
-  A.lrn[i] = 0.0;
-  A.lrnt[i] = 0.0;
-  const int x = i % A.L.nx, y = i / A.L.nx;
-  if (!is_solid(A, x, y)) A.lrn[i] = c[i];
 }
 
 cudaError_t adjoint_seed(const AdjDev& A, const double* c, cudaStream_t st) {
   const int b = nblk(A.N);
-  fwd_local<<<b, 256, 0, st>>>(A);
-  k_seed_weighted<<<b, 256, 0, st>>>(A, c);
-  adj_rho<<<b, 256, 0, st>>>(A);
+  fwd_local<<<b, kAdjThreads, 0, st>>>(A);   // also clears lrnt
+  k_seed_weighted<<<b, kAdjThreads, 0, st>>>(A, c);
+  adj_rho<<<b, kAdjThreads, 0, st>>>(A);
   return cudaGetLastError();
 }
 

@@ -30,6 +30,7 @@ lbcg_status fail(lbcg_status s, const char* fmt, ...) {
 
 constexpr int kGraphSteps = 32;   // steps per captured graph (even: the graph starts and ends on pool A)
 constexpr int kDefaultTY = 8;
+constexpr int kSMs = 152;
 
 size_t elem_size(int prec) { return prec == 0 ? 8 : (prec == 1 ? 4 : 2); }
 size_t compute_size(int prec) { return prec == 0 ? 8 : 4; }
@@ -499,6 +500,13 @@ lbcg_status lbcg_create_batch(int32_t n, const lbcg_geometry* geoms, const lbcg_
   CKC(cudaMemset(h->d_wall, 0, 4 * (size_t)node_total * cs));
   {
     lbcg_status s = upload_tiles(h);
+    // default schedule: the y-sweep when its strips give every SM a block, else tiles
+    // (FP64 arithmetic is slow per SM, so FP64 takes the smallest tiles, i.e. the most blocks)
+    if (s == LBCG_OK && h->nstrips < kSMs) {
+      h->sweep = 0;
+      h->ty = precision == LBCG_FP64 ? 4 : kDefaultTY;
+      s = upload_tiles(h);
+    }
     if (s != LBCG_OK) {
       free_handle(h);
       return s;
@@ -795,7 +803,8 @@ lbcg_status lbcg_adjoint(lbcg_handle* h, const lbcg_adjoint_spec* spec, lbcg_gra
   double *ckpt, *seg, *lamA, *lamB, *work, *c_dev;
   double *nsx, *nsy, *ct, *st;
   int* pick;
-  const int kWork = 9 + 9 + 3 + 2 + 2 + 2 + 4 + 9 + 9 + 2 + 2 + 2 + 2 + 2 + 2 + 4 + 4;  // N-sized arrays
+  // N-sized arrays: fr, fb, rr/rb/rn, gr, gc, n, dn, lf_r, lf_b, ln, lnt, lg, lrn/lrnt, 4 parameter adjoints
+  const int kWork = 9 + 9 + 3 + 2 + 2 + 2 + 4 + 9 + 9 + 2 + 2 + 2 + 2 + 4;
   if (!B.get(&ckpt, sb * (size_t)nseg) || !B.get(&seg, sb * (size_t)K) || !B.get(&lamA, 18 * (size_t)N * 8) ||
       !B.get(&lamB, 18 * (size_t)N * 8) || !B.get(&work, (size_t)kWork * N * 8) || !B.get(&c_dev, (size_t)N * 8) ||
       !B.get(&nsx, (size_t)N * 8) || !B.get(&nsy, (size_t)N * 8) || !B.get(&ct, (size_t)N * 8) ||
@@ -857,11 +866,8 @@ lbcg_status lbcg_adjoint(lbcg_handle* h, const lbcg_adjoint_spec* spec, lbcg_gra
   A.lnt_y = take(1);
   A.lg_x = take(1);
   A.lg_y = take(1);
-  A.lgr_x = take(1);
-  A.lgr_y = take(1);
   A.lrn = take(1);
   A.lrnt = take(1);
-  A.ldn = take(4);
   A.p_sigma = take(1);
   A.p_hR = take(1);
   A.p_hB = take(1);
@@ -926,27 +932,66 @@ lbcg_status lbcg_adjoint(lbcg_handle* h, const lbcg_adjoint_spec* spec, lbcg_gra
   A.src = static_cast<const double*>(h->pool[h->cur]);
   A.lam = lamA;
   CK(h, adjoint_seed(A, c_dev, h->stream));
-  // ---- reverse, one checkpoint segment at a time
-  double* lam_cur = lamA;   // adjoint of the state after the step being reversed
-  double* lam_new = lamB;
-  for (int64_t k = nseg - 1; k >= 0; --k) {
-    const int64_t ns = std::min<int64_t>(K, T - k * K);
-    // recompute the states of the segment: seg[j] = state before step k*K + j
-    CK(h, cudaMemcpyAsync(seg, reinterpret_cast<char*>(ckpt) + sb * k, sb, cudaMemcpyDeviceToDevice, h->stream));
+  // ---- reverse, one checkpoint segment at a time.  A segment's work (recompute its states
+  // from the checkpoint, then reverse its steps) is captured once per (length, adjoint
+  // buffer parity) as a CUDA graph and replayed; only the checkpoint copy is outside.
+  CK(h, cudaMemsetAsync(seg, 0, sb * (size_t)K, h->stream));   // slots the push never writes
+  auto enqueue_segment = [&](int64_t ns, bool lam_in_a) -> cudaError_t {
     for (int64_t j = 1; j < ns; ++j) {
       LaunchStep p = make_launch(h, 0, nullptr, 0, h->ntiles);
       p.src = reinterpret_cast<char*>(seg) + sb * (j - 1);
       p.dst = reinterpret_cast<char*>(seg) + sb * j;
-      CK(h, cudaMemcpyAsync(p.dst, p.src, sb, cudaMemcpyDeviceToDevice, h->stream));  // solid slots and padding
-      CK(h, launch_step(h->prec, p, h->stream));
+      cudaError_t e = launch_step(h->prec, p, h->stream);
+      if (e != cudaSuccess) return e;
     }
+    double* lc = lam_in_a ? lamA : lamB;
+    double* ln = lam_in_a ? lamB : lamA;
     for (int64_t j = ns - 1; j >= 0; --j) {
-      A.src = reinterpret_cast<const double*>(reinterpret_cast<char*>(seg) + sb * j);
-      A.lam_next = lam_cur;
-      A.lam = lam_new;
-      CK(h, adjoint_step(A, h->stream));
-      std::swap(lam_cur, lam_new);
+      AdjDev a = A;
+      a.src = reinterpret_cast<const double*>(reinterpret_cast<char*>(seg) + sb * j);
+      a.lam_next = lc;
+      a.lam = ln;
+      cudaError_t e = adjoint_step(a, h->stream);
+      if (e != cudaSuccess) return e;
+      std::swap(lc, ln);
     }
+    return cudaSuccess;
+  };
+  struct SegGraph {
+    int64_t ns;
+    bool lam_in_a;
+    cudaGraphExec_t exec;
+  };
+  struct SegGraphs {
+    std::vector<SegGraph> v;
+    ~SegGraphs() {
+      for (SegGraph& g : v) cudaGraphExecDestroy(g.exec);
+    }
+  } graphs;
+  bool lam_in_a = true;   // the seed is in lamA
+  for (int64_t k = nseg - 1; k >= 0; --k) {
+    const int64_t ns = std::min<int64_t>(K, T - k * K);
+    CK(h, cudaMemcpyAsync(seg, reinterpret_cast<char*>(ckpt) + sb * k, sb, cudaMemcpyDeviceToDevice, h->stream));
+    cudaGraphExec_t exec = nullptr;
+    for (const SegGraph& g : graphs.v)
+      if (g.ns == ns && g.lam_in_a == lam_in_a) exec = g.exec;
+    if (!exec) {
+      cudaGraph_t g = nullptr;
+      CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+      const cudaError_t le = enqueue_segment(ns, lam_in_a);
+      const cudaError_t ee = cudaStreamEndCapture(h->stream, &g);
+      if (le != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(h, le, "adjoint launch during capture");
+      }
+      if (ee != cudaSuccess) return cuda_fail(h, ee, "cudaStreamEndCapture (adjoint)");
+      const cudaError_t ie = cudaGraphInstantiate(&exec, g, 0);
+      cudaGraphDestroy(g);
+      if (ie != cudaSuccess) return cuda_fail(h, ie, "cudaGraphInstantiate (adjoint)");
+      graphs.v.push_back({ns, lam_in_a, exec});
+    }
+    CK(h, cudaGraphLaunch(exec, h->stream));
+    if (ns & 1) lam_in_a = !lam_in_a;
   }
   // ---- parameter adjoints
   std::vector<double> ps(N), phR(N), phB(N), pth(N);
@@ -998,6 +1043,65 @@ lbcg_status lbcg_set_tile(lbcg_handle* h, int32_t ty) {
     h->graph = nullptr;
   }
   return upload_tiles(h);
+}
+
+lbcg_status lbcg_autotune(lbcg_handle* h, int32_t probe_steps, int32_t* schedule) {
+  lbcg_status s = check_handle(h);
+  if (s != LBCG_OK) return s;
+  if (probe_steps < 1) return fail(LBCG_E_ARG, "probe_steps must be >= 1");
+  if (h->profiling) return fail(LBCG_E_ARG, "switch profiling off before autotuning");
+  CK(h, cudaStreamSynchronize(h->stream));
+  if (h->graph) {
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  struct Cand {
+    int sweep, ty;
+  };
+  const Cand cand[4] = {{1, h->ty}, {0, 4}, {0, 8}, {0, 16}};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(h, cudaEventCreate(&e0));
+  cudaError_t e = cudaEventCreate(&e1);
+  int best = 0;
+  float best_ms = 0.f;
+  for (int c = 0; c < 4 && e == cudaSuccess; ++c) {
+    h->sweep = cand[c].sweep;
+    h->ty = cand[c].ty;
+    s = upload_tiles(h);
+    if (s != LBCG_OK) break;
+    // src = current state, dst = the other buffer: repeated launches rewrite the same next
+    // state, so the probe does not advance the simulation
+    const LaunchStep p = make_launch(h, h->cur, nullptr, 0, h->ntiles);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = launch_step(h->prec, p, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+    for (int k = 0; k < probe_steps && e == cudaSuccess; ++k) e = launch_step(h->prec, p, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess && (c == 0 || ms < best_ms)) {
+      best = c;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e != cudaSuccess) return cuda_fail(h, e, "autotune probe");
+  if (s != LBCG_OK) return s;
+  h->sweep = cand[best].sweep;
+  h->ty = cand[best].ty;
+  s = upload_tiles(h);
+  if (s != LBCG_OK) return s;
+  if (schedule) *schedule = h->sweep ? 0 : h->ty;
+  return LBCG_OK;
+}
+
+lbcg_status lbcg_schedule(const lbcg_handle* h, int32_t* schedule) {
+  lbcg_status s = check_handle(h);
+  if (s != LBCG_OK) return s;
+  if (!schedule) return fail(LBCG_E_ARG, "NULL schedule");
+  *schedule = h->sweep ? 0 : h->ty;
+  return LBCG_OK;
 }
 
 lbcg_status lbcg_profile(lbcg_handle* h, int32_t enable) {

@@ -63,10 +63,10 @@ struct AdjDev {
   const double* sin_t;
   // forward intermediates (compact)
   double *fr, *fb;       // [9][N] post-streaming populations after the Zou-He columns
-  double *rr, *rb, *rn;  // colour densities, rho^N (virtual value on outermost solid nodes)
+  double *rr, *rb, *rn;  // colour densities, rho^N (fluid nodes; 0 on solid nodes)
   double *grx, *gry;     // raw gradient (Eq. 28)
   double *gcx, *gcy;     // corrected gradient (Eq. 31; = raw off Omega_Fb)
-  double *nxv, *nyv;     // n on fluid nodes, virtual n on outermost solid nodes
+  double *nxv, *nyv;     // n on fluid nodes (0 on solid nodes)
   double *dn;            // [4][N] d_x n_x, d_y n_x, d_x n_y, d_y n_y
   int *pick;             // 1 or 2: the candidate Eq. 36 chose (0 off Omega_Fb / below guard)
   // adjoints
@@ -74,11 +74,9 @@ struct AdjDev {
   double* lam;             // [18][N] adjoint of the stored state before the step
   double *lf_r, *lf_b;     // [9][N] adjoint of the post-Zou-He populations
   double *ln_x, *ln_y;     // adjoint of n (local part)
-  double *lnt_x, *lnt_y;   // adjoint of the virtual-filled n (scatter target)
-  double *lg_x, *lg_y;     // adjoint of the corrected gradient
-  double *lgr_x, *lgr_y;   // adjoint of the raw gradient
-  double *lrn, *lrnt;      // adjoint of rho^N (local part) and of the virtual-filled rho^N
-  double *ldn;             // [4][N]
+  double *lnt_x, *lnt_y;   // adjoint of n through the neighbours' grad n (scatter target)
+  double *lg_x, *lg_y;     // adjoint of the corrected gradient (force path)
+  double *lrn, *lrnt;      // adjoint of rho^N: local part, and through the neighbours' gradient
   double *p_sigma, *p_hR, *p_hB, *p_theta;  // per-node parameter adjoints (accumulated)
 };
 

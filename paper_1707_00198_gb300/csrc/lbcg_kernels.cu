@@ -793,6 +793,14 @@ __global__ void k_from_storage(const LatDev* __restrict__ lats, int lat, const S
 }
 
 // ------------------------------------------------------------------ launchers
+// Block size of the 1-D list kernels: a short list (one small lattice) is split into small
+// blocks so that it spreads over the SMs instead of queueing on a few of them.
+inline int list_threads(int n) {
+  int t = 256;
+  while (t > 32 && (n + t - 1) / t < 2 * 152) t >>= 1;
+  return t;
+}
+
 template <typename S>
 static cudaError_t launch_all(const LaunchStep& p, cudaStream_t st) {
   using T = typename Store<S>::T;
@@ -801,15 +809,16 @@ static cudaError_t launch_all(const LaunchStep& p, cudaStream_t st) {
   };
   rec(0);
   if (p.nband > 0) {
-    k_band<S><<<(p.nband + 255) / 256, 256, 0, st>>>(p.lats, p.band, p.nband, static_cast<const S*>(p.src),
-                                                     static_cast<T*>(p.band_rn));
+    const int t = list_threads(p.nband);
+    k_band<S><<<(p.nband + t - 1) / t, t, 0, st>>>(p.lats, p.band, p.nband, static_cast<const S*>(p.src),
+                                                   static_cast<T*>(p.band_rn));
   }
   rec(1);
   rec(2);
   if (p.nofb > 0) {
-    k_wall<T><<<(p.nofb + 255) / 256, 256, 0, st>>>(p.lats, p.ofb, p.nofb, p.flags,
-                                                    static_cast<const T*>(p.band_rn), static_cast<T*>(p.wall),
-                                                    p.node_total);
+    const int t = list_threads(p.nofb);
+    k_wall<T><<<(p.nofb + t - 1) / t, t, 0, st>>>(p.lats, p.ofb, p.nofb, p.flags, static_cast<const T*>(p.band_rn),
+                                                  static_cast<T*>(p.wall), p.node_total);
   }
   rec(3);
   rec(4);

@@ -107,6 +107,8 @@ def library():
         "lbcg_field_moments_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
                                                  C.c_void_p]),
         "lbcg_adjoint": (C.c_int, [H, C.POINTER(lbcg_adjoint_spec), C.POINTER(lbcg_grads)]),
+        "lbcg_autotune": (C.c_int, [H, C.c_int32, C.POINTER(C.c_int32)]),
+        "lbcg_schedule": (C.c_int, [H, C.POINTER(C.c_int32)]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -120,7 +122,7 @@ def exported_symbols() -> list:
     return ["lbcg_create", "lbcg_create_batch", "lbcg_step", "lbcg_observables", "lbcg_get_populations",
             "lbcg_set_populations", "lbcg_get_fields", "lbcg_state_bytes", "lbcg_upload_state",
             "lbcg_download_state", "lbcg_set_sweep", "lbcg_set_tile", "lbcg_profile", "lbcg_kernel_times", "lbcg_launches_per_step", "lbcg_total_nodes", "lbcg_destroy",
-            "lbcg_last_error", "lbcg_field_moments_noalloc", "lbcg_adjoint"]
+            "lbcg_last_error", "lbcg_field_moments_noalloc", "lbcg_adjoint", "lbcg_autotune", "lbcg_schedule"]
 
 
 def _check(status: int):
@@ -212,6 +214,19 @@ def lbcg_set_tile(h: int, ty: int):
 
 def lbcg_set_sweep(h: int, rows: int = 0):
     _check(library().lbcg_set_sweep(h, rows))
+
+
+def lbcg_autotune(h: int, probe_steps: int = 10) -> int:
+    """Time each step schedule on the current state and keep the fastest (0 = sweep, else tile height)."""
+    out = C.c_int32(-1)
+    _check(library().lbcg_autotune(h, probe_steps, C.byref(out)))
+    return out.value
+
+
+def lbcg_schedule(h: int) -> int:
+    out = C.c_int32(-1)
+    _check(library().lbcg_schedule(h, C.byref(out)))
+    return out.value
 
 
 def lbcg_profile(h: int, enable: bool):
@@ -313,6 +328,13 @@ class Lattice:
 
     def set_sweep(self, rows: int = 0):
         lbcg_set_sweep(self.h, rows)
+
+    def autotune(self, probe_steps: int = 10) -> int:
+        return lbcg_autotune(self.h, probe_steps)
+
+    @property
+    def schedule(self) -> int:
+        return lbcg_schedule(self.h)
 
     @property
     def state_bytes(self) -> int:

@@ -218,3 +218,22 @@ def test_full_size_capillary_fp32_sampled_windows():
         gB = s1[1][:, ys][:, :, xs]
         worst = max(worst, np.abs(gR[inner] - oR.numpy()[inner]).max(), np.abs(gB[inner] - oB.numpy()[inner]).max())
     assert worst <= 2e-6, worst
+
+
+def test_autotune_keeps_the_state_and_parity():
+    """lbcg_autotune probes every schedule on the current state without advancing it; the
+    schedule it keeps still matches the oracle."""
+    from paper_1707_00198_gb300.lbcg import Lattice
+    g, p = I.config_adjoint()          # 400 x 42 displacement channel
+    _, ref = oracle_run(g, p, 20)
+    L = Lattice(g, p, "fp64")
+    assert L.schedule == 4             # too few sweep strips for 152 SMs: FP64 takes 32x4 tiles
+    L.step(10)
+    before = L.populations()
+    sched = L.autotune(5)
+    assert sched in (0, 4, 8, 16) and L.schedule == sched
+    assert np.array_equal(L.populations(), before)
+    L.step(10)
+    out = L.populations()
+    L.close()
+    assert float(np.abs(out - ref).max()) <= TOL64
