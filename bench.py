@@ -333,7 +333,10 @@ def run_ours(args):
     achieved = alg_bytes / (step_ms / 1e3) / 1e9
     peaks = measured_peaks()
     peak, peak_src = (peaks["hbm_gbs"], "measured") if peaks and "hbm_gbs" in peaks else (6800.0, "fallback")
-    kname = f"k_step<{args.precision},ty{args.ty}>" if args.ty else f"k_sweep<{args.precision}>"
+    if args.ty:
+        kname = f"k_step<{args.precision},ty{args.ty}>"
+    else:
+        kname = "k_sweep<fp64>" if args.precision == "fp64" else f"k_sweepf<{args.precision}>"
     traffic = recorded_traffic(kname, nf)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "kernel": kname, "peak_source": peak_src,

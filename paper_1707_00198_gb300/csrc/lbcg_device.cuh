@@ -41,6 +41,11 @@ enum { BC_PERIODIC = 0, BC_CLOSED = 1, BC_INOUT = 2 };
 
 // threads of a k_sweep block; its strip has kSweepThreads - 4 interior columns
 constexpr int kSweepThreads = 128;
+__host__ __device__ constexpr int sweep_width(bool /*fp64*/) { return kSweepThreads - 4; }
+// resident k_sweepf blocks per SM it is compiled for (registers <= 65536 / (128 * this)),
+// FP32 storage and 16-bit storage
+constexpr int kSweepFMinBlocks = 5;
+constexpr int kSweepFMinBlocks16 = 6;
 
 // Per-lattice constants, resident in global memory, one entry per lattice of a handle.
 struct LatDev {

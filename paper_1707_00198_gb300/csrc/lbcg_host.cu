@@ -2,6 +2,7 @@
 // (Sec. II.C), solid normals (Eq. 32-33), work lists, device memory, graph-captured stepping,
 // observables and state transfer.  All arithmetic of the time step runs in the kernels of
 // lbcg_kernels.cu; the host only prepares geometry once per handle.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -273,10 +274,13 @@ void build_tiles(lbcg_handle* h, std::vector<int4>& tiles) {
 // columns and rows hold no fluid node are skipped.
 void build_strips(lbcg_handle* h, std::vector<int4>& strips) {
   strips.clear();
-  const int W = kSweepThreads - 4;
+  const int W = sweep_width(h->prec == LBCG_FP64);
   long long nx_strips = 0;
   for (const LatHost& L : h->lats) nx_strips += (L.nx + W - 1) / W;
-  const long long target = 152LL * 8;
+  // automatic segment height: split the strips into about 16 blocks per SM (FP64: 8), with
+  // at least 8 rows per segment.  Blocks are launched in lattice / strip / segment order,
+  // so neighbouring segments run together and their shared halo rows stay in L2.
+  const long long target = h->prec == LBCG_FP64 ? 152LL * 8 : 152LL * 16;
   for (size_t l = 0; l < h->lats.size(); ++l) {
     const LatHost& L = h->lats[l];
     int rows = h->sweep_rows;
@@ -491,6 +495,7 @@ lbcg_status lbcg_create_batch(int32_t n, const lbcg_geometry* geoms, const lbcg_
   } while (0)
   CKC(cudaMemcpy(h->d_flags, h->flags_host.data(), (size_t)node_total, cudaMemcpyHostToDevice));
   CKC(cudaMemcpy(h->d_nbmask, mask_host.data(), (size_t)node_total, cudaMemcpyHostToDevice));
+
   CKC(cudaMemcpy(h->d_lats, ld.data(), n * sizeof(LatDev), cudaMemcpyHostToDevice));
   if (!band.empty()) CKC(cudaMemcpy(h->d_band, band.data(), band.size() * sizeof(int4), cudaMemcpyHostToDevice));
   if (!ofb.empty()) CKC(cudaMemcpy(h->d_ofb, ofb.data(), ofb.size() * sizeof(OfbEntry), cudaMemcpyHostToDevice));

@@ -12,6 +12,8 @@
 //             u, nu, MRT collision with Guo forcing (Eq. 1-9, 17, 18) -> recolouring
 //             (Eq. 14) -> push of the post-collision populations to the neighbours
 //             (streaming, Eq. 15) with half-way bounce-back at solid neighbours.
+#include <algorithm>
+
 #include "lbcg_device.cuh"
 #include "lbcg_internal.h"
 
@@ -747,6 +749,305 @@ __global__ void __launch_bounds__(NTH, sizeof(typename Store<S>::T) == 4 ? 1024 
   }
 }
 
+// ------------------------------------------------------------------ k_sweepf (FP32 arithmetic)
+// The y-sweep of k_sweep for the storage forms that compute in FP32, arranged so that no
+// value is fetched from memory twice and no load is waited on right after it is issued:
+//  - the populations of row r + 1 are loaded into registers while row r is processed (the
+//    row loop is unrolled twice, so the two register buffers alternate without copies);
+//  - stage 1 keeps what the collision of the row needs, the nine totals f_a = f_a,R + f_a,B
+//    and (rho_R, rho_B), in a three-row ring in shared memory that only the owning thread
+//    reads, so the collision two rows later neither reloads nor re-sums the populations;
+//  - the moment sums and the back-transform share partial sums (fewer FP32 operations).
+template <typename S, int NTH>
+__global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSweepFMinBlocks16) k_sweepf(SweepArgs A) {
+  using T = float;
+  constexpr int RR = 5;   // rho^N / flags ring (rows r-4 .. r)
+  constexpr int RN = 3;   // n, grad ring (rows r-3 .. r-1)
+  constexpr int RF = 3;   // f totals / (rho_R, rho_B) ring (rows r-2 .. r)
+  using P = Pair<T>;
+  using V = typename P::V;
+  __shared__ T srn[RR][NTH];
+  __shared__ uint8_t sfl[RR][NTH];
+  __shared__ V sn[RN][NTH], sg[RN][NTH];
+  __shared__ T sf[RF][9][NTH];
+  __shared__ V srb[RF][NTH];
+  __shared__ LatDev sL;
+
+  const int4 sp = A.strips[blockIdx.x];
+  const int t = threadIdx.x;
+  if (t == 0) sL = A.lats[sp.x];
+  __syncthreads();
+  const int nx = sL.nx, ny = sL.ny, pitch = sL.pitch;
+  const bool px = sL.bcx == BC_PERIODIC, py = sL.bcy == BC_PERIODIC, inout = sL.bcx == BC_INOUT;
+  const T r0 = T(sL.rho0), u_in = T(sL.u_in), rho_out = T(sL.rho_out), eps2 = T(sL.grad_eps) * T(sL.grad_eps);
+  const T hsig = T(0.5) * T(sL.sigma), beta = T(sL.beta), se = T(sL.s_e), seps = T(sL.s_eps), sq = T(sL.s_q);
+  const T kDe = T(-6) * (T(1) - T(0.5) * se), kDeps = T(6) * (T(1) - T(0.5) * seps), kq = T(1) - T(0.5) * sq;
+  const T hdiff = T(sL.h_inv_nuR) - T(sL.h_inv_nuB), hsum = T(sL.h_inv_nuR) + T(sL.h_inv_nuB);
+  const uint8_t* __restrict__ fl = A.flags + sL.node_off;
+  const uint8_t* __restrict__ nbm = A.nbmask + sL.node_off;
+  const S* __restrict__ src = static_cast<const S*>(A.src) + sL.pop_off;
+  S* __restrict__ dst = static_cast<S*>(A.dst) + sL.pop_off;
+
+  const int cx = sp.y - 2 + t;
+  const int xm = wrap_or_clamp(cx, nx, px);
+  const int xl = wrap_or_clamp(cx - 1, nx, px), xr = wrap_or_clamp(cx + 1, nx, px);
+  const int tc = px ? t : min(max(t + xm - cx, 1), NTH - 2);
+  const int kxs = wrap_or_clamp(sp.y - 2 + tc, nx, px);
+  const bool interior = t >= 2 && t < NTH - 2 && cx < nx;
+  const bool edge = inout && (xm == 0 || xm == nx - 1);
+  const int ys = sp.z, ye = sp.w;
+  const int colk[3] = {(xl >> 5) * kSeg + (xl & 31) * 2, (xm >> 5) * kSeg + (xm & 31) * 2,
+                       (xr >> 5) * kSeg + (xr & 31) * 2};
+  const int rowseg = (pitch >> 5) * kSeg;
+
+  auto map_row = [&](int v) {
+    if (py) {
+      while (v < 0) v += ny;
+      while (v >= ny) v -= ny;
+      return v;
+    }
+    return v < 0 ? 0 : (v >= ny ? ny - 1 : v);
+  };
+
+  int ym3 = 0, ym2 = 0, ym1 = 0, ym0 = 0;
+  int s4 = 0, s3 = 1, s2 = 2, s1 = 3, s0 = 4;
+  int n2 = 0, n1 = 1, n0 = 2;
+  int q2 = 0, q1 = 1, q0 = 2;
+  RawNode<S> bufA, bufB;
+  uint8_t flA, flB;
+  // populations and flag of the first row
+  {
+    const int y = map_row(ys - 2);
+    bufA.load(src + y * rowseg + colk[1]);
+    flA = fl[y * pitch + xm];
+  }
+
+  auto body = [&](const int r, RawNode<S>& cur, const uint8_t f_r, RawNode<S>& nxt, uint8_t& f_nxt) {
+    {
+      const int t4 = s4;
+      s4 = s3;
+      s3 = s2;
+      s2 = s1;
+      s1 = s0;
+      s0 = t4;
+      const int tq = q2;
+      q2 = q1;
+      q1 = q0;
+      q0 = tq;
+      if (r == ys - 2) {
+        ym3 = map_row(r - 3);
+        ym2 = map_row(r - 2);
+        ym1 = map_row(r - 1);
+      } else {
+        ym3 = ym2;
+        ym2 = ym1;
+        ym1 = ym0;
+      }
+      ym0 = map_row(r);
+    }
+    // the next row's populations and flag travel while this row is processed
+    if (r + 1 <= ye + 1) {
+      const int y = map_row(r + 1);
+      nxt.load(src + y * rowseg + colk[1]);
+      f_nxt = fl[y * pitch + xm];
+    }
+    const int p = r - 2;
+    const bool collide = p >= ys && interior && !(sfl[s2][t] & F_SOLID);
+    uint8_t mask = 0;
+    if (collide) mask = nbm[ym2 * pitch + xm];
+    // ---- stage 1: rho^N, totals and colour densities of row r
+    {
+      T v = T(0);
+      if (!(f_r & F_SOLID)) {
+        T fr[9], fb[9];
+        cur.decode_to(r0, fr, fb);
+        if (edge) zou_he<T>(xm, nx, u_in, rho_out, fr, fb);
+        V srb_ = P::add(P::mk(fr[0], fb[0]), P::mk(fr[1], fb[1]));
+#pragma unroll
+        for (int a = 2; a < 9; ++a) srb_ = P::add(srb_, P::mk(fr[a], fb[a]));
+#pragma unroll
+        for (int a = 0; a < 9; ++a) sf[q0][a][t] = fr[a] + fb[a];
+        srb[q0][t] = srb_;
+        const T sr = srb_.x, sb = srb_.y;
+        const T w = (sr - sb) * rcp_(sr + sb);
+        v = sb == T(0) ? T(1) : (sr == T(0) ? T(-1) : w);
+      }
+      srn[s0][t] = v;
+      sfl[s0][t] = f_r;
+    }
+    __syncthreads();
+    // ---- stage 2: grad rho^N and n of row r - 1
+    {
+      const int tn = n2;
+      n2 = n1;
+      n1 = n0;
+      n0 = tn;
+    }
+    if (r - 1 >= ys - 1 && t >= 1 && t < NTH - 1) {
+      const uint8_t f = sfl[s1][tc];
+      T ax = T(0), ay = T(0), nxv = T(0), nyv = T(0);
+      if (!(f & F_SOLID)) {
+        if (f & F_OFB) {
+          const long long NTOT = A.node_total;
+          const T* wall = static_cast<const T*>(A.wall) + sL.node_off;
+          const int k = ym1 * pitch + kxs;
+          ax = wall[k];
+          ay = wall[NTOT + k];
+          nxv = wall[2 * NTOT + k];
+          nyv = wall[3 * NTOT + k];
+        } else {
+          const T* rm = srn[s2];
+          const T* rc = srn[s1];
+          const T* rp = srn[s0];
+          const T w1 = T(1.0 / 9.0), w2 = T(1.0 / 36.0);
+          ax = w1 * (rc[tc + 1] - rc[tc - 1]) + w2 * (rp[tc + 1] - rp[tc - 1] + rm[tc + 1] - rm[tc - 1]);
+          ay = w1 * (rp[tc] - rm[tc]) + w2 * (rp[tc + 1] + rp[tc - 1] - rm[tc - 1] - rm[tc + 1]);
+          ax *= T(3);
+          ay *= T(3);
+          const T m2 = ax * ax + ay * ay;
+          if (m2 > eps2) {
+            const T inv = rsqrtf(m2);
+            nxv = ax * inv;
+            nyv = ay * inv;
+          }
+        }
+      } else if (f & F_OSOLID) {
+        const long long NTOT = A.node_total;
+        const T* wall = static_cast<const T*>(A.wall) + sL.node_off;
+        T vx = T(0), vy = T(0), den = T(0);
+        const int yr[3] = {ym2, ym1, ym0};
+        const int sr[3] = {s2, s1, s0};
+#pragma unroll
+        for (int b = 1; b < 9; ++b) {
+          if (!(sfl[sr[ey(b) + 1]][tc + ex(b)] & F_SOLID)) {
+            const int k2 = yr[ey(b) + 1] * pitch + wrap_or_clamp(sp.y - 2 + tc + ex(b), nx, px);
+            vx += wgt<T>(b) * wall[2 * NTOT + k2];
+            vy += wgt<T>(b) * wall[3 * NTOT + k2];
+            den += wgt<T>(b);
+          }
+        }
+        if (den > T(0)) {
+          nxv = vx / den;
+          nyv = vy / den;
+        }
+      }
+      sn[n0][t] = P::mk(nxv, nyv);
+      sg[n0][t] = P::mk(ax, ay);
+    }
+    __syncthreads();
+    // ---- stage 3: collide and push row p = r - 2
+    if (!collide) return;
+    const uint8_t myf = sfl[s2][t];
+    T f[9];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) f[a] = sf[q2][a][t];
+    const V rb = srb[q2][t];
+    const T rhoR = rb.x, rhoB = rb.y, rn = srn[s2][t];
+    // grad n (Eq. 28), curvature (Eq. 13), force (Eq. 10)
+    const V* nm = sn[n2];
+    const V* n0v = sn[n1];
+    const V* np = sn[n0];
+    const V W1 = P::mk(T(1.0 / 9.0), T(1.0 / 9.0)), W2 = P::mk(T(1.0 / 36.0), T(1.0 / 36.0));
+    const V nm_l = nm[t - 1], nm_c = nm[t], nm_r = nm[t + 1];
+    const V n0_l = n0v[t - 1], n0_c = n0v[t], n0_r = n0v[t + 1];
+    const V np_l = np[t - 1], np_c = np[t], np_r = np[t + 1];
+    const V dX = P::fma(W1, P::sub(n0_r, n0_l), P::mul(W2, P::add(P::sub(np_r, np_l), P::sub(nm_r, nm_l))));
+    const V dY = P::fma(W1, P::sub(np_c, nm_c), P::mul(W2, P::sub(P::add(np_r, np_l), P::add(nm_l, nm_r))));
+    const T nxo = n0_c.x, nyo = n0_c.y;
+    const T kappa = T(3) * (-nxo * nxo * dY.y - nyo * nyo * dX.x + nxo * nyo * (dY.x + dX.y));
+    const T hsk = hsig * kappa;
+    const V gv = sg[n1][t];
+    const T Fx = hsk * gv.x, Fy = hsk * gv.y;
+    // moments (Eq. 3) from shared partial sums
+    const T p13 = f[1] + f[3], m13 = f[1] - f[3], p24 = f[2] + f[4], m24 = f[2] - f[4];
+    const T p57 = f[5] + f[7], m57 = f[5] - f[7], p68 = f[6] + f[8], m68 = f[6] - f[8];
+    const T s14 = p13 + p24, pxx = p13 - p24, s58 = p57 + p68, pxy = p57 - p68;
+    const T Bx = m57 - m68, Dy = m57 + m68;   // f5 - f6 - f7 + f8, f5 + f6 - f7 - f8
+    const T jx = m13 + Bx, jy = m24 + Dy;
+    const T qx = fmaf(T(-2), m13, Bx), qy = fmaf(T(-2), m24, Dy);
+    const T me = fmaf(T(-4), f[0], fmaf(T(2), s58, -s14));
+    const T meps = fmaf(T(4), f[0], fmaf(T(-2), s14, s58));
+    // velocity (Eq. 17), relaxation rate of the viscous moments (Eq. 5, 18)
+    const T rho = rhoR + rhoB;
+    const T irho = rcp_(rho);
+    const T ux = fmaf(T(0.5), Fx, jx) * irho;
+    const T uy = fmaf(T(0.5), Fy, jy) * irho;
+    const T inv_nu = fmaf(rn, hdiff, hsum);
+    const T sv = inv_nu * rcp_(fmaf(T(0.5), inv_nu, T(3)));
+    // non-equilibrium moments with the Guo source (Eq. 1-9)
+    const T uy2 = uy * uy, uyF = uy * Fy;
+    const T u2 = fmaf(ux, ux, uy2), uF = fmaf(ux, Fx, uyF);
+    const T De = fmaf(se, fmaf(-rho, fmaf(T(3), u2, T(-2)), me), kDe * uF);
+    const T Deps = fmaf(seps, fmaf(-rho, fmaf(T(-3), u2, T(1)), meps), kDeps * uF);
+    const T Dqx = fmaf(sq, fmaf(rho, ux, qx), kq * Fx);
+    const T Dqy = fmaf(sq, fmaf(rho, uy, qy), kq * Fy);
+    const T csv = fmaf(T(-0.5), sv, T(1));
+    const T Dxx = fmaf(sv, fmaf(-rho, fmaf(ux, ux, -uy2), pxx), -csv * (T(2) * fmaf(ux, Fx, -uyF)));
+    const T Dxy = fmaf(sv, fmaf(-rho * ux, uy, pxy), -csv * fmaf(ux, Fy, uy * Fx));
+    // back to populations: f' = f - M^-1 Delta, M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4)
+    const T ae = De * T(1.0 / 36.0), aeps = Deps * T(1.0 / 36.0);
+    const T axx = Dxx * T(0.25), axy = Dxy * T(0.25);
+    const T U1 = T(-1.0 / 6.0) * (Dqx + Fx), U2 = T(-1.0 / 6.0) * (Dqy + Fy);   // a_jx - 2 a_qx, a_jy - 2 a_qy
+    const T X = fmaf(T(1.0 / 12.0), Dqx, T(-1.0 / 6.0) * Fx);                     // a_jx + a_qx
+    const T Y = fmaf(T(1.0 / 12.0), Dqy, T(-1.0 / 6.0) * Fy);                     // a_jy + a_qy
+    const T c14 = fmaf(T(-2), aeps, -ae), c58 = fmaf(T(2), ae, aeps);
+    const T T13 = c14 + axx, T24 = c14 - axx, Pp = c58 + axy, Qm = c58 - axy;
+    const T XpY = X + Y, XmY = X - Y;
+    T fp[9];
+    fp[0] = fmaf(T(4), ae - aeps, f[0]);
+    fp[1] = (f[1] - T13) - U1;
+    fp[3] = (f[3] - T13) + U1;
+    fp[2] = (f[2] - T24) - U2;
+    fp[4] = (f[4] - T24) + U2;
+    fp[5] = (f[5] - Pp) - XpY;
+    fp[7] = (f[7] - Pp) + XpY;
+    fp[6] = (f[6] - Qm) + XmY;
+    fp[8] = (f[8] - Qm) - XmY;
+    // recolouring (Eq. 14): oR = (rho_R / rho) f' + beta (rho_R rho_B / rho) w_a e_a.n, oB = f' - oR
+    const T cR = rhoR * irho;
+    const T pc = beta * rhoR * (rhoB * irho);
+    const T c1 = pc * T(1.0 / 9.0), c2 = pc * T(1.0 / 36.0);
+    T pert[9];
+    pert[0] = T(0);
+    pert[1] = c1 * nxo;
+    pert[2] = c1 * nyo;
+    pert[3] = -pert[1];
+    pert[4] = -pert[2];
+    pert[5] = c2 * (nxo + nyo);
+    pert[8] = c2 * (nxo - nyo);
+    pert[7] = -pert[5];
+    pert[6] = -pert[8];
+    const int kn = ym2 * rowseg + colk[1];
+    const int rowk[3] = {ym3 * rowseg, ym2 * rowseg, ym1 * rowseg};
+    if (mask == 0 && !(myf & F_EDGE)) {
+#pragma unroll
+      for (int a = 0; a < 9; ++a) {
+        const T oR = fmaf(cR, fp[a], pert[a]);
+        store_pair<S>(dst + rowk[ey(a) + 1] + colk[ex(a) + 1] + a * kDir, oR, fp[a] - oR, wgt<T>(a) * r0);
+      }
+    } else {
+      const bool okx[3] = {px || cx - 1 >= 0, true, px || cx + 1 < nx};
+      const bool oky[3] = {py || p - 1 >= 0, true, py || p + 1 < ny};
+#pragma unroll
+      for (int a = 0; a < 9; ++a) {
+        const T oR = fmaf(cR, fp[a], pert[a]);
+        int k = kn + a * kDir;
+        if (a != 0) {
+          if (!(okx[ex(a) + 1] && oky[ey(a) + 1])) continue;
+          if (mask & (1u << (a - 1))) k = kn + opp(a) * kDir;
+          else k = rowk[ey(a) + 1] + colk[ex(a) + 1] + a * kDir;
+        }
+        store_pair<S>(dst + k, oR, fp[a] - oR, wgt<T>(a) * r0);
+      }
+    }
+  };
+
+  for (int r = ys - 2; r <= ye + 1; r += 2) {
+    body(r, bufA, flA, bufB, flB);
+    if (r + 1 <= ye + 1) body(r + 1, bufB, flB, bufA, flA);
+  }
+}
+
 // ------------------------------------------------------------------ layout conversion
 // host layout: double [2][9][ny][nx] (f_R block then f_B block) <-> storage pool
 template <typename S>
@@ -825,7 +1126,8 @@ static cudaError_t launch_all(const LaunchStep& p, cudaStream_t st) {
   if (p.sweep && p.macro == nullptr) {
     if (p.nstrips > 0) {
       SweepArgs B{p.lats, p.strips, p.src, p.dst, p.flags, p.nbmask, p.wall, p.node_total};
-      k_sweep<S, kSweepThreads><<<p.nstrips, kSweepThreads, 0, st>>>(B);
+      if constexpr (sizeof(T) == 4) k_sweepf<S, kSweepThreads><<<p.nstrips, kSweepThreads, 0, st>>>(B);
+      else k_sweep<S, kSweepThreads><<<p.nstrips, kSweepThreads, 0, st>>>(B);
     }
   } else if (p.ntiles > 0) {
     StepArgs A{p.lats, p.tiles, p.src, p.dst, p.flags, p.band_rn, p.wall, p.node_total, p.macro};
