@@ -41,21 +41,24 @@ DTYPE = {"fp64": "f64", "fp32": "f32", "fp16": "f16-store/f32-math", "bf16": "bf
 
 
 # ----------------------------------------------------------------------------- workloads
-def workload(name: str, seed: int = 0, lattices: int = 64):
+def workload(name: str, rank: int = 0, lattices: int = 64):
+    """The synthetic workload of one rank.  The batched sweep gives every rank the same
+    channel widths (equal work: weak scaling) with its own draw of (M, Ca, theta); the
+    single-lattice workloads are replicas."""
     if name == "batched_sweep":
-        return I.channel_sweep(lattices, seed=seed), \
+        return I.channel_sweep(lattices, seed=0, param_seed=rank if rank else None), \
             f"{lattices} displacement channels, W~U{{40..200}}, L=10W, (M,Ca,theta) grids"
     if name == "capillary":
         g, p = I.config_capillary()
         return ([g], [p]), "capillary filling 1200x80, d=40, L=800, theta=30deg, sigma=1e-2"
     if name == "fingering":
-        g, p = I.config_fingering(M=1.0, Ca=0.05, theta_deg=90.0, seed=seed)
+        g, p = I.config_fingering(M=1.0, Ca=0.05, theta_deg=90.0, seed=0)
         return ([g], [p]), "displacement channel 2000x102, M=1, Ca=0.05, theta=90deg"
     if name == "static_droplet":
         g, p = I.config_static_droplet()
         return ([g], [p]), "static droplet 100x50, R=20, theta=60deg"
     if name == "roofline_box":
-        g = I.two_wall_box(8192, 4096, bands=8, noise=1e-3, seed=seed)
+        g = I.two_wall_box(8192, 4096, bands=8, noise=1e-3, seed=0)
         return ([g], [I.Params(sigma=0.01, theta=math.radians(60))]), "two-wall box 8192x4096, 8 colour bands"
     raise SystemExit(f"unknown workload {name}")
 
@@ -81,6 +84,16 @@ def fluid_nodes(geoms) -> int:
 
 
 # ----------------------------------------------------------------------------- helpers
+def reduce_over_ranks(ms: float, nf: int, ws: int, device: str):
+    """(max over ranks of the timed region in ms, fluid nodes summed over ranks)."""
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    n = torch.tensor([float(nf)], dtype=torch.float64, device=device)
+    if ws > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(n)
+    return float(t.item()), int(round(n.item()))
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -190,7 +203,7 @@ def run_reference(args):
     if rank != 0:
         return
     from oracle import lbcg_oracle as O
-    (geoms, prms), desc = workload(args.workload, seed=0, lattices=args.lattices)
+    (geoms, prms), desc = workload(args.workload, rank=0, lattices=args.lattices)
     g, p = reference_sample(geoms, prms)
     lat = O.make_lattice(g, p.theta)
     fR, fB = O.init_state(lat, g.rhoN0, p.rho0, p)
@@ -254,6 +267,31 @@ def measure_form(geoms, prms, precision, K, W, stream, with_profile=False, ty=0)
     return lat, ms, kt, flush is not None
 
 
+def sequential_rate(lbcg, geoms, prms, precision: str, K: int, W: int, stream) -> dict:
+    """The same channels as independent single-lattice handles, stepped one after another
+    (each with its own default schedule and CUDA-graph replay): the baseline the batched
+    launch is compared with."""
+    hs = [lbcg.Lattice(g, p, precision, stream=stream.cuda_stream) for g, p in zip(geoms, prms)]
+    try:
+        for L in hs:
+            L.step(W)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for L in hs:
+                L.step(K)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+    finally:
+        for L in hs:
+            L.close()
+    nf = fluid_nodes(geoms)
+    return {"MLUPS": nf * K / (ms / 1e3) / 1e6, "steps": K, "handles": len(geoms),
+            "schedules": "each handle's default (lattices this small take 32x8 tiles)"}
+
+
 def adjoint_rate(lbcg, stream, T: int, K: int):
     """Wall time of lbcg_adjoint (forward with checkpoints + reverse sweep) for the finger
     length of a 400x42 displacement channel, M=10, Ca=0.05, theta=60 deg, in FP64."""
@@ -290,7 +328,7 @@ def run_ours(args):
     ge.build()
     from paper_1707_00198_gb300 import lbcg
 
-    (geoms, prms), desc = workload(args.workload, seed=rank, lattices=args.lattices)
+    (geoms, prms), desc = workload(args.workload, rank=rank, lattices=args.lattices)
     nf = fluid_nodes(geoms)
     nodes = sum(g.nx * g.ny for g in geoms)
     stream = torch.cuda.Stream()
@@ -317,13 +355,8 @@ def run_ours(args):
         torch.distributed.barrier()
     kms, ksteps = lbcg.lbcg_kernel_times(lat.h)
     lbcg.lbcg_profile(lat.h, False)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    nf_all = torch.tensor([float(nf)], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(nf_all)
-    ms_max = float(t.item())
-    value = float(nf_all.item()) * args.steps / (ms_max / 1e3) / 1e6
+    ms_max, nf_total = reduce_over_ranks(ms, nf, ws, "cuda")
+    value = nf_total * args.steps / (ms_max / 1e3) / 1e6
     launches = args.steps * lat.launches_per_step
     obs = lbcg.lbcg_observables(lat.h, 0, lbcg.obs_spec(ny=geoms[0].ny), raise_on_diverged=False)
 
@@ -357,7 +390,7 @@ def run_ours(args):
         lbcg.lbcg_download_state(lat.h, pin.data_ptr(), sb)
     torch.cuda.synchronize()
     te = time.perf_counter() - t0
-    e2e = {"value": nf * Ke / te / 1e6 * (float(nf_all.item()) / nf), "unit": "MLUPS", "h2d_bytes_per_step": sb,
+    e2e = {"value": nf * Ke / te / 1e6 * (nf_total / nf), "unit": "MLUPS", "h2d_bytes_per_step": sb,
            "d2h_bytes_per_step": sb, "steps": Ke,
            "path": "lbcg_upload_state (pinned) + lbcg_step(1) + lbcg_download_state per step"}
     lat.close()
@@ -374,6 +407,13 @@ def run_ours(args):
             L2.close()
             forms[prec] = {"MLUPS": nf * Kf / (msf / 1e3) / 1e6,
                            "hbm_gbs_alg": 36 * STORE_BYTES[prec] * nf * Kf / (msf / 1e3) / 1e9}
+
+    # ---- batched launch against the same channels as sequential single-lattice runs
+    seq = None
+    if rank == 0 and args.workload == "batched_sweep" and not args.no_forms:
+        seq = sequential_rate(lbcg, geoms, prms, args.precision, max(10, args.steps // 10), args.warmup, stream)
+        seq["batched_MLUPS"] = value / ws
+        seq["batched_speedup"] = seq["batched_MLUPS"] / seq["MLUPS"]
 
     # ---- the discrete adjoint on the 400x42 channel (FP64, rank 0)
     adj = None
@@ -398,7 +438,8 @@ def run_ours(args):
                            else "inputs larger than L2", "mlups_counts": "fluid-node updates"},
                 "hbm_gbs_alg": whole_gbs, "hbm_frac_alg": whole_gbs / peak,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-                "forms": forms, "adjoint": adj, "nonfinite_lattice0": obs.get("nonfinite", None)}
+                "forms": forms, "batched_vs_sequential": seq, "adjoint": adj,
+                "nonfinite_lattice0": obs.get("nonfinite", None)}
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()

@@ -175,10 +175,11 @@ lbcg_status lbcg_set_tile(lbcg_handle* h, int32_t ty);
  * if dJ_dtheta_node is not NULL, per node [ny*nx] (zero off the outermost fluid nodes).
  * Objectives: LBCG_OBJ_WEIGHTED, J = sum_x weight(x) rho^N(x) (weight: host [ny*nx]);
  * LBCG_OBJ_FINGER_LENGTH, J = x_tip - x_cl (Sec. III.D; rows as in lbcg_obs_spec), whose
- * derivative is taken at the crossing cells found at T.  FP64 single-lattice handles only
+ * derivative is taken at the crossing cells found at T; LBCG_OBJ_RED_MASS, J = the red
+ * (invading) fluid's mass sum_x rho_R(x), i.e. the displaced mass plus its initial value.  FP64 single-lattice handles only
  * (else LBCG_E_UNSUPPORTED); device memory for nsteps/checkpoint + checkpoint + 2 states
  * is allocated for the call and freed before it returns. */
-enum { LBCG_OBJ_WEIGHTED = 0, LBCG_OBJ_FINGER_LENGTH = 1 };
+enum { LBCG_OBJ_WEIGHTED = 0, LBCG_OBJ_FINGER_LENGTH = 1, LBCG_OBJ_RED_MASS = 2 };
 typedef struct {
   int64_t nsteps, checkpoint;
   int32_t objective;

@@ -533,6 +533,20 @@ __global__ void __launch_bounds__(kAdjThreads) k_seed_weighted(AdjDev A, const d
   A.lrn[i] = is_solid(A, x, y) ? 0.0 : c[i];
 }
 
+// Seed for J = sum over fluid nodes of rho_R = sum_a f_a,R (the red mass) of the stored state.
+__global__ void __launch_bounds__(kAdjThreads) k_seed_red_mass(AdjDev A) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.N) return;
+  const int N = A.N;
+  const int x = i % A.L.nx, y = i / A.L.nx;
+  const double one = is_solid(A, x, y) ? 0.0 : 1.0;
+  for (int a = 0; a < 9; ++a) {
+    A.lf_r[a * N + i] = one;
+    A.lf_b[a * N + i] = 0.0;
+  }
+  A.lrn[i] = 0.0;
+}
+
 }  // namespace
 
 // One reverse step: lam <- (d step / d state)^T lam_next, parameter adjoints accumulated.
@@ -548,10 +562,11 @@ cudaError_t adjoint_step(const AdjDev& A, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t adjoint_seed(const AdjDev& A, const double* c, cudaStream_t st) {
+cudaError_t adjoint_seed(const AdjDev& A, const double* c, bool red_mass, cudaStream_t st) {
   const int b = nblk(A.N);
   fwd_local<<<b, kAdjThreads, 0, st>>>(A);   // also clears lrnt
-  k_seed_weighted<<<b, kAdjThreads, 0, st>>>(A, c);
+  if (red_mass) k_seed_red_mass<<<b, kAdjThreads, 0, st>>>(A);
+  else k_seed_weighted<<<b, kAdjThreads, 0, st>>>(A, c);
   adj_rho<<<b, kAdjThreads, 0, st>>>(A);
   return cudaGetLastError();
 }

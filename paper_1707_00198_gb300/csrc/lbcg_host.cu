@@ -278,15 +278,18 @@ void build_strips(lbcg_handle* h, std::vector<int4>& strips) {
   long long nx_strips = 0;
   for (const LatHost& L : h->lats) nx_strips += (L.nx + W - 1) / W;
   // automatic segment height: split the strips into about 16 blocks per SM (FP64: 8), with
-  // at least 8 rows per segment.  Blocks are launched in lattice / strip / segment order,
-  // so neighbouring segments run together and their shared halo rows stay in L2.
-  const long long target = h->prec == LBCG_FP64 ? 152LL * 8 : 152LL * 16;
+  // at least 24 rows per segment (FP64: 8), since each segment also sweeps 4 warm-up rows.
+  // Blocks are launched in lattice / strip / segment order, so neighbouring segments run
+  // together and their shared halo rows stay in L2.
+  const bool fp64 = h->prec == LBCG_FP64;
+  const long long target = fp64 ? 152LL * 8 : 152LL * 16;
+  const int min_rows = fp64 ? 8 : 24;
   for (size_t l = 0; l < h->lats.size(); ++l) {
     const LatHost& L = h->lats[l];
     int rows = h->sweep_rows;
     if (rows <= 0) {
       const long long k = nx_strips >= target ? 1 : (target + nx_strips - 1) / nx_strips;
-      rows = int(std::max<long long>(8, (L.ny + k - 1) / k));
+      rows = int(std::max<long long>(min_rows, (L.ny + k - 1) / k));
     }
     for (int x0 = 0; x0 < L.nx; x0 += W)
       for (int y0 = 0; y0 < L.ny; y0 += rows) {
@@ -797,7 +800,8 @@ lbcg_status lbcg_adjoint(lbcg_handle* h, const lbcg_adjoint_spec* spec, lbcg_gra
   if (h->lats.size() != 1) return fail(LBCG_E_UNSUPPORTED, "the adjoint runs on single-lattice handles");
   if (spec->nsteps < 1 || spec->checkpoint < 1) return fail(LBCG_E_ARG, "nsteps and checkpoint must be >= 1");
   if (spec->objective == LBCG_OBJ_WEIGHTED && !spec->weight) return fail(LBCG_E_ARG, "weighted objective needs weight");
-  if (spec->objective != LBCG_OBJ_WEIGHTED && spec->objective != LBCG_OBJ_FINGER_LENGTH)
+  if (spec->objective != LBCG_OBJ_WEIGHTED && spec->objective != LBCG_OBJ_FINGER_LENGTH &&
+      spec->objective != LBCG_OBJ_RED_MASS)
     return fail(LBCG_E_ARG, "unknown objective %d", spec->objective);
   const LatHost& L = h->lats[0];
   const int nx = L.nx, ny = L.ny, N = nx * ny;
@@ -890,7 +894,11 @@ lbcg_status lbcg_adjoint(lbcg_handle* h, const lbcg_adjoint_spec* spec, lbcg_gra
   if (s != LBCG_OK) return s;
   const double* rhoN = fields.data() + N;
   double J = 0.0;
-  if (spec->objective == LBCG_OBJ_WEIGHTED) {
+  if (spec->objective == LBCG_OBJ_RED_MASS) {
+    const double* rho = fields.data();
+    for (int i = 0; i < N; ++i)
+      if (!L.solid[i]) J += 0.5 * rho[i] * (1.0 + rhoN[i]);
+  } else if (spec->objective == LBCG_OBJ_WEIGHTED) {
     for (int i = 0; i < N; ++i)
       if (!L.solid[i]) {
         cw[i] = spec->weight[i];
@@ -936,7 +944,7 @@ lbcg_status lbcg_adjoint(lbcg_handle* h, const lbcg_adjoint_spec* spec, lbcg_gra
   CK(h, cudaMemcpyAsync(c_dev, cw.data(), N * 8, cudaMemcpyHostToDevice, h->stream));
   A.src = static_cast<const double*>(h->pool[h->cur]);
   A.lam = lamA;
-  CK(h, adjoint_seed(A, c_dev, h->stream));
+  CK(h, adjoint_seed(A, c_dev, spec->objective == LBCG_OBJ_RED_MASS, h->stream));
   // ---- reverse, one checkpoint segment at a time.  A segment's work (recompute its states
   // from the checkpoint, then reverse its steps) is captured once per (length, adjoint
   // buffer parity) as a CUDA graph and replayed; only the checkpoint copy is outside.

@@ -81,7 +81,8 @@ struct AdjDev {
 };
 
 cudaError_t adjoint_step(const AdjDev& A, cudaStream_t st);
-cudaError_t adjoint_seed(const AdjDev& A, const double* weight, cudaStream_t st);
+// seed lam = dJ/d(state): J = sum weight * rho^N (red_mass false) or the red mass (true)
+cudaError_t adjoint_seed(const AdjDev& A, const double* weight, bool red_mass, cudaStream_t st);
 
 // Sets the calling thread's message returned by lbcg_last_error() (lbcg_host.cu).
 void set_last_error(const char* msg);

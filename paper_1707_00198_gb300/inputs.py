@@ -232,12 +232,17 @@ THETA_GRID = (30.0, 60.0, 90.0, 120.0, 150.0)
 
 
 def channel_sweep(n: int = 64, seed: int = 0, wmin: int = 40, wmax: int = 200,
-                  aspect: int = 10, x_I_frac: float = 0.05):
+                  aspect: int = 10, x_I_frac: float = 0.05, param_seed: Optional[int] = None):
     """A batch of displacement channels of uneven size with (M, Ca, theta) drawn from the grids.
 
-    Widths W ~ U{wmin..wmax}, lengths 10*W; returns (geometries, params).
+    Widths W ~ U{wmin..wmax}, lengths 10*W; returns (geometries, params).  With
+    ``param_seed`` the widths still come from ``seed`` but (M, Ca, theta) and the interface
+    noise come from ``param_seed``: batches of equal size with different parameters (one
+    per rank of a weak-scaling run).
     """
     rng = np.random.default_rng(seed)
+    prng = None if param_seed is None else np.random.default_rng(param_seed)
+    gseed = seed if param_seed is None else param_seed
     geoms: List[Geometry] = []
     prms: List[Params] = []
     for i in range(n):
@@ -245,8 +250,10 @@ def channel_sweep(n: int = 64, seed: int = 0, wmin: int = 40, wmax: int = 200,
         M = float(rng.choice(M_GRID))
         Ca = float(rng.choice(CA_GRID))
         th = float(rng.choice(THETA_GRID))
+        if prng is not None:
+            M, Ca, th = float(prng.choice(M_GRID)), float(prng.choice(CA_GRID)), float(prng.choice(THETA_GRID))
         geoms.append(displacement_channel(W=W, L=aspect * W, x_I=max(4.0, x_I_frac * aspect * W),
-                                          seed=seed * 1000 + i))
+                                          seed=gseed * 1000 + i))
         prms.append(fingering_params(M, Ca, th))
     return geoms, prms
 

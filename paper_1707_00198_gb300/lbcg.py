@@ -61,7 +61,8 @@ class lbcg_grads(C.Structure):
                 ("dJ_dtheta", C.c_double), ("dJ_dtheta_node", C.POINTER(C.c_double))]
 
 
-LBCG_OBJ_WEIGHTED, LBCG_OBJ_FINGER_LENGTH = 0, 1
+LBCG_OBJ_WEIGHTED, LBCG_OBJ_FINGER_LENGTH, LBCG_OBJ_RED_MASS = 0, 1, 2
+OBJECTIVES = {"weighted": LBCG_OBJ_WEIGHTED, "finger_length": LBCG_OBJ_FINGER_LENGTH, "red_mass": LBCG_OBJ_RED_MASS}
 
 
 class LBCGError(RuntimeError):
@@ -263,14 +264,15 @@ def lbcg_field_moments_noalloc(fields_ptr: int, mask_ptr: int, nx: int, ny: int,
 
 
 def lbcg_adjoint(h: int, nx: int, ny: int, nsteps: int, checkpoint: int, weight: Optional[np.ndarray] = None,
-                 tip_rows=None, cl_rows=None) -> dict:
+                 tip_rows=None, cl_rows=None, objective: Optional[str] = None) -> dict:
     """Run nsteps forward, then the reverse sweep; returns J and its gradients.  With `weight`
-    ([ny, nx]) J = sum weight * rho^N at the last step; without it J is the finger length."""
+    ([ny, nx]) J = sum weight * rho^N at the last step; otherwise `objective` selects
+    "finger_length" (the default) or "red_mass"."""
     if weight is not None:
         w = np.ascontiguousarray(weight, dtype=np.float64).reshape(ny, nx)
         obj, wp = LBCG_OBJ_WEIGHTED, _dptr(w)
     else:
-        w, obj, wp = None, LBCG_OBJ_FINGER_LENGTH, None
+        w, obj, wp = None, OBJECTIVES[objective or "finger_length"], None
     o = obs_spec(ny=ny, tip_rows=tip_rows, cl_rows=cl_rows)
     spec = lbcg_adjoint_spec(nsteps, checkpoint, obj, wp, o.tip_row0, o.tip_row1, o.cl_row0, o.cl_row1)
     dth = np.zeros((ny, nx), dtype=np.float64)
