@@ -60,6 +60,7 @@ struct lbcg_handle {
   int cur = 0;
   uint8_t* d_flags = nullptr;
   uint8_t* d_nbmask = nullptr;
+  int* d_err = nullptr;    // device error word (a sweep block's bounded wait ran out)
   void* d_band_rn = nullptr;
   void* d_wall = nullptr;
   double* d_macro = nullptr;
@@ -316,6 +317,7 @@ LaunchStep make_launch(lbcg_handle* h, int src, double* macro, int tile_begin, i
   p.dst = h->pool[src ^ 1];
   p.flags = h->d_flags;
   p.nbmask = h->d_nbmask;
+  p.err = h->d_err;
   p.band_rn = h->d_band_rn;
   p.wall = h->d_wall;
   p.node_total = h->node_total;
@@ -332,7 +334,7 @@ void free_handle(lbcg_handle* h) {
   for (cudaEvent_t e : h->events) cudaEventDestroy(e);
   void* ptrs[] = {h->pool[0], h->pool[1], h->d_flags, h->d_band_rn, h->d_wall,   h->d_macro,
                   h->d_lats,  h->d_tiles, h->d_band,  h->d_ofb,     h->d_obs,    h->d_strips,
-                  h->d_nbmask};
+                  h->d_nbmask, h->d_err};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -364,6 +366,16 @@ lbcg_status ensure_macro(lbcg_handle* h) {
       return fail(LBCG_E_NOMEM, "cannot allocate the macroscopic fields");
     CK(h, cudaMemsetAsync(h->d_macro, 0, 4 * (size_t)h->node_total * sizeof(double), h->stream));
   }
+  return LBCG_OK;
+}
+
+// After a synchronisation: a sweep block gave up waiting for a staged row (the data of that
+// step is then unreliable).  The word stays set; the handle should be recreated.
+lbcg_status check_device_error(lbcg_handle* h) {
+  int e = 0;
+  if (cudaMemcpy(&e, h->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return cuda_fail(h, cudaGetLastError(), "reading the device error word");
+  if (e) return fail(LBCG_E_TIMEOUT, "a sweep kernel's bounded wait for a staged row ran out");
   return LBCG_OK;
 }
 
@@ -478,6 +490,7 @@ lbcg_status lbcg_create_batch(int32_t n, const lbcg_geometry* geoms, const lbcg_
   auto alloc = [&](void** p, size_t bytes) { return cudaMalloc(p, std::max<size_t>(bytes, 16)) == cudaSuccess; };
   bool ok = alloc(&h->pool[0], 18 * (size_t)node_total * es) && alloc(&h->pool[1], 18 * (size_t)node_total * es) &&
             alloc((void**)&h->d_flags, (size_t)node_total) && alloc((void**)&h->d_nbmask, (size_t)node_total) &&
+            alloc((void**)&h->d_err, sizeof(int)) &&
             alloc(&h->d_band_rn, (size_t)node_total * cs) &&
             alloc(&h->d_wall, 4 * (size_t)node_total * cs) && alloc((void**)&h->d_lats, n * sizeof(LatDev)) &&
             alloc((void**)&h->d_band, band.size() * sizeof(int4)) &&
@@ -498,6 +511,8 @@ lbcg_status lbcg_create_batch(int32_t n, const lbcg_geometry* geoms, const lbcg_
   } while (0)
   CKC(cudaMemcpy(h->d_flags, h->flags_host.data(), (size_t)node_total, cudaMemcpyHostToDevice));
   CKC(cudaMemcpy(h->d_nbmask, mask_host.data(), (size_t)node_total, cudaMemcpyHostToDevice));
+  CKC(cudaMemset(h->d_err, 0, sizeof(int)));
+  CKC(prepare_kernels(precision));
 
   CKC(cudaMemcpy(h->d_lats, ld.data(), n * sizeof(LatDev), cudaMemcpyHostToDevice));
   if (!band.empty()) CKC(cudaMemcpy(h->d_band, band.data(), band.size() * sizeof(int4), cudaMemcpyHostToDevice));
@@ -617,6 +632,8 @@ lbcg_status lbcg_observables(lbcg_handle* h, int32_t lattice, const lbcg_obs_spe
   double o[kObsOut];
   CK(h, cudaMemcpyAsync(o, res, sizeof(o), cudaMemcpyDeviceToHost, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
+  s = check_device_error(h);
+  if (s != LBCG_OK) return s;
   memset(out, 0, sizeof(*out));
   out->step = h->step;
   out->mass_R = o[0];
@@ -688,7 +705,7 @@ lbcg_status lbcg_get_populations(lbcg_handle* h, int32_t lattice, double* host_o
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   cudaFree(tmp);
   if (e != cudaSuccess) return cuda_fail(h, e, "get_populations");
-  return LBCG_OK;
+  return check_device_error(h);
 }
 
 lbcg_status lbcg_set_populations(lbcg_handle* h, int32_t lattice, const double* host_in) {
@@ -751,7 +768,7 @@ lbcg_status lbcg_download_state(lbcg_handle* h, void* host_out, size_t bytes) {
   if (!host_out || bytes != lbcg_state_bytes(h)) return fail(LBCG_E_ARG, "state size mismatch");
   CK(h, cudaMemcpyAsync(host_out, h->pool[h->cur], bytes, cudaMemcpyDeviceToHost, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
-  return LBCG_OK;
+  return check_device_error(h);
 }
 
 }  // extern "C"

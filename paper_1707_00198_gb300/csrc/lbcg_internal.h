@@ -31,9 +31,13 @@ struct LaunchStep {
   int sweep;              // 1: k_sweep over strips, 0: k_step over tiles
   double* macro;          // non-null: write macroscopic fields instead of stepping (tiles)
   cudaEvent_t* ev;        // non-null: 6 events recorded around k_band, k_wall, k_step
+  int* err;               // device error word: a sweep block's bounded wait ran out
 };
 
 cudaError_t launch_step(int prec, const LaunchStep& p, cudaStream_t st);
+// One-time kernel attributes for a precision (the sweep's dynamic shared memory); called
+// before any launch or graph capture of that precision.
+cudaError_t prepare_kernels(int prec);
 cudaError_t launch_to_storage(int prec, const LatDev* lats, int lat, long long nn, const double* in,
                               const uint8_t* flags, void* pool, cudaStream_t st);
 cudaError_t launch_from_storage(int prec, const LatDev* lats, int lat, long long nn, const void* pool,

@@ -461,6 +461,7 @@ struct SweepArgs {
   const uint8_t* nbmask;  // bit a-1 set: the neighbour in direction a (1..8) is solid
   const void* wall;
   long long node_total;
+  int* err;               // set to 1 by a block whose wait for a staged row ran out (k_sweepf)
 };
 
 template <typename S, int NTH>
@@ -758,6 +759,56 @@ __global__ void __launch_bounds__(NTH, sizeof(typename Store<S>::T) == 4 ? 1024 
 //    and (rho_R, rho_B), in a three-row ring in shared memory that only the owning thread
 //    reads, so the collision two rows later neither reloads nor re-sums the populations;
 //  - the moment sums and the back-transform share partial sums (fewer FP32 operations).
+// ---- bulk asynchronous copies (global -> shared) completing on an mbarrier
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return static_cast<unsigned>(__cvta_generic_to_shared(p)); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// generic-proxy reads of a buffer are ordered before the async-proxy write that reuses it
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+// bounded wait: gives up after about a second of polling and reports it through *err
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int* err) {
+  for (int i = 0; i < (1 << 22); ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  atomicOr(err, 1);
+  return false;
+}
+// segments of a staged row: up to 5 contiguous ones for the strip's columns, plus one for the
+// columns a periodic strip wraps to
+constexpr int kStageSegs = 6;
+template <typename S>
+constexpr int sweepf_dyn_smem() { return 2 * kStageSegs * kSeg * int(sizeof(S)); }
+
+template <typename S>
+__device__ __forceinline__ void staged_pair(const S* row, int a, float& lo, float& hi) {
+  if constexpr (sizeof(S) == 4) {
+    const float2 v = *reinterpret_cast<const float2*>(row + a * kDir);
+    lo = v.x;
+    hi = v.y;
+  } else {
+    Store<S>::unpack(*reinterpret_cast<const uint32_t*>(row + a * kDir), lo, hi);
+  }
+}
+
 template <typename S, int NTH>
 __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSweepFMinBlocks16) k_sweepf(SweepArgs A) {
   using T = float;
@@ -772,6 +823,10 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
   __shared__ T sf[RF][9][NTH];
   __shared__ V srb[RF][NTH];
   __shared__ LatDev sL;
+  // two staged rows of populations (dynamic shared memory): [slot][kStageSegs * kSeg]
+  extern __shared__ __align__(128) unsigned char sraw_bytes[];
+  S* sraw = reinterpret_cast<S*>(sraw_bytes);
+  __shared__ __align__(8) uint64_t sbar[2];
 
   const int4 sp = A.strips[blockIdx.x];
   const int t = threadIdx.x;
@@ -799,6 +854,17 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
   const int colk[3] = {(xl >> 5) * kSeg + (xl & 31) * 2, (xm >> 5) * kSeg + (xm & 31) * 2,
                        (xr >> 5) * kSeg + (xr & 31) * 2};
   const int rowseg = (pitch >> 5) * kSeg;
+  // staged segments of this strip: [sA, sB] holds columns max(x0-2, 0) .. min(x0+125, nx-1);
+  // sX (or -1) the segment a periodic edge strip wraps to.  soff: this column's offset in a
+  // staged row, -1 if its segment is not staged (it is then loaded directly).
+  const int sA = max(sp.y - 2, 0) >> 5, sB = min(sp.y + NTH - 3, nx - 1) >> 5;
+  int sX = -1;
+  if (px && sp.y - 2 < 0 && ((nx - 1) >> 5) > sB) sX = (nx - 1) >> 5;
+  else if (px && sp.y + NTH - 3 >= nx && sA > 0) sX = 0;
+  const int soff = ((xm >> 5) >= sA && (xm >> 5) <= sB) ? ((xm >> 5) - sA) * kSeg + (xm & 31) * 2
+                   : ((xm >> 5) == sX ? (kStageSegs - 1) * kSeg + (xm & 31) * 2 : -1);
+  const unsigned bytesA = unsigned((sB - sA + 1) * kSeg * sizeof(S));
+  const unsigned bytesX = sX >= 0 ? unsigned(kSeg * sizeof(S)) : 0u;
 
   auto map_row = [&](int v) {
     if (py) {
@@ -813,16 +879,27 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
   int s4 = 0, s3 = 1, s2 = 2, s1 = 3, s0 = 4;
   int n2 = 0, n1 = 1, n0 = 2;
   int q2 = 0, q1 = 1, q0 = 2;
-  RawNode<S> bufA, bufB;
-  uint8_t flA, flB;
-  // populations and flag of the first row
-  {
-    const int y = map_row(ys - 2);
-    bufA.load(src + y * rowseg + colk[1]);
-    flA = fl[y * pitch + xm];
+  // issue the bulk copies of (mapped) row y into staging slot `slot` (one thread)
+  auto stage_row = [&](int y, int slot) {
+    S* d = sraw + slot * (kStageSegs * kSeg);
+    const S* g = src + (long long)y * rowseg;
+    fence_proxy_async();
+    mbar_expect_tx(&sbar[slot], bytesA + bytesX);
+    bulk_copy_g2s(d, g + sA * kSeg, bytesA, &sbar[slot]);
+    if (sX >= 0) bulk_copy_g2s(d + (kStageSegs - 1) * kSeg, g + sX * kSeg, bytesX, &sbar[slot]);
+  };
+  unsigned phase = 0;   // bit s: parity of the next completion of slot s
+  bool lost = false;    // a wait ran out: copies may still be in flight at the end
+  if (t == 0) {
+    mbar_init(&sbar[0], 1);
+    mbar_init(&sbar[1], 1);
+    mbar_init_fence();
   }
+  __syncthreads();
+  if (t == 0) stage_row(map_row(ys - 2), (ys - 2) & 1);
+  uint8_t f_cur = fl[map_row(ys - 2) * pitch + xm], f_nxt = 0;
 
-  auto body = [&](const int r, RawNode<S>& cur, const uint8_t f_r, RawNode<S>& nxt, uint8_t& f_nxt) {
+  auto body = [&](const int r) {
     {
       const int t4 = s4;
       s4 = s3;
@@ -845,12 +922,14 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
       }
       ym0 = map_row(r);
     }
-    // the next row's populations and flag travel while this row is processed
+    // the next row's populations (bulk copy) and flag travel while this row is processed;
+    // its slot held row r - 1, whose last reader finished before the previous barriers
     if (r + 1 <= ye + 1) {
       const int y = map_row(r + 1);
-      nxt.load(src + y * rowseg + colk[1]);
+      if (t == 0) stage_row(y, (r + 1) & 1);
       f_nxt = fl[y * pitch + xm];
     }
+    const uint8_t f_r = f_cur;
     const int p = r - 2;
     const bool collide = p >= ys && interior && !(sfl[s2][t] & F_SOLID);
     uint8_t mask = 0;
@@ -858,9 +937,22 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
     // ---- stage 1: rho^N, totals and colour densities of row r
     {
       T v = T(0);
+      const int slot = r & 1;
+      if (!mbar_wait(&sbar[slot], (phase >> slot) & 1u, A.err)) lost = true;
+      phase ^= 1u << slot;
       if (!(f_r & F_SOLID)) {
         T fr[9], fb[9];
-        cur.decode_to(r0, fr, fb);
+        if (soff >= 0) {
+          const S* row = sraw + slot * (kStageSegs * kSeg) + soff;
+#pragma unroll
+          for (int a = 0; a < 9; ++a) {
+            T lo, hi;
+            staged_pair<S>(row, a, lo, hi);
+            decode<S, T>(lo, hi, wgt<T>(a) * r0, fr[a], fb[a]);
+          }
+        } else {
+          load_raw<S>(src + ym0 * rowseg + colk[1], r0, fr, fb);
+        }
         if (edge) zou_he<T>(xm, nx, u_in, rho_out, fr, fb);
         V srb_ = P::add(P::mk(fr[0], fb[0]), P::mk(fr[1], fb[1]));
 #pragma unroll
@@ -1042,10 +1134,13 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
     }
   };
 
-  for (int r = ys - 2; r <= ye + 1; r += 2) {
-    body(r, bufA, flA, bufB, flB);
-    if (r + 1 <= ye + 1) body(r + 1, bufB, flB, bufA, flA);
+  for (int r = ys - 2; r <= ye + 1; ++r) {
+    body(r);
+    f_cur = f_nxt;
   }
+  // after a lost wait, do not leave with copies into this block's shared memory in flight
+  if (lost)
+    for (int j = 0; j < 2; ++j) mbar_wait(&sbar[j], (phase >> j) & 1u, A.err);
 }
 
 // ------------------------------------------------------------------ layout conversion
@@ -1125,8 +1220,9 @@ static cudaError_t launch_all(const LaunchStep& p, cudaStream_t st) {
   rec(4);
   if (p.sweep && p.macro == nullptr) {
     if (p.nstrips > 0) {
-      SweepArgs B{p.lats, p.strips, p.src, p.dst, p.flags, p.nbmask, p.wall, p.node_total};
-      if constexpr (sizeof(T) == 4) k_sweepf<S, kSweepThreads><<<p.nstrips, kSweepThreads, 0, st>>>(B);
+      SweepArgs B{p.lats, p.strips, p.src, p.dst, p.flags, p.nbmask, p.wall, p.node_total, p.err};
+      if constexpr (sizeof(T) == 4)
+        k_sweepf<S, kSweepThreads><<<p.nstrips, kSweepThreads, sweepf_dyn_smem<S>(), st>>>(B);
       else k_sweep<S, kSweepThreads><<<p.nstrips, kSweepThreads, 0, st>>>(B);
     }
   } else if (p.ntiles > 0) {
@@ -1149,6 +1245,21 @@ static cudaError_t launch_all(const LaunchStep& p, cudaStream_t st) {
   }
   rec(5);
   return cudaGetLastError();
+}
+
+template <typename S>
+static cudaError_t prepare_sweepf() {
+  return cudaFuncSetAttribute(k_sweepf<S, kSweepThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              sweepf_dyn_smem<S>());
+}
+
+cudaError_t prepare_kernels(int prec) {
+  switch (prec) {
+    case 1: return prepare_sweepf<float>();
+    case 2: return prepare_sweepf<__half>();
+    case 3: return prepare_sweepf<__nv_bfloat16>();
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_step(int prec, const LaunchStep& p, cudaStream_t st) {
