@@ -292,15 +292,55 @@ def sequential_rate(lbcg, geoms, prms, precision: str, K: int, W: int, stream) -
             "schedules": "each handle's default (lattices this small take 32x8 tiles)"}
 
 
-def adjoint_rate(lbcg, stream, T: int, K: int):
+def observable_errors(lbcg, stream) -> dict:
+    """Error of each storage form's observables against an FP64 run of the same case: the
+    sessile droplet (100x50, theta 60 deg) after 2000 steps -- contact angle and colour masses --
+    and a fingering channel (400x42, M=5, Ca=0.05, theta=60 deg) after 4000 steps -- finger-tip
+    position, finger length and contact-line speed over the last 2000 steps."""
+    gd, pd = I.config_static_droplet()
+    gf, pf = I.displacement_channel(W=40, L=400, x_I=40.0, seed=0), I.fingering_params(5.0, 0.05, 60.0)
+
+    def droplet(prec):
+        L = lbcg.Lattice(gd, pd, prec, stream=stream.cuda_stream)
+        try:
+            o0 = L.observables(wall_y=0.5)
+            L.step(2000)
+            o = L.observables(wall_y=0.5)
+        finally:
+            L.close()
+        return o["theta_deg"], o["mass_R"], o["mass_B"], o0["mass_R"]
+
+    def finger(prec):
+        L = lbcg.Lattice(gf, pf, prec, stream=stream.cuda_stream)
+        try:
+            L.step(2000)
+            a = L.observables()
+            L.step(2000)
+            b = L.observables()
+        finally:
+            L.close()
+        return b["x_tip"], b["x_tip"] - b["x_cl"], (b["x_cl"] - a["x_cl"]) / 2000.0
+
+    ref_d, ref_f = droplet("fp64"), finger("fp64")
+    out = {"reference": {"theta_deg": ref_d[0], "x_tip": ref_f[0], "finger_length": ref_f[1], "dS_dt": ref_f[2]}}
+    for prec in ("fp32", "fp16", "bf16"):
+        d, f = droplet(prec), finger(prec)
+        out[prec] = {"theta_deg_err": d[0] - ref_d[0], "mass_R_rel_err": (d[1] - ref_d[1]) / ref_d[1],
+                     "x_tip_rel_err": (f[0] - ref_f[0]) / ref_f[0], "finger_length_err": f[1] - ref_f[1],
+                     "dS_dt_rel_err": (f[2] - ref_f[2]) / ref_f[2]}
+    return out
+
+
+def adjoint_rate(lbcg, stream, T: int, K: int, precision: str = "fp32"):
     """Wall time of lbcg_adjoint (forward with checkpoints + reverse sweep) for the finger
-    length of a 400x42 displacement channel, M=10, Ca=0.05, theta=60 deg, in FP64."""
+    length of a 400x42 displacement channel, M=10, Ca=0.05, theta=60 deg; the forward steps
+    and checkpoints in `precision`, the reverse sweep in FP64."""
     g, p = I.config_adjoint()
-    L = lbcg.Lattice(g, p, "fp64", stream=stream.cuda_stream)
+    L = lbcg.Lattice(g, p, precision, stream=stream.cuda_stream)
     try:
         L.adjoint(2 * K, K)          # warm-up: first launches, allocations
         L.close()
-        L = lbcg.Lattice(g, p, "fp64", stream=stream.cuda_stream)
+        L = lbcg.Lattice(g, p, precision, stream=stream.cuda_stream)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         out = L.adjoint(T, K)
@@ -312,7 +352,8 @@ def adjoint_rate(lbcg, stream, T: int, K: int):
         L.close()
     nf = int((g.solid == 0).sum())
     return {"workload": f"displacement channel {g.nx}x{g.ny}, M=10, Ca=0.05, theta=60deg, J = finger length",
-            "precision": "fp64", "steps": T, "checkpoint": K, "seconds": t, "s_per_step": t / T,
+            "precision": f"{precision} forward, fp64 reverse", "steps": T, "checkpoint": K, "seconds": t,
+            "s_per_step": t / T,
             "mlups_forward_plus_reverse": nf * T / t / 1e6, "J": out["J"], "dJ_dtheta": out["dtheta"],
             "dJ_dsigma": out["dsigma"], "dJ_dnu_R": out["dnu_R"], "dJ_dnu_B": out["dnu_B"],
             "timing": "host clock around the whole call (it synchronises)"}
@@ -415,10 +456,14 @@ def run_ours(args):
         seq["batched_MLUPS"] = value / ws
         seq["batched_speedup"] = seq["batched_MLUPS"] / seq["MLUPS"]
 
+    # ---- observable error of the storage forms against FP64 (rank 0)
+    obs_err = observable_errors(lbcg, stream) if (rank == 0 and not args.no_forms) else None
+
     # ---- the discrete adjoint on the 400x42 channel (FP64, rank 0)
     adj = None
     if rank == 0 and not args.no_adjoint:
-        adj = adjoint_rate(lbcg, stream, args.adjoint_steps, args.adjoint_checkpoint)
+        adj = adjoint_rate(lbcg, stream, args.adjoint_steps, args.adjoint_checkpoint, "fp32")
+        adj["fp64"] = adjoint_rate(lbcg, stream, args.adjoint_steps, args.adjoint_checkpoint, "fp64")
 
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N=1 only)
     cpu = None
@@ -438,7 +483,7 @@ def run_ours(args):
                            else "inputs larger than L2", "mlups_counts": "fluid-node updates"},
                 "hbm_gbs_alg": whole_gbs, "hbm_frac_alg": whole_gbs / peak,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-                "forms": forms, "batched_vs_sequential": seq, "adjoint": adj,
+                "forms": forms, "observable_error_vs_fp64": obs_err, "batched_vs_sequential": seq, "adjoint": adj,
                 "nonfinite_lattice0": obs.get("nonfinite", None)}
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -176,9 +176,12 @@ lbcg_status lbcg_set_tile(lbcg_handle* h, int32_t ty);
  * Objectives: LBCG_OBJ_WEIGHTED, J = sum_x weight(x) rho^N(x) (weight: host [ny*nx]);
  * LBCG_OBJ_FINGER_LENGTH, J = x_tip - x_cl (Sec. III.D; rows as in lbcg_obs_spec), whose
  * derivative is taken at the crossing cells found at T; LBCG_OBJ_RED_MASS, J = the red
- * (invading) fluid's mass sum_x rho_R(x), i.e. the displaced mass plus its initial value.  FP64 single-lattice handles only
- * (else LBCG_E_UNSUPPORTED); device memory for nsteps/checkpoint + checkpoint + 2 states
- * is allocated for the call and freed before it returns. */
+ * (invading) fluid's mass sum_x rho_R(x), i.e. the displaced mass plus its initial value.
+ * Single-lattice FP64 or FP32 handles (else LBCG_E_UNSUPPORTED).  On an FP32 handle the
+ * forward steps, checkpoints and segment recomputation are the FP32 step; the reverse kernels
+ * read those states and run in FP64 (the gradient of the FP32 trajectory's map, evaluated in
+ * double).  Device memory for nsteps/checkpoint + checkpoint states and the FP64 adjoint
+ * arrays is allocated for the call and freed before it returns. */
 enum { LBCG_OBJ_WEIGHTED = 0, LBCG_OBJ_FINGER_LENGTH = 1, LBCG_OBJ_RED_MASS = 2 };
 typedef struct {
   int64_t nsteps, checkpoint;

@@ -7,7 +7,8 @@ x_tip - x_cl of Sec. III.D, the red mass, or a weighted sum of rho^N).  Its back
 dJ/d(theta per node), dJ/d sigma, dJ/d nu_R and dJ/d nu_B from the same call: the reverse
 sweep runs in the forward of this Function and its results are kept for backward.  Any
 further dependence (the viscosity ratio M = nu_R / nu_B, a global angle broadcast to the
-wall nodes) follows by torch's chain rule.  FP64, one lattice per call.
+wall nodes) follows by torch's chain rule.  One lattice per call; the forward runs in the
+spec's precision (FP64, or FP32 with an FP64 reverse sweep).
 """
 from __future__ import annotations
 
@@ -29,6 +30,7 @@ class ObjectiveSpec:
     checkpoint: int
     objective: str = "finger_length"       # "finger_length", "red_mass" or "weighted"
     weight: Optional[np.ndarray] = None    # [ny, nx], for "weighted"
+    precision: str = "fp64"                # "fp64" or "fp32" (forward steps and checkpoints)
 
 
 class WettingObjective(torch.autograd.Function):
@@ -38,7 +40,7 @@ class WettingObjective(torch.autograd.Function):
         g = dataclasses.replace(spec.geom, theta_node=np.ascontiguousarray(th))
         p = dataclasses.replace(spec.params, sigma=float(sigma), nu_R=float(nu_R), nu_B=float(nu_B),
                                 theta=float(th.mean()))
-        L = Lattice(g, p, "fp64")
+        L = Lattice(g, p, spec.precision)
         try:
             if spec.objective == "weighted":
                 out = L.adjoint(spec.nsteps, spec.checkpoint, weight=spec.weight)

@@ -54,7 +54,17 @@ __global__ void __launch_bounds__(kAdjThreads) fwd_local(AdjDev A) {
     return;
   }
   double fr[9], fb[9], rR, rB;
-  load_node<double>(A.L, A.src, x, y, fr, fb);
+  if (A.src_fp32) {
+    // FP32 forward: its post-Zou-He populations, widened; everything after is FP64
+    float fr32[9], fb32[9];
+    load_node<float>(A.L, static_cast<const float*>(A.src), x, y, fr32, fb32);
+    for (int a = 0; a < 9; ++a) {
+      fr[a] = fr32[a];
+      fb[a] = fb32[a];
+    }
+  } else {
+    load_node<double>(A.L, static_cast<const double*>(A.src), x, y, fr, fb);
+  }
   for (int a = 0; a < 9; ++a) {
     A.fr[a * N + i] = fr[a];
     A.fb[a * N + i] = fb[a];
@@ -397,7 +407,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_normal(AdjDev A) {
   {
     const double gx = A.gcx[i], gy = A.gcy[i];
     const double m = sqrt(gx * gx + gy * gy);
-    if (m > A.L.grad_eps) {
+    if (m > A.n_eps) {   // below it n is frozen in the reverse sweep (see AdjDev::n_eps)
       const double im = 1.0 / m, nx = gx * im, ny = gy * im;
       const double dot = nx * lnx + ny * lny;
       lgx += (lnx - nx * dot) * im;

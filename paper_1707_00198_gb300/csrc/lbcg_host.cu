@@ -10,6 +10,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/lbcg.h"
 #include "lbcg_internal.h"
 
@@ -18,6 +20,12 @@ using namespace lbcg;
 namespace {
 
 thread_local std::string g_err;
+
+// NVTX range over one public call (shown by Nsight tools; inert without a profiler)
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
 
 lbcg_status fail(lbcg_status s, const char* fmt, ...) {
   char buf[512];
@@ -404,6 +412,7 @@ const char* lbcg_last_error(void) { return g_err.c_str(); }
 
 lbcg_status lbcg_create_batch(int32_t n, const lbcg_geometry* geoms, const lbcg_params* prms, int32_t precision,
                               void* stream, lbcg_handle** out) {
+  Range range_("lbcg_create_batch");
   g_err.clear();
   if (!out) return fail(LBCG_E_ARG, "NULL output handle pointer");
   *out = nullptr;
@@ -569,6 +578,7 @@ lbcg_status lbcg_create(const lbcg_geometry* geom, const lbcg_params* prm, int32
 }
 
 lbcg_status lbcg_step(lbcg_handle* h, int64_t nsteps) {
+  Range range_("lbcg_step");
   lbcg_status s = check_handle(h);
   if (s != LBCG_OK) return s;
   if (nsteps < 0) return fail(LBCG_E_ARG, "nsteps < 0");
@@ -618,6 +628,7 @@ lbcg_status lbcg_step(lbcg_handle* h, int64_t nsteps) {
 }
 
 lbcg_status lbcg_observables(lbcg_handle* h, int32_t lattice, const lbcg_obs_spec* spec, lbcg_obs* out) {
+  Range range_("lbcg_observables");
   lbcg_status s = check_handle(h);
   if (s != LBCG_OK) return s;
   if (!spec || !out) return fail(LBCG_E_ARG, "NULL spec or output");
@@ -810,10 +821,12 @@ bool crossing_derivative(const std::vector<double>& prof, int& i0, double& x, do
 extern "C" {
 
 lbcg_status lbcg_adjoint(lbcg_handle* h, const lbcg_adjoint_spec* spec, lbcg_grads* out) {
+  Range range_("lbcg_adjoint");
   lbcg_status s = check_handle(h);
   if (s != LBCG_OK) return s;
   if (!spec || !out) return fail(LBCG_E_ARG, "NULL spec or output");
-  if (h->prec != 0) return fail(LBCG_E_UNSUPPORTED, "the adjoint runs on FP64 handles");
+  if (h->prec != LBCG_FP64 && h->prec != LBCG_FP32)
+    return fail(LBCG_E_UNSUPPORTED, "the adjoint runs on FP64 or FP32 handles");
   if (h->lats.size() != 1) return fail(LBCG_E_UNSUPPORTED, "the adjoint runs on single-lattice handles");
   if (spec->nsteps < 1 || spec->checkpoint < 1) return fail(LBCG_E_ARG, "nsteps and checkpoint must be >= 1");
   if (spec->objective == LBCG_OBJ_WEIGHTED && !spec->weight) return fail(LBCG_E_ARG, "weighted objective needs weight");
@@ -861,6 +874,8 @@ lbcg_status lbcg_adjoint(lbcg_handle* h, const lbcg_adjoint_spec* spec, lbcg_gra
   }
   A.N = N;
   A.flags = h->d_flags;
+  A.src_fp32 = h->prec == LBCG_FP32 ? 1 : 0;
+  A.n_eps = h->prec == LBCG_FP32 ? std::max(1e-5, L.prm.grad_eps) : L.prm.grad_eps;
   A.nsx = nsx;
   A.nsy = nsy;
   A.cos_t = ct;
@@ -959,7 +974,7 @@ lbcg_status lbcg_adjoint(lbcg_handle* h, const lbcg_adjoint_spec* spec, lbcg_gra
     }
   }
   CK(h, cudaMemcpyAsync(c_dev, cw.data(), N * 8, cudaMemcpyHostToDevice, h->stream));
-  A.src = static_cast<const double*>(h->pool[h->cur]);
+  A.src = h->pool[h->cur];
   A.lam = lamA;
   CK(h, adjoint_seed(A, c_dev, spec->objective == LBCG_OBJ_RED_MASS, h->stream));
   // ---- reverse, one checkpoint segment at a time.  A segment's work (recompute its states
@@ -978,7 +993,7 @@ lbcg_status lbcg_adjoint(lbcg_handle* h, const lbcg_adjoint_spec* spec, lbcg_gra
     double* ln = lam_in_a ? lamB : lamA;
     for (int64_t j = ns - 1; j >= 0; --j) {
       AdjDev a = A;
-      a.src = reinterpret_cast<const double*>(reinterpret_cast<char*>(seg) + sb * j);
+      a.src = reinterpret_cast<char*>(seg) + sb * j;
       a.lam_next = lc;
       a.lam = ln;
       cudaError_t e = adjoint_step(a, h->stream);
@@ -1076,6 +1091,7 @@ lbcg_status lbcg_set_tile(lbcg_handle* h, int32_t ty) {
 }
 
 lbcg_status lbcg_autotune(lbcg_handle* h, int32_t probe_steps, int32_t* schedule) {
+  Range range_("lbcg_autotune");
   lbcg_status s = check_handle(h);
   if (s != LBCG_OK) return s;
   if (probe_steps < 1) return fail(LBCG_E_ARG, "probe_steps must be >= 1");

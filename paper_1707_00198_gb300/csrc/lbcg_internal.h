@@ -59,7 +59,13 @@ cudaError_t launch_observables(const LatDev* lats, int lat, int nx, int ny, cons
 struct AdjDev {
   LatDev L;
   int N;
-  const double* src;     // stored state (population pool of the lattice)
+  const void* src;       // stored state (population pool of the lattice), FP64 or FP32
+  int src_fp32;          // 1: the state is stored in FP32 (an FP32 forward; FP64 reverse)
+  // |grad rho^N| at or below which the reverse sweep takes n = g/|g| as constant.  FP64
+  // states: the forward's own guard.  FP32 states: 1e-5 -- their pure phases carry rounding
+  // noise |grad rho^N| ~ 1e-7 whose normals the forward only ever multiplies by ~0, but whose
+  // 1/|g| ~ 1e8 would give the linearised map a spurious growing mode.
+  double n_eps;
   const uint8_t* flags;  // node flags (pitch layout)
   const double* nsx;     // solid normal at outermost fluid nodes (compact, 0 elsewhere)
   const double* nsy;

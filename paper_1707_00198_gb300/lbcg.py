@@ -321,7 +321,7 @@ class Lattice:
         return lbcg_get_fields(self.h, lattice, g.nx, g.ny)
 
     def adjoint(self, nsteps: int, checkpoint: int, weight: Optional[np.ndarray] = None, **kw) -> dict:
-        """Gradients of J at step (current + nsteps); see lbcg_adjoint.  FP64, one lattice."""
+        """Gradients of J at step (current + nsteps); see lbcg_adjoint.  FP64 or FP32, one lattice."""
         g = self.geoms[0]
         return lbcg_adjoint(self.h, g.nx, g.ny, nsteps, checkpoint, weight, **kw)
 

@@ -147,8 +147,8 @@ def test_adjoint_rejects_unsupported_handles():
     lbcg = _lib()
     g = I.displacement_channel(W=6, L=16, x_I=6.0, seed=3)
     p = I.fingering_params(M=3.0, Ca=0.1, theta_deg=60.0)
-    L = lbcg.Lattice(g, p, "fp32")
-    with pytest.raises(lbcg.LBCGError, match="FP64"):
+    L = lbcg.Lattice(g, p, "fp16")
+    with pytest.raises(lbcg.LBCGError, match="FP64 or FP32"):
         L.adjoint(2, 1, weight=np.zeros((g.ny, g.nx)))
     L.close()
     L = lbcg.Lattice([g, g], [p, p], "fp64")
@@ -220,3 +220,36 @@ def test_autograd_function_viscosity_ratio_and_global_angle():
     assert _close(M.grad.item(), fd_M, 2e-5, 1e-9), (M.grad.item(), fd_M)
     assert _close(theta.grad.item(), fd_t, 2e-5, 1e-9), (theta.grad.item(), fd_t)
     assert sigma.grad is not None and np.isfinite(sigma.grad.item())
+
+
+def test_fp32_adjoint_against_fp32_finite_differences_and_the_fp64_adjoint():
+    """The adjoint of an FP32 forward run (FP32 steps and checkpoints, FP64 reverse sweep) on
+    the finger length of the 400 x 42 channel (M = 10, Ca = 0.05, theta = 60 deg, 4000 steps,
+    checkpoint every 200): within 1e-3 relative of central finite differences of the FP32
+    forward path with a step of 1e-3 (relative for sigma, nu_R, nu_B; radians for theta), and
+    within 2e-3 of the FP64 adjoint (a different map: the trajectories differ by rounding)."""
+    lbcg = _lib()
+    g, p = I.config_adjoint()
+    n, k = 4000, 200
+
+    def J(prm):
+        L = lbcg.Lattice(g, prm, "fp32")
+        L.step(n)
+        o = L.observables()
+        L.close()
+        return o["x_tip"] - o["x_cl"]
+
+    L = lbcg.Lattice(g, p, "fp32")
+    out = L.adjoint(n, k)
+    L.close()
+    L = lbcg.Lattice(g, p, "fp64")
+    ref = L.adjoint(n, k)
+    L.close()
+    assert _close(out["J"], J(p), 1e-9)
+    for key, field, d in (("dsigma", "sigma", 1e-3 * p.sigma), ("dnu_R", "nu_R", 1e-3 * p.nu_R),
+                          ("dnu_B", "nu_B", 1e-3 * p.nu_B), ("dtheta", "theta", 1e-3)):
+        fd = (J(I.Params(**{**p.__dict__, field: getattr(p, field) + d}))
+              - J(I.Params(**{**p.__dict__, field: getattr(p, field) - d}))) / (2 * d)
+        assert _close(out[key], fd, 1e-3), (key, out[key], fd)
+        assert _close(out[key], ref[key], 2e-3), (key, out[key], ref[key])
+    assert np.isfinite(out["dtheta_node"]).all()
