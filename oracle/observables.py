@@ -120,3 +120,34 @@ def observables(lat: O.OracleLattice, prm, fR, fB, wall_y: float = 0.5, cyl=None
     out["x_cl"] = sum(xs) / len(xs) if xs else -1.0
     out["nonfinite"] = int(not bool(torch.isfinite(mac["rho"][fl]).all()))
     return out
+
+
+def velocity_change(lat: O.OracleLattice, mac_then: dict, mac_now: dict) -> float:
+    """E_1 of Eq. 45: max over fluid nodes of max(|u_x^now - u_x^then|, |u_y^now - u_y^then|)
+    (the paper takes the two states 500 steps apart and stops when E_1 < 1e-7)."""
+    fl = lat.fluid
+    dx = (mac_now["ux"] - mac_then["ux"]).detach().abs()[fl]
+    dy = (mac_now["uy"] - mac_then["uy"]).detach().abs()[fl]
+    return float(torch.maximum(dx, dy).max())
+
+
+def npmt(lat: O.OracleLattice, mac: dict, cx: float, cy: float, r: float, inside_red: bool = True) -> dict:
+    """E_NPMT of Eq. 47 with the theoretical steady interface C = circle (cx, cy, r) in node
+    coordinates (node (x, y) is inside when (x - cx)^2 + (y - cy)^2 < r^2).  Masses are sums of
+    rho_R and rho_B (Eq. 16) over fluid nodes.  Read as each colour's mass on the wrong side of
+    C: with D the colour inside C and O the other, E = sqrt((m_O^in / m_O^all)^2 +
+    (m_D^out / m_D^all)^2)."""
+    fl = lat.fluid
+    ny, nx = fl.shape
+    y, x = torch.meshgrid(torch.arange(ny, dtype=O.DT), torch.arange(nx, dtype=O.DT), indexing="ij")
+    inside = ((x - cx) ** 2 + (y - cy) ** 2 < r * r) & fl
+    outside = fl & ~inside
+    rR, rB = mac["rhoR"].detach(), mac["rhoB"].detach()
+    m = dict(m_R_in=float(rR[inside].sum()), m_R_out=float(rR[outside].sum()),
+             m_B_in=float(rB[inside].sum()), m_B_out=float(rB[outside].sum()))
+    if inside_red:
+        wrong_O, all_O, wrong_D, all_D = m["m_B_in"], m["m_B_in"] + m["m_B_out"], m["m_R_out"], m["m_R_in"] + m["m_R_out"]
+    else:
+        wrong_O, all_O, wrong_D, all_D = m["m_R_in"], m["m_R_in"] + m["m_R_out"], m["m_B_out"], m["m_B_in"] + m["m_B_out"]
+    m["e_npmt"] = math.sqrt((wrong_O / all_O) ** 2 + (wrong_D / all_D) ** 2)
+    return m
