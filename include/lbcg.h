@@ -206,6 +206,27 @@ lbcg_status lbcg_adjoint(lbcg_handle* h, const lbcg_adjoint_spec* spec, lbcg_gra
 lbcg_status lbcg_autotune(lbcg_handle* h, int32_t probe_steps, int32_t* schedule);
 lbcg_status lbcg_schedule(const lbcg_handle* h, int32_t* schedule);
 
+/* Steady-state diagnostics of Sec. III, in FP64 over one lattice's fluid nodes.
+ *   e1: Eq. 45, max(|u_x - u_x'|, |u_y - u_y'|) between the current velocity and the one stored
+ *     by this lattice's previous lbcg_diagnostics call (taken at step prev_step; NaN and
+ *     prev_step = -1 on the first call).  Every call stores the current velocity.  The paper
+ *     calls it every 500 steps and stops when e1 < 1e-7.
+ *   e_npmt: Eq. 47, read as each colour's mass on the wrong side of the theoretical steady
+ *     interface C, the circle (cx, cy, r) in node coordinates (node (x, y) is inside when
+ *     (x-cx)^2 + (y-cy)^2 < r^2): sqrt((m_O^in / m_O^all)^2 + (m_D^out / m_D^all)^2), D the colour
+ *     inside C (inside_red != 0: red) and O the other; the four masses are returned too.
+ * The first call allocates the velocity store (2 doubles per node of the handle); the call
+ * synchronises the handle's stream. */
+typedef struct {
+  double cx, cy, r;
+  int32_t inside_red;
+} lbcg_diag_spec;
+typedef struct {
+  int64_t step, prev_step;
+  double e1, e_npmt, m_R_in, m_R_out, m_B_in, m_B_out;
+} lbcg_diag;
+lbcg_status lbcg_diagnostics(lbcg_handle* h, int32_t lattice, const lbcg_diag_spec* spec, lbcg_diag* out);
+
 /* Kernel timing with CUDA events on the handle's stream.  While enabled, lbcg_step launches
  * the kernels of each step directly (no graph) with an event recorded before and after each
  * of k_band, k_wall and k_step.  lbcg_kernel_times synchronises, returns in ms3[0..2] the

@@ -69,6 +69,8 @@ struct lbcg_handle {
   uint8_t* d_flags = nullptr;
   uint8_t* d_nbmask = nullptr;
   int* d_err = nullptr;    // device error word (a sweep block's bounded wait ran out)
+  double* d_usnap = nullptr;          // velocity stored by lbcg_diagnostics ([2][node_total])
+  std::vector<int64_t> snap_step;     // per lattice: step of that velocity, -1 = none
   void* d_band_rn = nullptr;
   void* d_wall = nullptr;
   double* d_macro = nullptr;
@@ -342,7 +344,7 @@ void free_handle(lbcg_handle* h) {
   for (cudaEvent_t e : h->events) cudaEventDestroy(e);
   void* ptrs[] = {h->pool[0], h->pool[1], h->d_flags, h->d_band_rn, h->d_wall,   h->d_macro,
                   h->d_lats,  h->d_tiles, h->d_band,  h->d_ofb,     h->d_obs,    h->d_strips,
-                  h->d_nbmask, h->d_err};
+                  h->d_nbmask, h->d_err, h->d_usnap};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -700,6 +702,45 @@ lbcg_status lbcg_observables(lbcg_handle* h, int32_t lattice, const lbcg_obs_spe
     }
   }
   if (out->nonfinite) return fail(LBCG_E_DIVERGED, "non-finite density in lattice %d at step %lld", lattice, (long long)h->step);
+  return LBCG_OK;
+}
+
+lbcg_status lbcg_diagnostics(lbcg_handle* h, int32_t lattice, const lbcg_diag_spec* spec, lbcg_diag* out) {
+  Range range_("lbcg_diagnostics");
+  lbcg_status s = check_handle(h);
+  if (s != LBCG_OK) return s;
+  if (!spec || !out) return fail(LBCG_E_ARG, "NULL spec or output");
+  if (lattice < 0 || lattice >= int(h->lats.size())) return fail(LBCG_E_ARG, "bad lattice index %d", lattice);
+  if (!(spec->r > 0)) return fail(LBCG_E_ARG, "the circle needs a radius > 0");
+  if (!h->d_usnap) {
+    if (cudaMalloc(&h->d_usnap, 2 * (size_t)h->node_total * sizeof(double)) != cudaSuccess)
+      return fail(LBCG_E_NOMEM, "cannot allocate the velocity snapshot");
+    h->snap_step.assign(h->lats.size(), -1);
+  }
+  s = run_macro(h, lattice);
+  if (s != LBCG_OK) return s;
+  const bool have = h->snap_step[lattice] >= 0;
+  double* parts = h->d_obs;
+  double* res = h->d_obs + obs_partials_doubles();   // the reduction scratch of lbcg_observables
+  CK(h, launch_diagnostics(h->d_lats, lattice, h->d_macro, h->node_total, h->d_flags, h->d_usnap, have, spec->cx,
+                           spec->cy, spec->r, parts, res, h->stream));
+  double q[6];
+  CK(h, cudaMemcpyAsync(q, res, sizeof(q), cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  s = check_device_error(h);
+  if (s != LBCG_OK) return s;
+  out->step = h->step;
+  out->prev_step = h->snap_step[lattice];
+  h->snap_step[lattice] = h->step;
+  out->e1 = have ? std::max(q[0], q[1]) : NAN;
+  out->m_R_in = q[2];
+  out->m_R_out = q[3];
+  out->m_B_in = q[4];
+  out->m_B_out = q[5];
+  const double mR = q[2] + q[3], mB = q[4] + q[5];
+  const double wrongO = spec->inside_red ? q[4] / mB : q[2] / mR;   // the outer colour inside C
+  const double wrongD = spec->inside_red ? q[3] / mR : q[5] / mB;   // the inner colour outside C
+  out->e_npmt = std::sqrt(wrongO * wrongO + wrongD * wrongD);
   return LBCG_OK;
 }
 

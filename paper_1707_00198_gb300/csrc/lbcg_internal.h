@@ -50,6 +50,12 @@ constexpr int kObsRows = 3;   // row-crossing results
 constexpr int kObsOut = kObsQ + kObsRows;
 constexpr int kObsBlocks = 304;  // 2 x 152 SMs
 size_t obs_partials_doubles();
+// Steady-state diagnostics (lbcg_obs.cu): 6 doubles into `out` -- max |du_x|, max |du_y|
+// against usnap ([2][node_total], overwritten with the current velocity), rho_R inside / outside
+// the circle, rho_B inside / outside.  `partials` holds kObsBlocks * 6 doubles.
+cudaError_t launch_diagnostics(const LatDev* lats, int lat, const double* macro, long long node_total,
+                               const uint8_t* flags, double* usnap, bool have_snap, double cx, double cy, double r,
+                               double* partials, double* out, cudaStream_t st);
 cudaError_t launch_observables(const LatDev* lats, int lat, int nx, int ny, const double* macro,
                                long long node_total, const uint8_t* flags, int tip0, int tip1, int cl0, int cl1,
                                double* partials, double* out, cudaStream_t st);

@@ -61,6 +61,15 @@ class lbcg_grads(C.Structure):
                 ("dJ_dtheta", C.c_double), ("dJ_dtheta_node", C.POINTER(C.c_double))]
 
 
+class lbcg_diag_spec(C.Structure):
+    _fields_ = [("cx", C.c_double), ("cy", C.c_double), ("r", C.c_double), ("inside_red", C.c_int32)]
+
+
+class lbcg_diag(C.Structure):
+    _fields_ = [("step", C.c_int64), ("prev_step", C.c_int64)] + [
+        (n, C.c_double) for n in ("e1", "e_npmt", "m_R_in", "m_R_out", "m_B_in", "m_B_out")]
+
+
 LBCG_OBJ_WEIGHTED, LBCG_OBJ_FINGER_LENGTH, LBCG_OBJ_RED_MASS = 0, 1, 2
 OBJECTIVES = {"weighted": LBCG_OBJ_WEIGHTED, "finger_length": LBCG_OBJ_FINGER_LENGTH, "red_mass": LBCG_OBJ_RED_MASS}
 
@@ -109,6 +118,7 @@ def library():
                                                  C.c_void_p]),
         "lbcg_adjoint": (C.c_int, [H, C.POINTER(lbcg_adjoint_spec), C.POINTER(lbcg_grads)]),
         "lbcg_autotune": (C.c_int, [H, C.c_int32, C.POINTER(C.c_int32)]),
+        "lbcg_diagnostics": (C.c_int, [H, C.c_int32, C.POINTER(lbcg_diag_spec), C.POINTER(lbcg_diag)]),
         "lbcg_schedule": (C.c_int, [H, C.POINTER(C.c_int32)]),
     }
     for name, (res, args) in sigs.items():
@@ -123,7 +133,7 @@ def exported_symbols() -> list:
     return ["lbcg_create", "lbcg_create_batch", "lbcg_step", "lbcg_observables", "lbcg_get_populations",
             "lbcg_set_populations", "lbcg_get_fields", "lbcg_state_bytes", "lbcg_upload_state",
             "lbcg_download_state", "lbcg_set_sweep", "lbcg_set_tile", "lbcg_profile", "lbcg_kernel_times", "lbcg_launches_per_step", "lbcg_total_nodes", "lbcg_destroy",
-            "lbcg_last_error", "lbcg_field_moments_noalloc", "lbcg_adjoint", "lbcg_autotune", "lbcg_schedule"]
+            "lbcg_last_error", "lbcg_field_moments_noalloc", "lbcg_adjoint", "lbcg_autotune", "lbcg_schedule", "lbcg_diagnostics"]
 
 
 def _check(status: int):
@@ -230,6 +240,15 @@ def lbcg_schedule(h: int) -> int:
     return out.value
 
 
+def lbcg_diagnostics(h: int, lattice: int, circle, inside_red: bool = True) -> dict:
+    """E_1 against the previous call's velocity and E_NPMT for the circle (cx, cy, r)."""
+    cx, cy, r = circle
+    out = lbcg_diag()
+    _check(library().lbcg_diagnostics(h, lattice, C.byref(lbcg_diag_spec(cx, cy, r, 1 if inside_red else 0)),
+                                      C.byref(out)))
+    return {k: getattr(out, k) for k, _ in lbcg_diag._fields_}
+
+
 def lbcg_profile(h: int, enable: bool):
     _check(library().lbcg_profile(h, 1 if enable else 0))
 
@@ -330,6 +349,9 @@ class Lattice:
 
     def set_sweep(self, rows: int = 0):
         lbcg_set_sweep(self.h, rows)
+
+    def diagnostics(self, circle, inside_red: bool = True, lattice: int = 0) -> dict:
+        return lbcg_diagnostics(self.h, lattice, circle, inside_red)
 
     def autotune(self, probe_steps: int = 10) -> int:
         return lbcg_autotune(self.h, probe_steps)
