@@ -90,6 +90,9 @@ typedef struct {
   double u_in;                 /* inlet velocity (LBCG_BCX_INOUT)                         */
   double rho_out;              /* outlet density (LBCG_BCX_INOUT)                         */
   double grad_eps;             /* n = 0 where |grad rho^N| <= grad_eps                    */
+  int32_t inlet_profile;       /* LBCG_BCX_INOUT inlet: 0 uniform u_in; 1 Poiseuille profile of
+                                  maximum u_in across the inlet column's fluid rows, the walls
+                                  half a node beyond its first and last fluid rows (Sec. III.D) */
 } lbcg_params;
 
 /* What lbcg_observables measures (all rows are 0-based y indices). */

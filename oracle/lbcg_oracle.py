@@ -424,6 +424,13 @@ def inlet_outlet(lat, prm, fR, fB):
     # inlet, x = 0: known 0, 2, 3, 4, 6, 7
     f = fR[:, :, 0] + fB[:, :, 0]
     u = prm.u_in
+    if getattr(prm, "inlet_profile", 0):
+        # Poiseuille profile of maximum u_in across the inlet column's fluid rows, the walls
+        # half a node beyond the first and last of them (Sec. III.D)
+        rows = torch.nonzero(fl_in, as_tuple=True)[0]
+        y0, w = float(rows.min()) - 0.5, float(rows.max() - rows.min() + 1)
+        s = (torch.arange(lat.ny, dtype=DT) - y0) / w
+        u = 4 * prm.u_in * s * (1 - s)
     rho = (f[0] + f[2] + f[4] + 2 * (f[3] + f[6] + f[7])) / (1 - u)
     f1 = f[3] + 2.0 / 3.0 * rho * u
     f5 = f[7] - 0.5 * (f[2] - f[4]) + rho * u / 6.0

@@ -465,7 +465,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_rho(AdjDev A) {
   double sr[9], sb[9];   // adjoint of the stored values
   if (L.bcx == BC_INOUT && x == 0) {
     // inlet: fr = f (f1, f5, f8 from Zou-He of the known totals), fb = 0
-    const double u = L.u_in;
+    const double u = inlet_u<double>(L, y);
     const double ck[9] = {1, 0, 1, 2, 1, 0, 2, 2, 0};
     double lt[9];
     for (int a = 0; a < 9; ++a) lt[a] = 0.0;

@@ -49,13 +49,23 @@ constexpr int kSweepFMinBlocks16 = 6;
 
 // Per-lattice constants, resident in global memory, one entry per lattice of a handle.
 struct LatDev {
-  int nx, ny, pitch, bcx, bcy, pad_;
+  int nx, ny, pitch, bcx, bcy, in_prof;   // in_prof: 1 = Poiseuille inlet profile
   long long pop_off;   // element offset of this lattice's block in the population pool
   long long plane;     // elements of one node-array plane of this lattice (pitch * ny)
   long long node_off;  // element offset of node (0,0) in the node arrays
   double nu_R, nu_B, sigma, beta, s_e, s_eps, s_q, rho0, u_in, rho_out, grad_eps;
   double h_inv_nuR, h_inv_nuB;  // 1/(2 nu_R), 1/(2 nu_B): the two weights of Eq. 18
+  double in_y0, in_w;           // inlet profile: s = (y - in_y0) / in_w across the channel
 };
+
+// Inlet velocity of row y (Sec. III.D): uniform u_in, or the Poiseuille profile
+// 4 u_in s (1 - s) whose maximum is u_in.
+template <typename T>
+__device__ __forceinline__ T inlet_u(const LatDev& L, int y) {
+  if (!L.in_prof) return T(L.u_in);
+  const double s = (y - L.in_y0) / L.in_w;
+  return T(4.0 * L.u_in * s * (1.0 - s));
+}
 
 // Entry of the outermost-fluid list: node, its solid normal and contact angle.
 struct OfbEntry {
@@ -315,7 +325,7 @@ __device__ __forceinline__ void load_node(const LatDev& L, const S* __restrict__
                                           typename Store<S>::T fr[9], typename Store<S>::T fb[9]) {
   using T = typename Store<S>::T;
   load_raw<S>(src + L.pop_off + pop_node(x, y, L.pitch), T(L.rho0), fr, fb);
-  if (L.bcx == BC_INOUT) zou_he<T>(x, L.nx, T(L.u_in), T(L.rho_out), fr, fb);
+  if (L.bcx == BC_INOUT) zou_he<T>(x, L.nx, inlet_u<T>(L, y), T(L.rho_out), fr, fb);
 }
 
 // rho^N of Eq. 12 from the colour densities of Eq. 16 (sequential sums in direction order)

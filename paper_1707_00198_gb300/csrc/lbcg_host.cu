@@ -147,6 +147,7 @@ lbcg_status validate(const lbcg_geometry* g, const lbcg_params* p, int idx) {
   if (!(std::fabs(p->u_in) < 1)) return fail(LBCG_E_UNSTABLE_PARAM, "lattice %d: |u_in| must be < 1", idx);
   if (!(p->rho_out > 0)) return fail(LBCG_E_UNSTABLE_PARAM, "lattice %d: rho_out must be > 0", idx);
   if (!(p->grad_eps >= 0)) return fail(LBCG_E_ARG, "lattice %d: grad_eps must be >= 0", idx);
+  if (p->inlet_profile != 0 && p->inlet_profile != 1) return fail(LBCG_E_ARG, "lattice %d: bad inlet_profile", idx);
   const double pi = 3.14159265358979323846;
   auto angle_ok = [&](double t) { return t > 0 && t < pi; };
   if (!g->theta_node && !angle_ok(p->theta)) return fail(LBCG_E_UNSTABLE_PARAM, "lattice %d: theta outside (0, pi)", idx);
@@ -477,6 +478,18 @@ lbcg_status lbcg_create_batch(int32_t n, const lbcg_geometry* geoms, const lbcg_
     d.s_q = p.s_q;
     d.rho0 = p.rho0;
     d.u_in = p.u_in;
+    d.in_prof = p.inlet_profile;
+    {
+      // fluid rows of the inlet column: the profile spans them, walls half a node beyond
+      int lo = -1, hi = -1;
+      for (int y = 0; y < geoms[l].ny; ++y)
+        if (!geoms[l].solid[(size_t)y * geoms[l].nx]) {
+          if (lo < 0) lo = y;
+          hi = y;
+        }
+      d.in_y0 = lo < 0 ? 0.0 : lo - 0.5;
+      d.in_w = lo < 0 ? 1.0 : double(hi - lo + 1);
+    }
     d.rho_out = p.rho_out;
     d.grad_eps = p.grad_eps;
     d.h_inv_nuR = 0.5 / p.nu_R;

@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(32 * TY, sizeof(typename Store<S>::T) == 4 ? 1
   auto load = [&](int c3x, int c3y, T fr_[9], T fb_[9]) {
     const int x = sxm[c3x];
     load_raw<S>(src + pop_node(x, sym[c3y], pitch), r0, fr_, fb_);
-    if (inout) zou_he<T>(x, nx, u_in, rho_out, fr_, fb_);
+    if (inout) zou_he<T>(x, nx, inlet_u<T>(sL, sym[c3y]), rho_out, fr_, fb_);
   };
   // rho^N (Eq. 12): exactly +-1 on single-colour nodes in both arithmetic paths
   auto indicator = [&](const T fr_[9], const T fb_[9], T& sr, T& sb) -> T {
@@ -574,7 +574,7 @@ __global__ void __launch_bounds__(NTH, sizeof(typename Store<S>::T) == 4 ? 1024 
       if (!(f & F_SOLID)) {
         T hr[9], hb[9], a1, a2;
         load_raw<S>(src + ym0 * rowseg + colk[1], r0, hr, hb);
-        if (inout) zou_he<T>(xm, nx, u_in, rho_out, hr, hb);
+        if (inout) zou_he<T>(xm, nx, inlet_u<T>(sL, ym0), rho_out, hr, hb);
         v = indicator(hr, hb, a1, a2);
       }
       srn[s0][t] = v;
@@ -651,7 +651,7 @@ __global__ void __launch_bounds__(NTH, sizeof(typename Store<S>::T) == 4 ? 1024 
     const uint8_t myf = sfl[s2][t];
     T fr[9], fb[9];
     pre.decode_to(r0, fr, fb);
-    if (inout) zou_he<T>(xm, nx, u_in, rho_out, fr, fb);
+    if (inout) zou_he<T>(xm, nx, inlet_u<T>(sL, ym2), rho_out, fr, fb);
     T rhoR, rhoB;
     const T rn = indicator(fr, fb, rhoR, rhoB);
     // grad n (Eq. 28) on (n_x, n_y) pairs, then the curvature (Eq. 13)
@@ -953,7 +953,7 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
         } else {
           load_raw<S>(src + ym0 * rowseg + colk[1], r0, fr, fb);
         }
-        if (edge) zou_he<T>(xm, nx, u_in, rho_out, fr, fb);
+        if (edge) zou_he<T>(xm, nx, inlet_u<T>(sL, ym0), rho_out, fr, fb);
         V srb_ = P::add(P::mk(fr[0], fb[0]), P::mk(fr[1], fb[1]));
 #pragma unroll
         for (int a = 2; a < 9; ++a) srb_ = P::add(srb_, P::mk(fr[a], fb[a]));

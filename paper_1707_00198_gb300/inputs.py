@@ -56,6 +56,7 @@ class Params:
     u_in: float = 0.0            # uniform inlet velocity (bc_x == "inout")
     rho_out: float = 1.0         # outlet density (bc_x == "inout")
     grad_eps: float = 1e-12      # |grad rho^N| at or below which n = 0
+    inlet_profile: int = 0       # 0: uniform u_in; 1: Poiseuille profile of maximum u_in
 
 
 @dataclasses.dataclass
@@ -275,6 +276,16 @@ def config_capillary() -> tuple:
 def config_fingering(M: float = 1.0, Ca: float = 0.05, theta_deg: float = 90.0, seed: int = 0):
     """Displacement channel: width 100, length 2000, interface at x=100."""
     return displacement_channel(W=100, L=2000, x_I=100.0, seed=seed), fingering_params(M, Ca, theta_deg)
+
+
+def config_wettability(theta_deg: float, seed: int = 0):
+    """Sec. III.D.2 (wettability): 630x60 domain (58 fluid rows between two wall rows), flat
+    initial interface at x = 30, Poiseuille inlet of maximum u0 = 0.1, pressure outlet,
+    nu_R = nu_B = 0.3 (M = 1), sigma = 0.06 (Ca = nu_R u0 / sigma = 0.5)."""
+    g = displacement_channel(W=58, L=630, x_I=30.0, amp=0.0, seed=seed)
+    p = Params(nu_R=0.3, nu_B=0.3, sigma=0.06, theta=math.radians(theta_deg), u_in=0.1, rho_out=1.0,
+               inlet_profile=1)
+    return g, p
 
 
 def config_adjoint(seed: int = 0):

@@ -54,6 +54,10 @@ CASES = [
     # inlet/outlet channel with closed walls (Zou-He columns inside the adjoint)
     ("channel", lambda: (I.displacement_channel(W=6, L=16, x_I=6.0, seed=3, noise=1e-2),
                          I.fingering_params(M=3.0, Ca=0.1, theta_deg=60.0)), 10, 4),
+    # Poiseuille inlet profile (Sec. III.D): the Zou-He transpose with a row-dependent velocity
+    ("poiseuille", lambda: (I.displacement_channel(W=7, L=16, x_I=6.0, seed=5, noise=1e-2),
+                            I.Params(**{**I.fingering_params(M=2.0, Ca=0.1, theta_deg=70.0).__dict__,
+                                        "u_in": 0.04, "inlet_profile": 1})), 10, 4),
     # periodic x, closed y, a sessile droplet: both contact lines on the bottom wall
     ("droplet", lambda: (I.flat_wall_droplet(24, 14, R=6.0, noise=1e-2, seed=2),
                          I.Params(sigma=0.02, nu_R=0.2, nu_B=0.05, theta=math.radians(120.0))), 12, 5),

@@ -314,3 +314,26 @@ def test_scalar_brute_force_agrees(case):
         fR, fB = O.step(lat, p, fR, fB)
         assert np.allclose(fR.numpy(), sR, atol=1e-14, rtol=0)
         assert np.allclose(fB.numpy(), sB, atol=1e-14, rtol=0)
+
+
+def test_poiseuille_inlet_imposes_the_profile():
+    """The Zou-He velocity inlet with the Poiseuille profile (Sec. III.D): on the inlet column
+    sum_a e_ax f_a / rho equals 4 u0 s (1 - s), s = (y - y0) / W across the W fluid rows, for any
+    incoming populations; its mean over the rows is u0 (2/3 + 1/(3 W^2))."""
+    g = I.displacement_channel(W=9, L=12, x_I=5.0, seed=0, noise=1e-2)
+    p = I.Params(u_in=0.05, inlet_profile=1)
+    lat = O.make_lattice(g, p.theta)
+    rng = np.random.default_rng(1)
+    fR = torch.tensor(rng.uniform(0.0, 0.2, (9, g.ny, g.nx)))
+    fB = torch.tensor(rng.uniform(0.0, 0.2, (9, g.ny, g.nx)))
+    fR, fB = O.inlet_outlet(lat, p, fR, fB)
+    f = (fR + fB)[:, :, 0]
+    ex = torch.tensor([e[0] for e in O.E], dtype=torch.float64)
+    u = (ex[:, None] * f).sum(0) / f.sum(0)
+    W = 9
+    rows = np.arange(1, W + 1)
+    s = (rows - 0.5) / W
+    want = 4 * p.u_in * s * (1 - s)
+    assert np.abs(u.numpy()[rows] - want).max() <= 1e-15
+    assert abs(want.mean() - p.u_in * (2 / 3 + 1 / (3 * W * W))) <= 1e-16
+    assert float(fB[:, rows, 0].abs().max()) == 0.0   # the inlet carries red only
