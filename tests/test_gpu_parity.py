@@ -360,3 +360,35 @@ def test_wettability_slopes_of_the_paper():
     assert abs(sL + 1.212e-4) <= 0.1 * 1.212e-4, sL
     tip = np.array(dS) + np.array(dL)
     assert np.abs(tip - 0.1).max() <= 0.003, tip
+
+
+def test_high_viscosity_ratio_plateau_of_the_paper():
+    """Sec. III.D.3 (Poiseuille inlet u0 = 0.01, nu_R = 0.5, theta = 90 deg, Ca = 0.48): for
+    M >= 20 the finger stops growing and the contact line moves at the mean inlet velocity
+    2/3 u0 = 0.00667 (the paper's plateau, whose '1/3' is read as 2/3: mass balance of a finger of
+    constant length); below it dS/dt grows with M.  Measured over steps 20000-40000."""
+    from paper_1707_00198_gb300 import lbcg
+    Ms = [5.0, 20.0, 100.0]
+    gs, ps = [], []
+    for M in Ms:
+        gs.append(I.displacement_channel(W=58, L=630, x_I=30.0, amp=0.0, seed=0))
+        ps.append(I.Params(nu_R=0.5, nu_B=0.5 / M, sigma=0.5 * 0.01 / 0.48, theta=math.radians(90.0), u_in=0.01,
+                           rho_out=1.0, inlet_profile=1))
+    L = lbcg.Lattice(gs, ps, "fp32")
+    L.step(20000)
+    rec = {M: [] for M in Ms}
+    for _ in range(11):
+        for i, M in enumerate(Ms):
+            o = lbcg.lbcg_observables(L.h, i, lbcg.obs_spec(ny=gs[i].ny))
+            rec[M].append((o["step"], o["x_tip"], o["x_cl"]))
+        L.step(2000)
+    L.close()
+    dS = {}
+    for M in Ms:
+        a = np.array(rec[M])
+        dS[M] = np.polyfit(a[:, 0], a[:, 2], 1)[0]
+        dL = np.polyfit(a[:, 0], a[:, 1] - a[:, 2], 1)[0]
+        if M >= 20:
+            assert abs(dS[M] - 2 / 3 * 0.01) <= 0.01 * 2 / 3 * 0.01, (M, dS[M])
+            assert abs(dL) <= 1e-5, (M, dL)
+    assert dS[5.0] < dS[20.0] - 1e-3
