@@ -251,6 +251,27 @@ def iso_gradient(lat: OracleLattice, phi: torch.Tensor):
     return gx / CS2, gy / CS2
 
 
+def one_sided_gradient(lat: OracleLattice, phi: torch.Tensor):
+    """Eq. 48 (scheme (b)): d_i phi(x) = sum_a w_a [phi(x + e_a) - phi(x)] e_ai / sum_a w_a e_ai^2
+    over the directions a whose neighbour is fluid.  The paper prints the denominator as
+    sum_a w_a; normalising each component by sum_a w_a e_ai^2 makes the estimate exact on
+    linear fields, as Eq. 28 is (as printed, a full stencil would return 0.6 of the gradient)."""
+    gx = torch.zeros_like(phi)
+    gy = torch.zeros_like(phi)
+    wx = torch.zeros_like(phi)
+    wy = torch.zeros_like(phi)
+    for a in range(1, 9):
+        ex, ey = E[a]
+        fl = lat.fluid_nb[a].to(DT)
+        d = neighbour(phi, ex, ey, lat.px, lat.py) - phi
+        gx = gx + W[a] * d * ex * fl
+        gy = gy + W[a] * d * ey * fl
+        wx = wx + W[a] * ex * ex * fl
+        wy = wy + W[a] * ey * ey * fl
+    return (torch.where(wx > 0, gx / torch.where(wx > 0, wx, torch.ones_like(wx)), torch.zeros_like(gx)),
+            torch.where(wy > 0, gy / torch.where(wy > 0, wy, torch.ones_like(wy)), torch.zeros_like(gy)))
+
+
 def wetting_correction(lat: OracleLattice, gx: torch.Tensor, gy: torch.Tensor, eps: float):
     """Eq. 30-36 on Omega_Fb nodes: keep |grad rho^N|, replace its direction by the rotated
     solid normal (n_f)_1 or (n_f)_2 nearer to the estimated direction."""
@@ -296,13 +317,27 @@ def interface_fields(lat: OracleLattice, prm, fR, fB):
     rho_safe = torch.where(fl, rho, torch.ones_like(rho))
     rhoN = torch.where(fl, (rhoR - rhoB) / rho_safe, torch.zeros_like(rho))       # Eq. 12
     eps = prm.grad_eps
-    gx, gy = iso_gradient(lat, virtual_fill(lat, rhoN))                              # Eq. 28-29
-    gx, gy = wetting_correction(lat, gx, gy, eps)                                    # Eq. 30-36
+    wetting = getattr(prm, "wetting", 0)
+    if wetting == 2:
+        # surface-energy formulation (Sec. III.A.1): rho^N = cos(theta) on the outermost solid
+        # nodes, no geometric correction
+        filled = torch.where(lat.outer_solid, torch.full_like(rhoN, math.cos(float(prm.theta))), rhoN)
+        gx, gy = iso_gradient(lat, filled)
+    else:
+        gx, gy = iso_gradient(lat, virtual_fill(lat, rhoN))                          # Eq. 28-29
+        gx, gy = wetting_correction(lat, gx, gy, eps)                                # Eq. 30-36
     gx = torch.where(fl, gx, torch.zeros_like(gx))
     gy = torch.where(fl, gy, torch.zeros_like(gy))
     nx_, ny_ = unit_normal(gx, gy, eps)
     dnx_dx, dnx_dy = iso_gradient(lat, virtual_fill(lat, nx_))                      # Eq. 29, 28 (second BC)
     dny_dx, dny_dy = iso_gradient(lat, virtual_fill(lat, ny_))
+    if wetting == 1:
+        # scheme (b) (Sec. III.A.2): grad n on the outermost fluid nodes by Eq. 48
+        bx_x, bx_y = one_sided_gradient(lat, nx_)
+        by_x, by_y = one_sided_gradient(lat, ny_)
+        fb = lat.omega_fb
+        dnx_dx, dnx_dy = torch.where(fb, bx_x, dnx_dx), torch.where(fb, bx_y, dnx_dy)
+        dny_dx, dny_dy = torch.where(fb, by_x, dny_dx), torch.where(fb, by_y, dny_dy)
     kappa = -nx_ * nx_ * dny_dy - ny_ * ny_ * dnx_dx + nx_ * ny_ * (dnx_dy + dny_dx)  # Eq. 13
     kappa = torch.where(fl, kappa, torch.zeros_like(kappa))
     Fx = 0.5 * prm.sigma * kappa * gx                                                # Eq. 10

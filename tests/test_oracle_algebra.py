@@ -213,3 +213,38 @@ def test_curvature_sign_and_size_on_a_circle():
     assert abs(k.mean().item() * R - 1) < 0.02, k.mean().item() * R
     # n . (x - c) < 0 (inward, into the red disc)
     assert bool(((nx_ * (x - 32.3) + ny_ * (y - 31.6))[band] < 0).all())
+
+
+def test_one_sided_gradient_of_scheme_b_is_exact_on_linear_fields():
+    """Eq. 48 as read (each component normalised by sum w e_i^2 over the fluid directions):
+    exact for phi = a x + b y next to a wall, where only fluid directions count, and in the bulk."""
+    import math
+    from paper_1707_00198_gb300 import inputs as I
+    g = I.flat_wall_droplet(14, 9, R=3.0, noise=0.0)
+    lat = O.make_lattice(g, math.radians(60))
+    y, x = torch.meshgrid(torch.arange(g.ny, dtype=O.DT), torch.arange(g.nx, dtype=O.DT), indexing="ij")
+    phi = 0.37 * x - 1.3 * y
+    gx, gy = O.one_sided_gradient(lat, phi)
+    # interior columns (periodic x wraps, so skip the two edge columns)
+    sel = lat.fluid.clone()
+    sel[:, 0] = False
+    sel[:, -1] = False
+    assert float((gx[sel] - 0.37).abs().max()) < 1e-13
+    assert float((gy[sel] + 1.3).abs().max()) < 1e-13
+
+
+def test_surface_energy_wall_gradient_closed_form():
+    """Surface-energy variant: rho^N = c on the fluid above a flat bottom wall, cos(theta) on the
+    solid row; on the first fluid row Eq. 28 gives d_y rho^N = (c - cos theta)/2, d_x = 0."""
+    import math
+    from paper_1707_00198_gb300 import inputs as I
+    g = I.flat_wall_droplet(16, 10, R=3.0, noise=0.0)
+    g.rhoN0[:] = 0.3
+    theta = math.radians(50)
+    p = I.Params(theta=theta, wetting=2)
+    lat = O.make_lattice(g, theta)
+    fR, fB = O.init_state(lat, g.rhoN0, p.rho0, p)
+    d = O.interface_fields(lat, p, fR, fB)
+    row = d["gy"][1]
+    assert float((row - (0.3 - math.cos(theta)) / 2).abs().max()) < 1e-14
+    assert float(d["gx"][1].abs().max()) < 1e-14
