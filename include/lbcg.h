@@ -93,6 +93,11 @@ typedef struct {
   int32_t inlet_profile;       /* LBCG_BCX_INOUT inlet: 0 uniform u_in; 1 Poiseuille profile of
                                   maximum u_in across the inlet column's fluid rows, the walls
                                   half a node beyond its first and last fluid rows (Sec. III.D) */
+  int32_t wetting;             /* 0: the paper's improved scheme (a) (Eq. 28-36, grad n with
+                                  Eq. 29 virtual n); 1: scheme (b) of Sec. III.A.2, grad n on
+                                  the outermost fluid nodes by Eq. 48; 2: the surface-energy
+                                  formulation, rho^N = cos(theta) on the outermost solid nodes
+                                  and no Eq. 30-36 correction (one global theta)              */
 } lbcg_params;
 
 /* What lbcg_observables measures (all rows are 0-based y indices). */

@@ -56,6 +56,8 @@ struct LatDev {
   double nu_R, nu_B, sigma, beta, s_e, s_eps, s_q, rho0, u_in, rho_out, grad_eps;
   double h_inv_nuR, h_inv_nuB;  // 1/(2 nu_R), 1/(2 nu_B): the two weights of Eq. 18
   double in_y0, in_w;           // inlet profile: s = (y - in_y0) / in_w across the channel
+  int wetting, pad2_;           // 0: improved scheme (a); 1: scheme (b), Eq. 48; 2: surface energy
+  double cos_theta;             // cos(theta) of the surface-energy variant
 };
 
 // Inlet velocity of row y (Sec. III.D): uniform u_in, or the Poiseuille profile

@@ -68,6 +68,7 @@ struct lbcg_handle {
   int cur = 0;
   uint8_t* d_flags = nullptr;
   uint8_t* d_nbmask = nullptr;
+  int scheme_b = 0;        // some lattice uses wetting scheme (b)
   int* d_err = nullptr;    // device error word (a sweep block's bounded wait ran out)
   double* d_usnap = nullptr;          // velocity stored by lbcg_diagnostics ([2][node_total])
   std::vector<int64_t> snap_step;     // per lattice: step of that velocity, -1 = none
@@ -148,6 +149,9 @@ lbcg_status validate(const lbcg_geometry* g, const lbcg_params* p, int idx) {
   if (!(p->rho_out > 0)) return fail(LBCG_E_UNSTABLE_PARAM, "lattice %d: rho_out must be > 0", idx);
   if (!(p->grad_eps >= 0)) return fail(LBCG_E_ARG, "lattice %d: grad_eps must be >= 0", idx);
   if (p->inlet_profile != 0 && p->inlet_profile != 1) return fail(LBCG_E_ARG, "lattice %d: bad inlet_profile", idx);
+  if (p->wetting < 0 || p->wetting > 2) return fail(LBCG_E_ARG, "lattice %d: bad wetting scheme %d", idx, p->wetting);
+  if (p->wetting == 2 && g->theta_node)
+    return fail(LBCG_E_UNSUPPORTED, "lattice %d: the surface-energy variant takes one global theta", idx);
   const double pi = 3.14159265358979323846;
   auto angle_ok = [&](double t) { return t > 0 && t < pi; };
   if (!g->theta_node && !angle_ok(p->theta)) return fail(LBCG_E_UNSTABLE_PARAM, "lattice %d: theta outside (0, pi)", idx);
@@ -329,6 +333,7 @@ LaunchStep make_launch(lbcg_handle* h, int src, double* macro, int tile_begin, i
   p.flags = h->d_flags;
   p.nbmask = h->d_nbmask;
   p.err = h->d_err;
+  p.scheme_b = h->scheme_b;
   p.band_rn = h->d_band_rn;
   p.wall = h->d_wall;
   p.node_total = h->node_total;
@@ -479,6 +484,9 @@ lbcg_status lbcg_create_batch(int32_t n, const lbcg_geometry* geoms, const lbcg_
     d.rho0 = p.rho0;
     d.u_in = p.u_in;
     d.in_prof = p.inlet_profile;
+    d.wetting = p.wetting;
+    if (p.wetting == 1) h->scheme_b = 1;
+    d.cos_theta = std::cos(p.theta);
     {
       // fluid rows of the inlet column: the profile spans them, walls half a node beyond
       int lo = -1, hi = -1;
@@ -882,6 +890,7 @@ lbcg_status lbcg_adjoint(lbcg_handle* h, const lbcg_adjoint_spec* spec, lbcg_gra
   if (h->prec != LBCG_FP64 && h->prec != LBCG_FP32)
     return fail(LBCG_E_UNSUPPORTED, "the adjoint runs on FP64 or FP32 handles");
   if (h->lats.size() != 1) return fail(LBCG_E_UNSUPPORTED, "the adjoint runs on single-lattice handles");
+  if (h->lats[0].prm.wetting != 0) return fail(LBCG_E_UNSUPPORTED, "the adjoint differentiates wetting scheme (a) only");
   if (spec->nsteps < 1 || spec->checkpoint < 1) return fail(LBCG_E_ARG, "nsteps and checkpoint must be >= 1");
   if (spec->objective == LBCG_OBJ_WEIGHTED && !spec->weight) return fail(LBCG_E_ARG, "weighted objective needs weight");
   if (spec->objective != LBCG_OBJ_WEIGHTED && spec->objective != LBCG_OBJ_FINGER_LENGTH &&

@@ -29,6 +29,7 @@ struct LaunchStep {
   const int4* strips;     // sweep schedule: (lattice, x0, y_begin, y_end)
   int nstrips;
   int sweep;              // 1: k_sweep over strips, 0: k_step over tiles
+  int scheme_b;           // 1: some lattice of the batch uses wetting scheme (b)
   double* macro;          // non-null: write macroscopic fields instead of stepping (tiles)
   cudaEvent_t* ev;        // non-null: 6 events recorded around k_band, k_wall, k_step
   int* err;               // device error word: a sweep block's bounded wait ran out

@@ -69,7 +69,9 @@ __global__ void __launch_bounds__(256) k_wall(const LatDev* __restrict__ lats, c
     const int yy = wrap_or_clamp(e.y + ey(a), L.ny, py);
     const long long k = (long long)yy * L.pitch + xx;
     T v;
-    if (fl[k] & F_SOLID) {
+    if ((fl[k] & F_SOLID) && L.wetting == 2) {
+      v = T(L.cos_theta);   // surface-energy formulation: rho^N = cos(theta) on the solid
+    } else if (fl[k] & F_SOLID) {
       // Eq. 29: weighted mean over the fluid neighbours of the outermost solid node
       T num = T(0), den = T(0);
 #pragma unroll
@@ -98,7 +100,10 @@ __global__ void __launch_bounds__(256) k_wall(const LatDev* __restrict__ lats, c
   const T eps = T(L.grad_eps);
   const T mag = rsqrt_(radd(rmul(gx, gx), rmul(gy, gy)));
   T cgx = gx, cgy = gy, nx = T(0), ny = T(0);
-  if (mag > eps) {
+  if (mag > eps && L.wetting == 2) {
+    nx = rdiv(gx, mag);   // no geometric correction: n from the raw gradient
+    ny = rdiv(gy, mag);
+  } else if (mag > eps) {
     const T esx = rdiv(gx, mag), esy = rdiv(gy, mag);                 // Eq. 30
     const T nsx = T(e.nsx), nsy = T(e.nsy), c = T(e.cos_t), s = T(e.sin_t);
     const T f1x = rsub(rmul(nsx, c), rmul(nsy, s));                   // Eq. 34, +theta
@@ -124,6 +129,37 @@ __global__ void __launch_bounds__(256) k_wall(const LatDev* __restrict__ lats, c
   wall[node_total + k] = cgy;
   wall[2 * node_total + k] = nx;
   wall[3 * node_total + k] = ny;
+}
+
+// Eq. 48, wetting scheme (b) (lbcg_params.wetting = 1): grad n at an outermost fluid node from
+// its fluid neighbours only, d_i n = sum_a w_a (n(x + e_a) - n(x)) e_ai / sum_a w_a e_ai^2 over
+// the directions a whose neighbour is fluid (bit a-1 of `solid` clear).  nxs/nys[a] hold n at
+// x + e_a (a = 0: the node).  Returned divided by 3 (= c_s^2): the bulk kernels keep their
+// Eq. 28 sums at that scale and apply 1/c_s^2 in the curvature.
+template <typename T>
+__device__ __forceinline__ void grad_n_scheme_b(const T nxs[9], const T nys[9], unsigned solid, T& dxx, T& dyx, T& dxy,
+                                                T& dyy) {
+  T sxx = T(0), syx = T(0), sxy = T(0), syy = T(0), wx = T(0), wy = T(0);
+#pragma unroll
+  for (int a = 1; a < 9; ++a) {
+    if ((solid >> (a - 1)) & 1u) continue;
+    const T w = wgt<T>(a), ddx = nxs[a] - nxs[0], ddy = nys[a] - nys[0];
+    if (ex(a)) {
+      sxx += T(ex(a)) * w * ddx;
+      syx += T(ex(a)) * w * ddy;
+      wx += w;
+    }
+    if (ey(a)) {
+      sxy += T(ey(a)) * w * ddx;
+      syy += T(ey(a)) * w * ddy;
+      wy += w;
+    }
+  }
+  const T third = T(1) / T(3);
+  dxx = wx > T(0) ? sxx / wx * third : T(0);
+  dyx = wx > T(0) ? syx / wx * third : T(0);
+  dxy = wy > T(0) ? sxy / wy * third : T(0);
+  dyy = wy > T(0) ? syy / wy * third : T(0);
 }
 
 // ------------------------------------------------------------------ k_step
@@ -327,6 +363,18 @@ __global__ void __launch_bounds__(32 * TY, sizeof(typename Store<S>::T) == 4 ? 1
       dxy += T(ey(a)) * tx;
       dyy += T(ey(a)) * ty;
     }
+  }
+  if (sL.wetting == 1 && (sfl[(ly + 3) * W3 + lx + 3] & F_OFB)) {
+    T nxs[9], nys[9];
+    unsigned solid = 0;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+      const int o = (c1y + ey(a)) * W1 + c1x + ex(a);
+      nxs[a] = snx[o];
+      nys[a] = sny[o];
+      if (a && (sfl[(ly + 3 + ey(a)) * W3 + lx + 3 + ex(a)] & F_SOLID)) solid |= 1u << (a - 1);
+    }
+    grad_n_scheme_b<T>(nxs, nys, solid, dxx, dyx, dxy, dyy);
   }
   const T nxo = snx[c1y * W1 + c1x], nyo = sny[c1y * W1 + c1x];
   // Eq. 13 (the factor 3 = 1/c_s^2 of Eq. 28 applied once) and Eq. 10
@@ -665,7 +713,18 @@ __global__ void __launch_bounds__(NTH, sizeof(typename Store<S>::T) == 4 ? 1024 
     // d_x (n_x, n_y) and d_y (n_x, n_y)
     const V dX = P::fma(W1, P::sub(n0_r, n0_l), P::mul(W2, P::add(P::sub(np_r, np_l), P::sub(nm_r, nm_l))));
     const V dY = P::fma(W1, P::sub(np_c, nm_c), P::mul(W2, P::sub(P::add(np_r, np_l), P::add(nm_l, nm_r))));
-    const T dxx = dX.x, dyx = dX.y, dxy = dY.x, dyy = dY.y;
+    T dxx = dX.x, dyx = dX.y, dxy = dY.x, dyy = dY.y;
+    if (sL.wetting == 1 && (myf & F_OFB)) {
+      const V* rows3[3] = {nm, n0v, np};
+      T nxs[9], nys[9];
+#pragma unroll
+      for (int a = 0; a < 9; ++a) {
+        const V v = rows3[ey(a) + 1][t + ex(a)];
+        nxs[a] = v.x;
+        nys[a] = v.y;
+      }
+      grad_n_scheme_b<T>(nxs, nys, mask, dxx, dyx, dxy, dyy);
+    }
     const T nxo = n0_c.x, nyo = n0_c.y;
     const T kappa = T(3) * (-nxo * nxo * dyy - nyo * nyo * dxx + nxo * nyo * (dxy + dyx));
     const T hsk = T(0.5) * sigma * kappa;
@@ -809,7 +868,8 @@ __device__ __forceinline__ void staged_pair(const S* row, int a, float& lo, floa
   }
 }
 
-template <typename S, int NTH>
+// kSchemeB: compiled in only for batches with a scheme-(b) lattice (the branch costs registers)
+template <typename S, int NTH, bool kSchemeB>
 __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSweepFMinBlocks16) k_sweepf(SweepArgs A) {
   using T = float;
   constexpr int RR = 5;   // rho^N / flags ring (rows r-4 .. r)
@@ -1043,8 +1103,21 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
     const V nm_l = nm[t - 1], nm_c = nm[t], nm_r = nm[t + 1];
     const V n0_l = n0v[t - 1], n0_c = n0v[t], n0_r = n0v[t + 1];
     const V np_l = np[t - 1], np_c = np[t], np_r = np[t + 1];
-    const V dX = P::fma(W1, P::sub(n0_r, n0_l), P::mul(W2, P::add(P::sub(np_r, np_l), P::sub(nm_r, nm_l))));
-    const V dY = P::fma(W1, P::sub(np_c, nm_c), P::mul(W2, P::sub(P::add(np_r, np_l), P::add(nm_l, nm_r))));
+    V dX = P::fma(W1, P::sub(n0_r, n0_l), P::mul(W2, P::add(P::sub(np_r, np_l), P::sub(nm_r, nm_l))));
+    V dY = P::fma(W1, P::sub(np_c, nm_c), P::mul(W2, P::sub(P::add(np_r, np_l), P::add(nm_l, nm_r))));
+    if constexpr (kSchemeB) {
+      if (sL.wetting == 1 && (myf & F_OFB)) {
+        const V* rows3[3] = {nm, n0v, np};
+        T nxs[9], nys[9];
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+          const V v = rows3[ey(a) + 1][t + ex(a)];
+          nxs[a] = v.x;
+          nys[a] = v.y;
+        }
+        grad_n_scheme_b<T>(nxs, nys, mask, dX.x, dX.y, dY.x, dY.y);
+      }
+    }
     const T nxo = n0_c.x, nyo = n0_c.y;
     const T kappa = T(3) * (-nxo * nxo * dY.y - nyo * nyo * dX.x + nxo * nyo * (dY.x + dX.y));
     const T hsk = hsig * kappa;
@@ -1222,7 +1295,10 @@ static cudaError_t launch_all(const LaunchStep& p, cudaStream_t st) {
     if (p.nstrips > 0) {
       SweepArgs B{p.lats, p.strips, p.src, p.dst, p.flags, p.nbmask, p.wall, p.node_total, p.err};
       if constexpr (sizeof(T) == 4)
-        k_sweepf<S, kSweepThreads><<<p.nstrips, kSweepThreads, sweepf_dyn_smem<S>(), st>>>(B);
+      {
+        if (p.scheme_b) k_sweepf<S, kSweepThreads, true><<<p.nstrips, kSweepThreads, sweepf_dyn_smem<S>(), st>>>(B);
+        else k_sweepf<S, kSweepThreads, false><<<p.nstrips, kSweepThreads, sweepf_dyn_smem<S>(), st>>>(B);
+      }
       else k_sweep<S, kSweepThreads><<<p.nstrips, kSweepThreads, 0, st>>>(B);
     }
   } else if (p.ntiles > 0) {
@@ -1249,8 +1325,12 @@ static cudaError_t launch_all(const LaunchStep& p, cudaStream_t st) {
 
 template <typename S>
 static cudaError_t prepare_sweepf() {
-  return cudaFuncSetAttribute(k_sweepf<S, kSweepThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              sweepf_dyn_smem<S>());
+  cudaError_t e = cudaFuncSetAttribute(k_sweepf<S, kSweepThreads, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, sweepf_dyn_smem<S>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_sweepf<S, kSweepThreads, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             sweepf_dyn_smem<S>());
+  return e;
 }
 
 cudaError_t prepare_kernels(int prec) {

@@ -57,6 +57,7 @@ class Params:
     rho_out: float = 1.0         # outlet density (bc_x == "inout")
     grad_eps: float = 1e-12      # |grad rho^N| at or below which n = 0
     inlet_profile: int = 0       # 0: uniform u_in; 1: Poiseuille profile of maximum u_in
+    wetting: int = 0             # 0: improved scheme (a); 1: scheme (b), Eq. 48; 2: surface energy
 
 
 @dataclasses.dataclass

@@ -35,7 +35,7 @@ class lbcg_geometry(C.Structure):
 
 class lbcg_params(C.Structure):
     _fields_ = [(n, C.c_double) for n in ("nu_R", "nu_B", "sigma", "theta", "beta", "s_e", "s_eps", "s_q",
-                                          "rho0", "u_in", "rho_out", "grad_eps")] + [("inlet_profile", C.c_int32)]
+                                          "rho0", "u_in", "rho_out", "grad_eps")] + [("inlet_profile", C.c_int32), ("wetting", C.c_int32)]
 
 
 class lbcg_obs_spec(C.Structure):
@@ -158,7 +158,7 @@ def _marshal(geoms: Sequence[Geometry], prms: Sequence[Params]):
         G[i] = lbcg_geometry(g.nx, g.ny, _BCX[g.bc_x], _BCY[g.bc_y], solid.ctypes.data_as(C.POINTER(C.c_uint8)),
                              _dptr(rn), _dptr(nrm), _dptr(th))
         P[i] = lbcg_params(p.nu_R, p.nu_B, p.sigma, p.theta, p.beta, p.s_e, p.s_eps, p.s_q, p.rho0, p.u_in,
-                           p.rho_out, p.grad_eps, int(p.inlet_profile))
+                           p.rho_out, p.grad_eps, int(p.inlet_profile), int(p.wetting))
     return G, P, keep
 
 

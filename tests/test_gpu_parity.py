@@ -73,6 +73,16 @@ def _cases():
     rng = np.random.default_rng(7)
     g.theta_node = rng.uniform(th(40), th(140), size=(g.ny, g.nx))
     yield "per_node_theta_45x21", g, I.Params(sigma=0.02)
+    g = I.flat_wall_droplet(45, 21, R=7.0, xc=20.7, noise=1e-3, seed=12, closed_x=True)
+    yield "scheme_b_closed_box_45x21", g, I.Params(theta=th(50), sigma=0.02, wetting=1)
+    g = I.cylinder_droplet(60, 50, Rs=10.0, cx=30.0, cy=18.0, Rd=9.0, theta=th(110), noise=1e-3, seed=13,
+                           analytic_normal=False)
+    yield "scheme_b_cylinder_60x50", g, I.Params(theta=th(110), sigma=0.02, wetting=1)
+    g = I.flat_wall_droplet(45, 21, R=7.0, xc=20.7, noise=1e-3, seed=14)
+    yield "surface_energy_45x21", g, I.Params(theta=th(70), sigma=0.02, wetting=2)
+    g = I.displacement_channel(W=20, L=110, x_I=25.0, seed=15, noise=1e-3)
+    yield "surface_energy_channel_110x22", g, I.Params(**{**I.fingering_params(M=5.0, Ca=0.1, theta_deg=40.0).__dict__,
+                                                         "wetting": 2})
     yield "tiny_periodic_7x6", I.periodic_box_droplet(7, 6, R=2.2, xc=3.3, yc=2.8, noise=1e-2, seed=8), \
         I.Params(sigma=0.03)
     yield "tiny_walls_5x5", I.flat_wall_droplet(5, 5, R=1.6, xc=2.2, noise=1e-2, seed=9), I.Params(sigma=0.03)
@@ -392,3 +402,21 @@ def test_high_viscosity_ratio_plateau_of_the_paper():
             assert abs(dS[M] - 2 / 3 * 0.01) <= 0.01 * 2 / 3 * 0.01, (M, dS[M])
             assert abs(dL) <= 1e-5, (M, dL)
     assert dS[5.0] < dS[20.0] - 1e-3
+
+
+@pytest.mark.parametrize("wetting", [1, 2], ids=["scheme_b", "surface_energy"])
+def test_wetting_variants_in_every_schedule(wetting):
+    """The wetting variants through the y-sweep and tile kernels: FP64 40 steps within 1e-10 of
+    the oracle; FP32 one step from the oracle's state within 2e-6."""
+    g = I.flat_wall_droplet(77, 29, R=11.0, xc=30.2, noise=1e-3, seed=2, closed_x=True)
+    p = I.Params(theta=math.radians(130), sigma=0.03, nu_R=0.1, nu_B=0.3, wetting=wetting)
+    lat, ref = oracle_run(g, p, 40)
+    _, s20 = oracle_run(g, p, 20)
+    _, ref1 = oracle_run(g, p, 1, torch.from_numpy(s20[0]), torch.from_numpy(s20[1]))
+    for ty, rows in ((4, None), (0, 0)):
+        L, got = gpu_run(g, p, 40, ty=ty, rows=rows)
+        L.close()
+        assert np.abs(got - ref).max() <= TOL64, (ty, rows, np.abs(got - ref).max())
+        L, got1 = gpu_run(g, p, 1, prec="fp32", ty=8 if ty else 0, rows=rows, state=s20)
+        L.close()
+        assert np.abs(got1 - ref1).max() <= 2e-6, (ty, rows, np.abs(got1 - ref1).max())
