@@ -887,6 +887,10 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
   extern __shared__ __align__(128) unsigned char sraw_bytes[];
   S* sraw = reinterpret_cast<S*>(sraw_bytes);
   __shared__ __align__(8) uint64_t sbar[2];
+  // the staged rows' flags and neighbour-solid masks ([slot][0: flags, 1: mask][byte]), and the
+  // mask of rows r-4 .. r for the collision two rows later
+  __shared__ __align__(16) uint8_t sfg[2][2][NTH + 32];
+  __shared__ uint8_t snb[RR][NTH];
 
   const int4 sp = A.strips[blockIdx.x];
   const int t = threadIdx.x;
@@ -924,6 +928,11 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
   const int soff = ((xm >> 5) >= sA && (xm >> 5) <= sB) ? ((xm >> 5) - sA) * kSeg + (xm & 31) * 2
                    : ((xm >> 5) == sX ? (kStageSegs - 1) * kSeg + (xm & 31) * 2 : -1);
   const unsigned bytesA = unsigned((sB - sA + 1) * kSeg * sizeof(S));
+  // flag / mask bytes of the strip's columns, from a 16-byte boundary, a multiple of 16 long
+  // (the 32-aligned pitch keeps it inside the row); fo: this column's byte, -1 if outside
+  const int fx0 = max(sp.y - 2, 0) & ~15;
+  const unsigned fbytes = unsigned((min(sp.y + NTH - 3, nx - 1) - fx0 + 16) & ~15);
+  const int fo = (xm >= fx0 && xm < fx0 + int(fbytes)) ? xm - fx0 : -1;
   const unsigned bytesX = sX >= 0 ? unsigned(kSeg * sizeof(S)) : 0u;
 
   auto map_row = [&](int v) {
@@ -944,8 +953,10 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
     S* d = sraw + slot * (kStageSegs * kSeg);
     const S* g = src + (long long)y * rowseg;
     fence_proxy_async();
-    mbar_expect_tx(&sbar[slot], bytesA + bytesX);
+    mbar_expect_tx(&sbar[slot], bytesA + bytesX + 2 * fbytes);
     bulk_copy_g2s(d, g + sA * kSeg, bytesA, &sbar[slot]);
+    bulk_copy_g2s(&sfg[slot][0][0], fl + (long long)y * pitch + fx0, fbytes, &sbar[slot]);
+    bulk_copy_g2s(&sfg[slot][1][0], nbm + (long long)y * pitch + fx0, fbytes, &sbar[slot]);
     if (sX >= 0) bulk_copy_g2s(d + (kStageSegs - 1) * kSeg, g + sX * kSeg, bytesX, &sbar[slot]);
   };
   unsigned phase = 0;   // bit s: parity of the next completion of slot s
@@ -957,7 +968,6 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
   }
   __syncthreads();
   if (t == 0) stage_row(map_row(ys - 2), (ys - 2) & 1);
-  uint8_t f_cur = fl[map_row(ys - 2) * pitch + xm], f_nxt = 0;
 
   auto body = [&](const int r) {
     {
@@ -987,19 +997,18 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
     if (r + 1 <= ye + 1) {
       const int y = map_row(r + 1);
       if (t == 0) stage_row(y, (r + 1) & 1);
-      f_nxt = fl[y * pitch + xm];
     }
-    const uint8_t f_r = f_cur;
     const int p = r - 2;
     const bool collide = p >= ys && interior && !(sfl[s2][t] & F_SOLID);
-    uint8_t mask = 0;
-    if (collide) mask = nbm[ym2 * pitch + xm];
+    const uint8_t mask = collide ? snb[s2][t] : 0;
     // ---- stage 1: rho^N, totals and colour densities of row r
     {
       T v = T(0);
       const int slot = r & 1;
       if (!mbar_wait(&sbar[slot], (phase >> slot) & 1u, A.err)) lost = true;
       phase ^= 1u << slot;
+      const uint8_t f_r = fo >= 0 ? sfg[slot][0][fo] : fl[ym0 * pitch + xm];
+      snb[s0][t] = fo >= 0 ? sfg[slot][1][fo] : nbm[ym0 * pitch + xm];
       if (!(f_r & F_SOLID)) {
         T fr[9], fb[9];
         if (soff >= 0) {
@@ -1209,7 +1218,6 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
 
   for (int r = ys - 2; r <= ye + 1; ++r) {
     body(r);
-    f_cur = f_nxt;
   }
   // after a lost wait, do not leave with copies into this block's shared memory in flight
   if (lost)
