@@ -237,11 +237,12 @@ lbcg_status lbcg_diagnostics(lbcg_handle* h, int32_t lattice, const lbcg_diag_sp
 
 /* Kernel timing with CUDA events on the handle's stream.  While enabled, lbcg_step launches
  * the kernels of each step directly (no graph) with an event recorded before and after each
- * of k_band, k_wall and k_step.  lbcg_kernel_times synchronises, returns in ms3[0..2] the
- * summed milliseconds of those three kernels over the steps taken since the last call (or
- * since enabling) and their number in *steps, and restarts the sums. */
+ * of its two kernels: the wall kernel (rho^N on the wall band, Eq. 28-36 on the outermost fluid
+ * nodes) and the step kernel (y-sweep or tiles).  lbcg_kernel_times synchronises, returns in
+ * ms2[0..1] the summed milliseconds of those two kernels over the steps taken since the last
+ * call (or since enabling) and their number in *steps, and restarts the sums. */
 lbcg_status lbcg_profile(lbcg_handle* h, int32_t enable);
-lbcg_status lbcg_kernel_times(lbcg_handle* h, double* ms3, int64_t* steps);
+lbcg_status lbcg_kernel_times(lbcg_handle* h, double* ms2, int64_t* steps);
 
 /* Number of kernel launches one time step enqueues, and the number of lattice nodes
  * (fluid and solid) all lattices hold. */

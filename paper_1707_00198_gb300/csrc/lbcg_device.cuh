@@ -75,6 +75,26 @@ struct OfbEntry {
   double nsx, nsy, cos_t, sin_t;
 };
 
+// Work unit of the wall kernel (one block): consecutive outermost-fluid entries [wall0,
+// wall0 + nwall) of lattice `lat`, the fluid nodes [band0, band0 + nband) of the band list
+// (each as the offset of its populations in the lattice's pool, pop_node) whose rho^N they need, and the outermost solid nodes [virt0, virt0 + nvirt) of the virtual
+// list next to them (Eq. 29).  The kernel keeps rho^N of the band nodes in shared memory at
+// local indices 0 .. nband-1 and the virtual values at nband .. nband+nvirt-1.
+struct WallGroup {
+  int lat, wall0, nwall, band0, nband, virt0, nvirt, pad_;
+};
+// Local indices into that shared array, one per direction a = 1..8 (element a-1): for an
+// outermost fluid node, the value at x + e_a (band node or virtual solid node); for a virtual
+// node, the band node at x + e_a, or kWallNone if that neighbour is solid.
+struct WallSten {
+  uint16_t i[8];
+};
+constexpr uint16_t kWallNone = 0xFFFF;
+constexpr int kWallThreads = 128;   // block size
+constexpr int kWallMaxNodes = 256;  // outermost fluid nodes per group, at most
+constexpr int kWallCap = 1024;      // shared values per group (band + virtual), at most
+constexpr int kWallVirtCap = 512;   // virtual nodes per group, at most
+
 // D2Q9 velocity set (Sec. II.A), as constant-folding functions of the direction index.
 __host__ __device__ constexpr int ex(int a) {
   return (a == 1 || a == 5 || a == 8) ? 1 : ((a == 3 || a == 6 || a == 7) ? -1 : 0);

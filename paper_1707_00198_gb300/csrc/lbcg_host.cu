@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -72,7 +73,6 @@ struct lbcg_handle {
   int* d_err = nullptr;    // device error word (a sweep block's bounded wait ran out)
   double* d_usnap = nullptr;          // velocity stored by lbcg_diagnostics ([2][node_total])
   std::vector<int64_t> snap_step;     // per lattice: step of that velocity, -1 = none
-  void* d_band_rn = nullptr;
   void* d_wall = nullptr;
   double* d_macro = nullptr;
   LatDev* d_lats = nullptr;
@@ -82,8 +82,11 @@ struct lbcg_handle {
   int sweep_rows = 0;     // rows per strip segment, 0 = automatic
   int4* d_strips = nullptr;
   int nstrips = 0;
-  int4* d_band = nullptr;
-  int nband = 0;
+  WallGroup* d_groups = nullptr;   // wall kernel work units and their tables
+  int ngroups = 0;
+  int* d_wband = nullptr;
+  WallSten* d_wvirt = nullptr;
+  WallSten* d_wsten = nullptr;
   OfbEntry* d_ofb = nullptr;
   int nofb = 0;
   double* d_obs = nullptr;   // partials then outputs
@@ -91,7 +94,7 @@ struct lbcg_handle {
   std::vector<uint8_t> flags_host;
   std::vector<OfbEntry> ofb_host;
   bool profiling = false;
-  std::vector<cudaEvent_t> events;   // 6 per profiled step
+  std::vector<cudaEvent_t> events;   // 4 per profiled step
   size_t events_used = 0;
 };
 
@@ -165,9 +168,9 @@ lbcg_status validate(const lbcg_geometry* g, const lbcg_params* p, int idx) {
   return LBCG_OK;
 }
 
-// Classification of one lattice (Sec. II.C): flags, wall band, outermost-fluid entries.
+// Classification of one lattice (Sec. II.C): flags, neighbour masks, outermost-fluid entries.
 void classify(const lbcg_geometry* g, const lbcg_params* p, int lat, std::vector<uint8_t>& flags_local,
-              std::vector<uint8_t>& mask_local, std::vector<int4>& band, std::vector<OfbEntry>& ofb) {
+              std::vector<uint8_t>& mask_local, std::vector<OfbEntry>& ofb) {
   const int nx = g->nx, ny = g->ny;
   const bool px = g->bc_x == LBCG_BCX_PERIODIC, py = g->bc_y == LBCG_BCY_PERIODIC;
   auto S = [&](int x, int y) { return g->solid[(size_t)y * nx + x] != 0; };
@@ -200,20 +203,6 @@ void classify(const lbcg_geometry* g, const lbcg_params* p, int lat, std::vector
       if (near) f |= F_NEAR;
       flags_local[(size_t)y * nx + x] = f;
     }
-  // wall band: outermost fluid nodes and their fluid neighbours
-  std::vector<uint8_t> inband((size_t)nx * ny, 0);
-  for (int y = 0; y < ny; ++y)
-    for (int x = 0; x < nx; ++x) {
-      if (!(flags_local[(size_t)y * nx + x] & F_OFB)) continue;
-      inband[(size_t)y * nx + x] = 1;
-      for (int a = 1; a < 9; ++a) {
-        const int xx = wrap_clamp(x + EXH[a], nx, px), yy = wrap_clamp(y + EYH[a], ny, py);
-        if (!S(xx, yy)) inband[(size_t)yy * nx + xx] = 1;
-      }
-    }
-  for (int y = 0; y < ny; ++y)
-    for (int x = 0; x < nx; ++x)
-      if (inband[(size_t)y * nx + x]) band.push_back(make_int4(lat, x, y, 0));
   // E8 stencil (Eq. 33): the weights are k/5040 with integer k = 960, 448, 84, 32, 1 for
   // |c|^2 = 1, 2, 4, 5, 8; the sums are taken exactly over the integers k
   struct C8 {
@@ -269,6 +258,102 @@ void classify(const lbcg_geometry* g, const lbcg_params* p, int lat, std::vector
     }
 }
 
+// Work units of the wall kernel: runs of consecutive outermost fluid entries of one lattice,
+// at most gmax entries and kWallCap shared values (band + virtual nodes) per unit.  Each unit
+// lists the fluid nodes whose rho^N its entries read (their fluid neighbours and the fluid
+// neighbours of their solid neighbours, Eq. 28-29) and the solid neighbours (virtual nodes),
+// and every entry gets the local index of the value at each of its 8 neighbours.  Nodes next
+// to two units appear in both.  Each unit's band run starts on a multiple of 4 entries and the
+// list ends with 4 padding entries: the kernel copies the runs in 16-byte pieces.
+void build_wall_groups(const std::vector<LatHost>& lats, const std::vector<OfbEntry>& ofb, int gmax,
+                       std::vector<WallGroup>& groups, std::vector<int>& band, std::vector<WallSten>& virt,
+                       std::vector<WallSten>& sten) {
+  groups.clear();
+  band.clear();
+  virt.clear();
+  sten.assign(ofb.size(), WallSten{});
+  size_t i = 0;
+  while (i < ofb.size()) {
+    const int l = ofb[i].lat;
+    const LatHost& L = lats[l];
+    const int nx = L.nx, ny = L.ny;
+    const bool px = L.bcx == LBCG_BCX_PERIODIC, py = L.bcy == LBCG_BCY_PERIODIC;
+    auto solid = [&](long long k) { return L.solid[(size_t)k] != 0; };
+    auto nbr = [&](long long k, int a) {
+      const int x = int(k % nx), y = int(k / nx);
+      return (long long)wrap_clamp(y + EYH[a], ny, py) * nx + wrap_clamp(x + EXH[a], nx, px);
+    };
+    std::unordered_map<long long, int> bmap, vmap;
+    std::vector<long long> gb, gv, nb, nv;
+    size_t j = i;
+    while (j < ofb.size() && ofb[j].lat == l && j - i < (size_t)gmax) {
+      nb.clear();
+      nv.clear();
+      auto want_band = [&](long long k) {
+        if (!bmap.count(k) && std::find(nb.begin(), nb.end(), k) == nb.end()) nb.push_back(k);
+      };
+      const long long k0 = (long long)ofb[j].y * nx + ofb[j].x;
+      for (int a = 1; a < 9; ++a) {
+        const long long k = nbr(k0, a);
+        if (!solid(k)) {
+          want_band(k);
+        } else if (!vmap.count(k) && std::find(nv.begin(), nv.end(), k) == nv.end()) {
+          nv.push_back(k);
+          for (int b = 1; b < 9; ++b) {
+            const long long k2 = nbr(k, b);
+            if (!solid(k2)) want_band(k2);
+          }
+        }
+      }
+      if (j > i && (gb.size() + gv.size() + nb.size() + nv.size() > (size_t)kWallCap ||
+                    gv.size() + nv.size() > (size_t)kWallVirtCap))
+        break;
+      for (long long k : nb) {
+        bmap[k] = int(gb.size());
+        gb.push_back(k);
+      }
+      for (long long k : nv) {
+        vmap[k] = int(gv.size());
+        gv.push_back(k);
+      }
+      ++j;
+    }
+    // row-major order, so that neighbouring threads load neighbouring nodes
+    std::sort(gb.begin(), gb.end());
+    std::sort(gv.begin(), gv.end());
+    for (size_t m = 0; m < gb.size(); ++m) bmap[gb[m]] = int(m);
+    for (size_t m = 0; m < gv.size(); ++m) vmap[gv[m]] = int(m);
+    while (band.size() % 4) band.push_back(0);   // each group's band run starts on 16 bytes
+    WallGroup G{};
+    G.lat = l;
+    G.wall0 = int(i);
+    G.nwall = int(j - i);
+    G.band0 = int(band.size());
+    G.nband = int(gb.size());
+    G.virt0 = int(virt.size());
+    G.nvirt = int(gv.size());
+    for (long long k : gb) band.push_back(pop_node(int(k % nx), int(k / nx), L.pitch));
+    for (long long k : gv) {
+      WallSten q{};
+      for (int b = 1; b < 9; ++b) {
+        const long long k2 = nbr(k, b);
+        q.i[b - 1] = solid(k2) ? kWallNone : uint16_t(bmap.at(k2));
+      }
+      virt.push_back(q);
+    }
+    for (size_t m = i; m < j; ++m) {
+      const long long k0 = (long long)ofb[m].y * nx + ofb[m].x;
+      for (int a = 1; a < 9; ++a) {
+        const long long k = nbr(k0, a);
+        sten[m].i[a - 1] = solid(k) ? uint16_t(G.nband + vmap.at(k)) : uint16_t(bmap.at(k));
+      }
+    }
+    groups.push_back(G);
+    i = j;
+  }
+  band.insert(band.end(), 4, 0);   // the last group's final 16-byte piece stays in bounds
+}
+
 void build_tiles(lbcg_handle* h, std::vector<int4>& tiles) {
   tiles.clear();
   for (size_t l = 0; l < h->lats.size(); ++l) {
@@ -321,10 +406,12 @@ void build_strips(lbcg_handle* h, std::vector<int4>& strips) {
 LaunchStep make_launch(lbcg_handle* h, int src, double* macro, int tile_begin, int tile_end) {
   LaunchStep p{};
   p.lats = h->d_lats;
-  p.band = h->d_band;
-  p.nband = h->nband;
+  p.groups = h->d_groups;
+  p.ngroups = h->ngroups;
+  p.wband = h->d_wband;
+  p.wvirt = h->d_wvirt;
+  p.wsten = h->d_wsten;
   p.ofb = h->d_ofb;
-  p.nofb = h->nofb;
   p.tiles = h->d_tiles + tile_begin;
   p.ntiles = tile_end - tile_begin;
   p.ty = h->ty;
@@ -334,7 +421,6 @@ LaunchStep make_launch(lbcg_handle* h, int src, double* macro, int tile_begin, i
   p.nbmask = h->d_nbmask;
   p.err = h->d_err;
   p.scheme_b = h->scheme_b;
-  p.band_rn = h->d_band_rn;
   p.wall = h->d_wall;
   p.node_total = h->node_total;
   p.macro = macro;
@@ -348,9 +434,9 @@ void free_handle(lbcg_handle* h) {
   if (!h) return;
   if (h->graph) cudaGraphExecDestroy(h->graph);
   for (cudaEvent_t e : h->events) cudaEventDestroy(e);
-  void* ptrs[] = {h->pool[0], h->pool[1], h->d_flags, h->d_band_rn, h->d_wall,   h->d_macro,
-                  h->d_lats,  h->d_tiles, h->d_band,  h->d_ofb,     h->d_obs,    h->d_strips,
-                  h->d_nbmask, h->d_err, h->d_usnap};
+  void* ptrs[] = {h->pool[0], h->pool[1], h->d_flags,  h->d_wall,  h->d_macro, h->d_lats,
+                  h->d_tiles, h->d_groups, h->d_wband, h->d_wvirt, h->d_wsten, h->d_ofb,
+                  h->d_obs,   h->d_strips, h->d_nbmask, h->d_err, h->d_usnap};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -444,7 +530,6 @@ lbcg_status lbcg_create_batch(int32_t n, const lbcg_geometry* geoms, const lbcg_
   }
   // layout
   std::vector<LatDev> ld(n);
-  std::vector<int4> band;
   std::vector<OfbEntry> ofb;
   long long node_total = 0;
   for (int l = 0; l < n; ++l) {
@@ -508,24 +593,36 @@ lbcg_status lbcg_create_batch(int32_t n, const lbcg_geometry* geoms, const lbcg_
   std::vector<uint8_t> mask_host((size_t)node_total, 0);
   for (int l = 0; l < n; ++l) {
     std::vector<uint8_t> fl, mk;
-    classify(&geoms[l], &prms[l], l, fl, mk, band, ofb);
+    classify(&geoms[l], &prms[l], l, fl, mk, ofb);
     const LatHost& L = h->lats[l];
     for (int y = 0; y < L.ny; ++y) {
       memcpy(&h->flags_host[L.node_off + (size_t)y * L.pitch], &fl[(size_t)y * L.nx], L.nx);
       memcpy(&mask_host[L.node_off + (size_t)y * L.pitch], &mk[(size_t)y * L.nx], L.nx);
     }
   }
-  h->nband = int(band.size());
   h->nofb = int(ofb.size());
   h->ofb_host = ofb;
+  // wall groups: smaller units when there are few outermost fluid nodes, so that they spread
+  // over the SMs
+  std::vector<WallGroup> groups;
+  std::vector<int> wband;
+  std::vector<WallSten> wvirt, wsten;
+  {
+    int gmax = kWallMaxNodes;
+    while (gmax > 32 && (h->nofb + gmax - 1) / gmax < 2 * kSMs) gmax >>= 1;
+    build_wall_groups(h->lats, ofb, gmax, groups, wband, wvirt, wsten);
+  }
+  h->ngroups = int(groups.size());
   const size_t es = elem_size(precision), cs = compute_size(precision);
   auto alloc = [&](void** p, size_t bytes) { return cudaMalloc(p, std::max<size_t>(bytes, 16)) == cudaSuccess; };
   bool ok = alloc(&h->pool[0], 18 * (size_t)node_total * es) && alloc(&h->pool[1], 18 * (size_t)node_total * es) &&
             alloc((void**)&h->d_flags, (size_t)node_total) && alloc((void**)&h->d_nbmask, (size_t)node_total) &&
             alloc((void**)&h->d_err, sizeof(int)) &&
-            alloc(&h->d_band_rn, (size_t)node_total * cs) &&
             alloc(&h->d_wall, 4 * (size_t)node_total * cs) && alloc((void**)&h->d_lats, n * sizeof(LatDev)) &&
-            alloc((void**)&h->d_band, band.size() * sizeof(int4)) &&
+            alloc((void**)&h->d_groups, groups.size() * sizeof(WallGroup)) &&
+            alloc((void**)&h->d_wband, wband.size() * sizeof(int)) &&
+            alloc((void**)&h->d_wvirt, wvirt.size() * sizeof(WallSten)) &&
+            alloc((void**)&h->d_wsten, wsten.size() * sizeof(WallSten)) &&
             alloc((void**)&h->d_ofb, ofb.size() * sizeof(OfbEntry)) &&
             alloc((void**)&h->d_obs, (obs_partials_doubles() + kObsOut) * sizeof(double));
   if (!ok) {
@@ -547,11 +644,16 @@ lbcg_status lbcg_create_batch(int32_t n, const lbcg_geometry* geoms, const lbcg_
   CKC(prepare_kernels(precision));
 
   CKC(cudaMemcpy(h->d_lats, ld.data(), n * sizeof(LatDev), cudaMemcpyHostToDevice));
-  if (!band.empty()) CKC(cudaMemcpy(h->d_band, band.data(), band.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  if (!groups.empty()) {
+    CKC(cudaMemcpy(h->d_groups, groups.data(), groups.size() * sizeof(WallGroup), cudaMemcpyHostToDevice));
+    CKC(cudaMemcpy(h->d_wband, wband.data(), wband.size() * sizeof(int), cudaMemcpyHostToDevice));
+    if (!wvirt.empty())
+      CKC(cudaMemcpy(h->d_wvirt, wvirt.data(), wvirt.size() * sizeof(WallSten), cudaMemcpyHostToDevice));
+    CKC(cudaMemcpy(h->d_wsten, wsten.data(), wsten.size() * sizeof(WallSten), cudaMemcpyHostToDevice));
+  }
   if (!ofb.empty()) CKC(cudaMemcpy(h->d_ofb, ofb.data(), ofb.size() * sizeof(OfbEntry), cudaMemcpyHostToDevice));
   CKC(cudaMemset(h->pool[0], 0, 18 * (size_t)node_total * es));
   CKC(cudaMemset(h->pool[1], 0, 18 * (size_t)node_total * es));
-  CKC(cudaMemset(h->d_band_rn, 0, (size_t)node_total * cs));
   CKC(cudaMemset(h->d_wall, 0, 4 * (size_t)node_total * cs));
   {
     lbcg_status s = upload_tiles(h);
@@ -607,8 +709,8 @@ lbcg_status lbcg_step(lbcg_handle* h, int64_t nsteps) {
   if (nsteps < 0) return fail(LBCG_E_ARG, "nsteps < 0");
   while (nsteps > 0) {
     if (h->profiling) {
-      if (h->events.size() < h->events_used + 6) {
-        for (int k = 0; k < 6; ++k) {
+      if (h->events.size() < h->events_used + 4) {
+        for (int k = 0; k < 4; ++k) {
           cudaEvent_t e;
           CK(h, cudaEventCreate(&e));
           h->events.push_back(e);
@@ -616,7 +718,7 @@ lbcg_status lbcg_step(lbcg_handle* h, int64_t nsteps) {
       }
       LaunchStep p = make_launch(h, h->cur, nullptr, 0, h->ntiles);
       p.ev = h->events.data() + h->events_used;
-      h->events_used += 6;
+      h->events_used += 4;
       CK(h, launch_step(h->prec, p, h->stream));
       h->cur ^= 1;
       h->step += 1;
@@ -1222,26 +1324,26 @@ lbcg_status lbcg_profile(lbcg_handle* h, int32_t enable) {
   return LBCG_OK;
 }
 
-lbcg_status lbcg_kernel_times(lbcg_handle* h, double* ms3, int64_t* steps) {
+lbcg_status lbcg_kernel_times(lbcg_handle* h, double* ms2, int64_t* steps) {
   lbcg_status s = check_handle(h);
   if (s != LBCG_OK) return s;
-  if (!ms3 || !steps) return fail(LBCG_E_ARG, "NULL output");
+  if (!ms2 || !steps) return fail(LBCG_E_ARG, "NULL output");
   CK(h, cudaStreamSynchronize(h->stream));
-  ms3[0] = ms3[1] = ms3[2] = 0.0;
-  for (size_t i = 0; i + 6 <= h->events_used; i += 6)
-    for (int k = 0; k < 3; ++k) {
+  ms2[0] = ms2[1] = 0.0;
+  for (size_t i = 0; i + 4 <= h->events_used; i += 4)
+    for (int k = 0; k < 2; ++k) {
       float t = 0.f;
       CK(h, cudaEventElapsedTime(&t, h->events[i + 2 * k], h->events[i + 2 * k + 1]));
-      ms3[k] += t;
+      ms2[k] += t;
     }
-  *steps = (int64_t)(h->events_used / 6);
+  *steps = (int64_t)(h->events_used / 4);
   h->events_used = 0;
   return LBCG_OK;
 }
 
 int32_t lbcg_launches_per_step(const lbcg_handle* h) {
   if (!h) return 0;
-  return (h->nband > 0 ? 1 : 0) + (h->nofb > 0 ? 1 : 0) + ((h->sweep ? h->nstrips : h->ntiles) > 0 ? 1 : 0);
+  return (h->ngroups > 0 ? 1 : 0) + ((h->sweep ? h->nstrips : h->ntiles) > 0 ? 1 : 0);
 }
 
 int64_t lbcg_total_nodes(const lbcg_handle* h) {

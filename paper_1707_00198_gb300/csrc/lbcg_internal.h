@@ -12,10 +12,12 @@ namespace lbcg {
 // Everything one launch of the step kernels needs (device pointers).
 struct LaunchStep {
   const LatDev* lats;
-  const int4* band;       // wall band list (lattice, x, y, -)
-  int nband;
-  const OfbEntry* ofb;    // outermost fluid list
-  int nofb;
+  const WallGroup* groups;   // wall kernel work units
+  int ngroups;
+  const int* wband;          // band nodes of the groups (population offset in their lattice)
+  const WallSten* wvirt;     // virtual (outermost solid) nodes of the groups
+  const WallSten* wsten;     // per outermost fluid node: its 8 neighbours' local indices
+  const OfbEntry* ofb;       // outermost fluid list
   const int4* tiles;      // tile list (lattice, x0, y0, -)
   int ntiles;
   int ty;                 // tile height (tiles are 32 wide)
@@ -23,7 +25,6 @@ struct LaunchStep {
   void* dst;
   const uint8_t* flags;
   const uint8_t* nbmask;  // per node: bit a-1 set if the neighbour in direction a is solid
-  void* band_rn;
   void* wall;
   long long node_total;
   const int4* strips;     // sweep schedule: (lattice, x0, y_begin, y_end)
@@ -31,7 +32,7 @@ struct LaunchStep {
   int sweep;              // 1: k_sweep over strips, 0: k_step over tiles
   int scheme_b;           // 1: some lattice of the batch uses wetting scheme (b)
   double* macro;          // non-null: write macroscopic fields instead of stepping (tiles)
-  cudaEvent_t* ev;        // non-null: 6 events recorded around k_band, k_wall, k_step
+  cudaEvent_t* ev;        // non-null: 4 events recorded around k_wall and the step kernel
   int* err;               // device error word: a sweep block's bounded wait ran out
 };
 

@@ -1,10 +1,10 @@
 // Kernels of one time step of the colour-gradient LBM with the improved wetting scheme
 // (arXiv 1707.00198, Sec. II).  Per step, in stream order:
-//   k_band  : rho^N (Eq. 12, 16) on the wall band = outermost fluid nodes and their fluid
-//             neighbours, from the post-streaming populations stored at each node;
-//   k_wall  : on every outermost fluid node the gradient of Eq. 28 with the virtual values
-//             of Eq. 29 and the contact-angle correction of Eq. 30-36 -> corrected gradient
-//             and unit normal, kept in two small node arrays;
+//   k_wall  : per group of outermost fluid nodes, rho^N (Eq. 12, 16) of the wall band (those
+//             nodes and their fluid neighbours) from the post-streaming populations, the
+//             virtual values of Eq. 29, then on each outermost fluid node the gradient of
+//             Eq. 28 and the contact-angle correction of Eq. 30-36 -> corrected gradient and
+//             unit normal, kept in small node arrays;
 //   k_step  : the fused bulk step over 32 x TY tiles: loads of each node's own populations
 //             -> rho^N on the tile plus a 2-node halo (shared memory) ->
 //             n on the tile plus a 1-node halo (outermost-fluid values from k_wall, virtual
@@ -25,82 +25,41 @@ struct StepArgs {
   const void* src;        // population pool read this step
   void* dst;              // population pool written this step
   const uint8_t* flags;   // node flags
-  const void* band_rn;    // rho^N on the wall band (compute type)
   void* wall;             // 4 planes of node arrays: g_x, g_y, n_x, n_y (compute type)
   long long node_total;   // elements per node-array plane
   double* macro;          // 4 planes of doubles: rho_R, rho_B, u_x, u_y (macro mode)
 };
 
-// ------------------------------------------------------------------ k_band
-template <typename S>
-__global__ void __launch_bounds__(256) k_band(const LatDev* __restrict__ lats, const int4* __restrict__ list,
-                                              int n, const S* __restrict__ src,
-                                              typename Store<S>::T* __restrict__ band_rn) {
-  using T = typename Store<S>::T;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int4 e = list[i];
-  const LatDev& L = lats[e.x];
-  const int x = e.y, y = e.z;
-  T fr[9], fb[9], rR, rB;
-  load_node<S>(L, src, x, y, fr, fb);
-  band_rn[L.node_off + (long long)y * L.pitch + x] = colour_indicator(fr, fb, rR, rB);
-}
-
 // ------------------------------------------------------------------ k_wall
-// Eq. 28 with Eq. 29 at solid neighbours, then Eq. 30-36; evaluated with the rounding-exact
-// helpers in the oracle's order (directions 1..8, products w*phi then sign).
+// One block per WallGroup, three phases separated by barriers:
+//   1. rho^N (Eq. 12, 16) of the group's band nodes from their post-streaming populations;
+//   2. the virtual value of each outermost solid node next to the group: the weighted mean of
+//      Eq. 29 over its fluid neighbours (rho^N = cos(theta) in the surface-energy variant);
+//   3. on each outermost fluid node, the gradient of Eq. 28 over those values, then the
+//      contact-angle correction of Eq. 30-36 -> corrected gradient and unit normal.
+// The arithmetic is rounding-exact in the oracle's order (directions 1..8, products w*phi
+// then sign); the host-built stencils only replace the flag lookups of that order.
+// Eq. 28 on an outermost fluid node from the shared values of its 8 neighbours, then
+// Eq. 30-36; writes the corrected gradient and unit normal.
 template <typename T>
-__global__ void __launch_bounds__(256) k_wall(const LatDev* __restrict__ lats, const OfbEntry* __restrict__ list,
-                                              int n, const uint8_t* __restrict__ flags,
-                                              const T* __restrict__ band_rn, T* __restrict__ wall,
-                                              long long node_total) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const OfbEntry e = list[i];
-  const LatDev& L = lats[e.lat];
-  const bool px = L.bcx == BC_PERIODIC, py = L.bcy == BC_PERIODIC;
-  const uint8_t* fl = flags + L.node_off;
-  const T* rn = band_rn + L.node_off;
+__device__ __forceinline__ void wall_node(const LatDev& sL, const OfbEntry& e, const WallSten& q, const T* val,
+                                          T* __restrict__ wall, long long node_total) {
   T gx = T(0), gy = T(0);
 #pragma unroll
   for (int a = 1; a < 9; ++a) {
-    const int xx = wrap_or_clamp(e.x + ex(a), L.nx, px);
-    const int yy = wrap_or_clamp(e.y + ey(a), L.ny, py);
-    const long long k = (long long)yy * L.pitch + xx;
-    T v;
-    if ((fl[k] & F_SOLID) && L.wetting == 2) {
-      v = T(L.cos_theta);   // surface-energy formulation: rho^N = cos(theta) on the solid
-    } else if (fl[k] & F_SOLID) {
-      // Eq. 29: weighted mean over the fluid neighbours of the outermost solid node
-      T num = T(0), den = T(0);
-#pragma unroll
-      for (int b = 1; b < 9; ++b) {
-        const int x2 = wrap_or_clamp(xx + ex(b), L.nx, px);
-        const int y2 = wrap_or_clamp(yy + ey(b), L.ny, py);
-        const long long k2 = (long long)y2 * L.pitch + x2;
-        if (!(fl[k2] & F_SOLID)) {
-          num = radd(num, rmul(wgt<T>(b), rn[k2]));
-          den = radd(den, wgt<T>(b));
-        }
-      }
-      v = rdiv(num, den);
-    } else {
-      v = rn[k];
-    }
-    const T t = rmul(wgt<T>(a), v);
-    if (ex(a) == 1) gx = radd(gx, t);
-    if (ex(a) == -1) gx = radd(gx, -t);
-    if (ey(a) == 1) gy = radd(gy, t);
-    if (ey(a) == -1) gy = radd(gy, -t);
+    const T tt = rmul(wgt<T>(a), val[q.i[a - 1]]);
+    if (ex(a) == 1) gx = radd(gx, tt);
+    if (ex(a) == -1) gx = radd(gx, -tt);
+    if (ey(a) == 1) gy = radd(gy, tt);
+    if (ey(a) == -1) gy = radd(gy, -tt);
   }
   const T cs2 = T(1.0 / 3.0);
   gx = rdiv(gx, cs2);
   gy = rdiv(gy, cs2);
-  const T eps = T(L.grad_eps);
+  const T eps = T(sL.grad_eps);
   const T mag = rsqrt_(radd(rmul(gx, gx), rmul(gy, gy)));
   T cgx = gx, cgy = gy, nx = T(0), ny = T(0);
-  if (mag > eps && L.wetting == 2) {
+  if (mag > eps && sL.wetting == 2) {
     nx = rdiv(gx, mag);   // no geometric correction: n from the raw gradient
     ny = rdiv(gy, mag);
   } else if (mag > eps) {
@@ -124,12 +83,115 @@ __global__ void __launch_bounds__(256) k_wall(const LatDev* __restrict__ lats, c
       ny = rdiv(cgy, m2);
     }
   }
-  const long long k = L.node_off + (long long)e.y * L.pitch + e.x;
+  const long long k = sL.node_off + (long long)e.y * sL.pitch + e.x;
   wall[k] = cgx;
   wall[node_total + k] = cgy;
   wall[2 * node_total + k] = nx;
   wall[3 * node_total + k] = ny;
 }
+
+// 16-byte asynchronous copy global -> shared (no register staging)
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(static_cast<unsigned>(__cvta_generic_to_shared(smem))),
+               "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+template <typename S>
+__global__ void __launch_bounds__(kWallThreads, sizeof(S) == 8 ? 3 : 5) k_wall(const LatDev* __restrict__ lats,
+                                                          const WallGroup* __restrict__ groups,
+                                                          const int* __restrict__ band,
+                                                          const WallSten* __restrict__ virt,
+                                                          const WallSten* __restrict__ sten,
+                                                          const OfbEntry* __restrict__ ofb, const S* __restrict__ src,
+                                                          typename Store<S>::T* __restrict__ wall, long long node_total) {
+  using T = typename Store<S>::T;
+  static_assert(sizeof(OfbEntry) % 16 == 0 && sizeof(WallSten) == 16, "16-byte table entries");
+  __shared__ T val[kWallCap];
+  __shared__ __align__(16) OfbEntry s_ofb[kWallMaxNodes];
+  __shared__ __align__(16) WallSten s_sten[kWallMaxNodes];
+  __shared__ __align__(16) WallSten s_virt[kWallVirtCap];
+  __shared__ __align__(16) int s_band[kWallCap];
+  __shared__ LatDev sL;
+  const WallGroup G = groups[blockIdx.x];
+  const int t = threadIdx.x;
+  // the group's tables, copied to shared memory in 16-byte pieces that are all in flight at
+  // once (band0 is a multiple of 4 and the band list is padded, so the last piece is in bounds)
+  {
+    constexpr int kO = int(sizeof(OfbEntry) / 16);
+    const int n1 = G.nwall * kO, n2 = n1 + G.nwall, n3 = n2 + G.nvirt, n4 = n3 + (G.nband + 3) / 4;
+    for (int c = t; c < n4; c += kWallThreads) {
+      const uint4* from;
+      uint4* to;
+      if (c < n1) {
+        from = reinterpret_cast<const uint4*>(ofb + G.wall0) + c;
+        to = reinterpret_cast<uint4*>(s_ofb) + c;
+      } else if (c < n2) {
+        from = reinterpret_cast<const uint4*>(sten + G.wall0) + (c - n1);
+        to = reinterpret_cast<uint4*>(s_sten) + (c - n1);
+      } else if (c < n3) {
+        from = reinterpret_cast<const uint4*>(virt + G.virt0) + (c - n2);
+        to = reinterpret_cast<uint4*>(s_virt) + (c - n2);
+      } else {
+        from = reinterpret_cast<const uint4*>(band + G.band0) + (c - n3);
+        to = reinterpret_cast<uint4*>(s_band) + (c - n3);
+      }
+      cp_async16(to, from);
+    }
+  }
+  if (t == 0) sL = lats[G.lat];
+  cp_async_wait_all();
+  __syncthreads();
+  // phase 1, UW band nodes at a time: their populations first, then the Zou-He columns and
+  // rho^N (indices past the end repeat the last node, so that no load sits behind a branch)
+  constexpr int UW = sizeof(S) == 8 ? 2 : 3;
+  const S* __restrict__ pop = src + sL.pop_off;
+  const T r0 = T(sL.rho0);
+  for (int i0 = t; i0 < G.nband; i0 += UW * kWallThreads) {
+    T fr[UW][9], fb[UW][9];
+    int off[UW];
+#pragma unroll
+    for (int v = 0; v < UW; ++v) off[v] = s_band[min(i0 + v * kWallThreads, G.nband - 1)];
+#pragma unroll
+    for (int v = 0; v < UW; ++v) load_raw<S>(pop + off[v], r0, fr[v], fb[v]);
+#pragma unroll
+    for (int v = 0; v < UW; ++v) {
+      const int i = i0 + v * kWallThreads;
+      if (i < G.nband) {
+        if (sL.bcx == BC_INOUT) {
+          // node of the population offset (the inverse of pop_node)
+          const int seg = off[v] / kSeg, segs = sL.pitch >> 5;
+          const int x = (seg % segs) * 32 + (off[v] % kSeg) / 2, y = seg / segs;
+          zou_he<T>(x, sL.nx, inlet_u<T>(sL, y), T(sL.rho_out), fr[v], fb[v]);
+        }
+        T rR, rB;
+        val[i] = colour_indicator(fr[v], fb[v], rR, rB);
+      }
+    }
+  }
+  __syncthreads();
+  for (int j = t; j < G.nvirt; j += kWallThreads) {
+    T v;
+    if (sL.wetting == 2) {
+      v = T(sL.cos_theta);   // surface-energy formulation: rho^N = cos(theta) on the solid
+    } else {
+      const WallSten q = s_virt[j];
+      T num = T(0), den = T(0);
+#pragma unroll
+      for (int b = 1; b < 9; ++b)
+        if (q.i[b - 1] != kWallNone) {
+          num = radd(num, rmul(wgt<T>(b), val[q.i[b - 1]]));
+          den = radd(den, wgt<T>(b));
+        }
+      v = rdiv(num, den);
+    }
+    val[G.nband + j] = v;
+  }
+  __syncthreads();
+  for (int w = t; w < G.nwall; w += kWallThreads) wall_node<T>(sL, s_ofb[w], s_sten[w], val, wall, node_total);
+}
+
 
 // Eq. 48, wetting scheme (b) (lbcg_params.wetting = 1): grad n at an outermost fluid node from
 // its fluid neighbours only, d_i n = sum_a w_a (n(x + e_a) - n(x)) e_ai / sum_a w_a e_ai^2 over
@@ -898,7 +960,7 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
   __syncthreads();
   const int nx = sL.nx, ny = sL.ny, pitch = sL.pitch;
   const bool px = sL.bcx == BC_PERIODIC, py = sL.bcy == BC_PERIODIC, inout = sL.bcx == BC_INOUT;
-  const T r0 = T(sL.rho0), u_in = T(sL.u_in), rho_out = T(sL.rho_out), eps2 = T(sL.grad_eps) * T(sL.grad_eps);
+  const T r0 = T(sL.rho0), rho_out = T(sL.rho_out), eps2 = T(sL.grad_eps) * T(sL.grad_eps);
   const T hsig = T(0.5) * T(sL.sigma), beta = T(sL.beta), se = T(sL.s_e), seps = T(sL.s_eps), sq = T(sL.s_q);
   const T kDe = T(-6) * (T(1) - T(0.5) * se), kDeps = T(6) * (T(1) - T(0.5) * seps), kq = T(1) - T(0.5) * sq;
   const T hdiff = T(sL.h_inv_nuR) - T(sL.h_inv_nuB), hsum = T(sL.h_inv_nuR) + T(sL.h_inv_nuB);
@@ -1270,14 +1332,6 @@ __global__ void k_from_storage(const LatDev* __restrict__ lats, int lat, const S
 }
 
 // ------------------------------------------------------------------ launchers
-// Block size of the 1-D list kernels: a short list (one small lattice) is split into small
-// blocks so that it spreads over the SMs instead of queueing on a few of them.
-inline int list_threads(int n) {
-  int t = 256;
-  while (t > 32 && (n + t - 1) / t < 2 * 152) t >>= 1;
-  return t;
-}
-
 template <typename S>
 static cudaError_t launch_all(const LaunchStep& p, cudaStream_t st) {
   using T = typename Store<S>::T;
@@ -1285,20 +1339,12 @@ static cudaError_t launch_all(const LaunchStep& p, cudaStream_t st) {
     if (p.ev) cudaEventRecord(p.ev[i], st);
   };
   rec(0);
-  if (p.nband > 0) {
-    const int t = list_threads(p.nband);
-    k_band<S><<<(p.nband + t - 1) / t, t, 0, st>>>(p.lats, p.band, p.nband, static_cast<const S*>(p.src),
-                                                   static_cast<T*>(p.band_rn));
-  }
+  if (p.ngroups > 0)
+    k_wall<S><<<p.ngroups, kWallThreads, 0, st>>>(p.lats, p.groups, p.wband, p.wvirt, p.wsten, p.ofb,
+                                                  static_cast<const S*>(p.src), static_cast<T*>(p.wall),
+                                                  p.node_total);
   rec(1);
   rec(2);
-  if (p.nofb > 0) {
-    const int t = list_threads(p.nofb);
-    k_wall<T><<<(p.nofb + t - 1) / t, t, 0, st>>>(p.lats, p.ofb, p.nofb, p.flags, static_cast<const T*>(p.band_rn),
-                                                  static_cast<T*>(p.wall), p.node_total);
-  }
-  rec(3);
-  rec(4);
   if (p.sweep && p.macro == nullptr) {
     if (p.nstrips > 0) {
       SweepArgs B{p.lats, p.strips, p.src, p.dst, p.flags, p.nbmask, p.wall, p.node_total, p.err};
@@ -1310,7 +1356,7 @@ static cudaError_t launch_all(const LaunchStep& p, cudaStream_t st) {
       else k_sweep<S, kSweepThreads><<<p.nstrips, kSweepThreads, 0, st>>>(B);
     }
   } else if (p.ntiles > 0) {
-    StepArgs A{p.lats, p.tiles, p.src, p.dst, p.flags, p.band_rn, p.wall, p.node_total, p.macro};
+    StepArgs A{p.lats, p.tiles, p.src, p.dst, p.flags, p.wall, p.node_total, p.macro};
     const bool macro = p.macro != nullptr;
     switch (p.ty) {
       case 4:
@@ -1327,7 +1373,7 @@ static cudaError_t launch_all(const LaunchStep& p, cudaStream_t st) {
         break;
     }
   }
-  rec(5);
+  rec(3);
   return cudaGetLastError();
 }
 

@@ -254,8 +254,8 @@ def lbcg_profile(h: int, enable: bool):
 
 
 def lbcg_kernel_times(h: int):
-    """(ms of k_band, k_wall, k_step summed, number of profiled steps)."""
-    ms = (C.c_double * 3)()
+    """(ms of the wall kernel and the step kernel summed, number of profiled steps)."""
+    ms = (C.c_double * 2)()
     n = C.c_int64()
     _check(library().lbcg_kernel_times(h, ms, C.byref(n)))
     return list(ms), n.value
