@@ -913,9 +913,9 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int* e
   atomicOr(err, 1);
   return false;
 }
-// segments of a staged row: up to 5 contiguous ones for the strip's columns, plus one for the
-// columns a periodic strip wraps to
-constexpr int kStageSegs = 6;
+// segments of a staged row: the (at most 5) contiguous ones holding the strip's columns; the
+// columns a periodic strip wraps to are loaded directly
+constexpr int kStageSegs = 5;
 template <typename S>
 constexpr int sweepf_dyn_smem() { return 2 * kStageSegs * kSeg * int(sizeof(S)); }
 
@@ -936,12 +936,12 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
   using T = float;
   constexpr int RR = 5;   // rho^N / flags ring (rows r-4 .. r)
   constexpr int RN = 3;   // n, grad ring (rows r-3 .. r-1)
-  constexpr int RF = 3;   // f totals / (rho_R, rho_B) ring (rows r-2 .. r)
+  constexpr int RF = 2;   // f totals / (rho_R, rho_B) ring (rows r-2, r-1; row r is written last)
   using P = Pair<T>;
   using V = typename P::V;
   __shared__ T srn[RR][NTH];
   __shared__ uint8_t sfl[RR][NTH];
-  __shared__ V sn[RN][NTH], sg[RN][NTH];
+  __shared__ V sn[RN][NTH];
   __shared__ T sf[RF][9][NTH];
   __shared__ V srb[RF][NTH];
   __shared__ LatDev sL;
@@ -980,22 +980,17 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
   const int colk[3] = {(xl >> 5) * kSeg + (xl & 31) * 2, (xm >> 5) * kSeg + (xm & 31) * 2,
                        (xr >> 5) * kSeg + (xr & 31) * 2};
   const int rowseg = (pitch >> 5) * kSeg;
-  // staged segments of this strip: [sA, sB] holds columns max(x0-2, 0) .. min(x0+125, nx-1);
-  // sX (or -1) the segment a periodic edge strip wraps to.  soff: this column's offset in a
-  // staged row, -1 if its segment is not staged (it is then loaded directly).
+  // staged segments of this strip: [sA, sB] holds columns max(x0-2, 0) .. min(x0+125, nx-1).
+  // soff: this column's offset in a staged row, -1 if its segment is not staged (a column a
+  // periodic edge strip wraps to; it is then loaded directly).
   const int sA = max(sp.y - 2, 0) >> 5, sB = min(sp.y + NTH - 3, nx - 1) >> 5;
-  int sX = -1;
-  if (px && sp.y - 2 < 0 && ((nx - 1) >> 5) > sB) sX = (nx - 1) >> 5;
-  else if (px && sp.y + NTH - 3 >= nx && sA > 0) sX = 0;
-  const int soff = ((xm >> 5) >= sA && (xm >> 5) <= sB) ? ((xm >> 5) - sA) * kSeg + (xm & 31) * 2
-                   : ((xm >> 5) == sX ? (kStageSegs - 1) * kSeg + (xm & 31) * 2 : -1);
+  const int soff = ((xm >> 5) >= sA && (xm >> 5) <= sB) ? ((xm >> 5) - sA) * kSeg + (xm & 31) * 2 : -1;
   const unsigned bytesA = unsigned((sB - sA + 1) * kSeg * sizeof(S));
   // flag / mask bytes of the strip's columns, from a 16-byte boundary, a multiple of 16 long
   // (the 32-aligned pitch keeps it inside the row); fo: this column's byte, -1 if outside
   const int fx0 = max(sp.y - 2, 0) & ~15;
   const unsigned fbytes = unsigned((min(sp.y + NTH - 3, nx - 1) - fx0 + 16) & ~15);
   const int fo = (xm >= fx0 && xm < fx0 + int(fbytes)) ? xm - fx0 : -1;
-  const unsigned bytesX = sX >= 0 ? unsigned(kSeg * sizeof(S)) : 0u;
 
   auto map_row = [&](int v) {
     if (py) {
@@ -1009,17 +1004,22 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
   int ym3 = 0, ym2 = 0, ym1 = 0, ym0 = 0;
   int s4 = 0, s3 = 1, s2 = 2, s1 = 3, s0 = 4;
   int n2 = 0, n1 = 1, n0 = 2;
-  int q2 = 0, q1 = 1, q0 = 2;
+  int q2 = 0, q1 = 1;   // f-total slots of rows r-2 and r-1
+  // thread-private values carried between rows in registers: the f totals and (rho_R, rho_B)
+  // of row r until they take the slot of row r-2 at the end of the iteration, and the colour
+  // gradient (stage 2, row r-1) until the collision of that row one iteration later
+  T ft[9];
+  V rbt = P::mk(T(0), T(0)), g_new = P::mk(T(0), T(0)), g_old = P::mk(T(0), T(0));
+  bool ft_ok = false;
   // issue the bulk copies of (mapped) row y into staging slot `slot` (one thread)
   auto stage_row = [&](int y, int slot) {
     S* d = sraw + slot * (kStageSegs * kSeg);
     const S* g = src + (long long)y * rowseg;
     fence_proxy_async();
-    mbar_expect_tx(&sbar[slot], bytesA + bytesX + 2 * fbytes);
+    mbar_expect_tx(&sbar[slot], bytesA + 2 * fbytes);
     bulk_copy_g2s(d, g + sA * kSeg, bytesA, &sbar[slot]);
     bulk_copy_g2s(&sfg[slot][0][0], fl + (long long)y * pitch + fx0, fbytes, &sbar[slot]);
     bulk_copy_g2s(&sfg[slot][1][0], nbm + (long long)y * pitch + fx0, fbytes, &sbar[slot]);
-    if (sX >= 0) bulk_copy_g2s(d + (kStageSegs - 1) * kSeg, g + sX * kSeg, bytesX, &sbar[slot]);
   };
   unsigned phase = 0;   // bit s: parity of the next completion of slot s
   bool lost = false;    // a wait ran out: copies may still be in flight at the end
@@ -1041,8 +1041,8 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
       s0 = t4;
       const int tq = q2;
       q2 = q1;
-      q1 = q0;
-      q0 = tq;
+      q1 = tq;
+      g_old = g_new;
       if (r == ys - 2) {
         ym3 = map_row(r - 3);
         ym2 = map_row(r - 2);
@@ -1089,12 +1089,13 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
 #pragma unroll
         for (int a = 2; a < 9; ++a) srb_ = P::add(srb_, P::mk(fr[a], fb[a]));
 #pragma unroll
-        for (int a = 0; a < 9; ++a) sf[q0][a][t] = fr[a] + fb[a];
-        srb[q0][t] = srb_;
+        for (int a = 0; a < 9; ++a) ft[a] = fr[a] + fb[a];
+        rbt = srb_;
         const T sr = srb_.x, sb = srb_.y;
         const T w = (sr - sb) * rcp_(sr + sb);
         v = sb == T(0) ? T(1) : (sr == T(0) ? T(-1) : w);
       }
+      ft_ok = !(f_r & F_SOLID);
       srn[s0][t] = v;
       sfl[s0][t] = f_r;
     }
@@ -1155,11 +1156,11 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
         }
       }
       sn[n0][t] = P::mk(nxv, nyv);
-      sg[n0][t] = P::mk(ax, ay);
+      g_new = P::mk(ax, ay);
     }
     __syncthreads();
-    // ---- stage 3: collide and push row p = r - 2
-    if (!collide) return;
+    // ---- stage 3: collide and push row p = r - 2; then row r's totals take row p's slot
+    if (collide) {
     const uint8_t myf = sfl[s2][t];
     T f[9];
 #pragma unroll
@@ -1192,7 +1193,7 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
     const T nxo = n0_c.x, nyo = n0_c.y;
     const T kappa = T(3) * (-nxo * nxo * dY.y - nyo * nyo * dX.x + nxo * nyo * (dY.x + dX.y));
     const T hsk = hsig * kappa;
-    const V gv = sg[n1][t];
+    const V gv = g_old;
     const T Fx = hsk * gv.x, Fy = hsk * gv.y;
     // moments (Eq. 3) from shared partial sums
     const T p13 = f[1] + f[3], m13 = f[1] - f[3], p24 = f[2] + f[4], m24 = f[2] - f[4];
@@ -1275,6 +1276,12 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
         }
         store_pair<S>(dst + k, oR, fp[a] - oR, wgt<T>(a) * r0);
       }
+    }
+    }
+    if (ft_ok) {
+#pragma unroll
+      for (int a = 0; a < 9; ++a) sf[q2][a][t] = ft[a];
+      srb[q2][t] = rbt;
     }
   };
 
