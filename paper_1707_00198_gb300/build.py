@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblbcg.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ("lbcg_host.cu", "lbcg_kernels.cu", "lbcg_obs.cu", "lbcg_noalloc.cu", "lbcg_adjoint.cu")
+SOURCES = ("lbcg_host.cu", "lbcg_kernels.cu", "lbcg_obs.cu", "lbcg_noalloc.cu", "lbcg_adjoint.cu", "lbcg_geom.cpp")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
@@ -48,7 +48,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     os.makedirs(BUILD, exist_ok=True)
 
     def compile_one(src):
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+        obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
         cmd = [nvcc, *_flags(extra_flags), "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:

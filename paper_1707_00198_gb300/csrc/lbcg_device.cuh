@@ -15,8 +15,8 @@
 //                 neighbours (half-way bounce-back: back into the node's own opposite slot;
 //                 across an open edge: dropped).
 //   node arrays : [y][pitch] per lattice: flags (uint8), the solid-neighbour mask (uint8),
-//                 and in the compute type T the rho^N of the wall band and the corrected
-//                 gradient / normal of the outermost fluid nodes.
+//                 and in the compute type T the corrected gradient / normal of the outermost
+//                 fluid nodes.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -26,16 +26,9 @@
 
 #include <cstring>
 
-namespace lbcg {
+#include "lbcg_geom.h"
 
-// node flags
-enum : uint8_t {
-  F_SOLID = 1,    // solid node (indicator s = 1 of Eq. 32)
-  F_OFB = 2,      // outermost fluid node (fluid with a solid D2Q9 neighbour), Omega_Fb
-  F_OSOLID = 4,   // outermost solid node (solid with a fluid D2Q9 neighbour), Eq. 29
-  F_NEAR = 8,     // within Chebyshev distance 3 of a solid node (excluded from the fit)
-  F_EDGE = 16,    // fluid node in an open (inlet/outlet) column: some pushes leave the lattice
-};
+namespace lbcg {
 
 enum { BC_PERIODIC = 0, BC_CLOSED = 1, BC_INOUT = 2 };
 
@@ -69,32 +62,6 @@ __device__ __forceinline__ T inlet_u(const LatDev& L, int y) {
   return T(4.0 * L.u_in * s * (1.0 - s));
 }
 
-// Entry of the outermost-fluid list: node, its solid normal and contact angle.
-struct OfbEntry {
-  int lat, x, y, pad_;
-  double nsx, nsy, cos_t, sin_t;
-};
-
-// Work unit of the wall kernel (one block): consecutive outermost-fluid entries [wall0,
-// wall0 + nwall) of lattice `lat`, the fluid nodes [band0, band0 + nband) of the band list
-// (each as the offset of its populations in the lattice's pool, pop_node) whose rho^N they need, and the outermost solid nodes [virt0, virt0 + nvirt) of the virtual
-// list next to them (Eq. 29).  The kernel keeps rho^N of the band nodes in shared memory at
-// local indices 0 .. nband-1 and the virtual values at nband .. nband+nvirt-1.
-struct WallGroup {
-  int lat, wall0, nwall, band0, nband, virt0, nvirt, pad_;
-};
-// Local indices into that shared array, one per direction a = 1..8 (element a-1): for an
-// outermost fluid node, the value at x + e_a (band node or virtual solid node); for a virtual
-// node, the band node at x + e_a, or kWallNone if that neighbour is solid.
-struct WallSten {
-  uint16_t i[8];
-};
-constexpr uint16_t kWallNone = 0xFFFF;
-constexpr int kWallThreads = 128;   // block size
-constexpr int kWallMaxNodes = 256;  // outermost fluid nodes per group, at most
-constexpr int kWallCap = 1024;      // shared values per group (band + virtual), at most
-constexpr int kWallVirtCap = 512;   // virtual nodes per group, at most
-
 // D2Q9 velocity set (Sec. II.A), as constant-folding functions of the direction index.
 __host__ __device__ constexpr int ex(int a) {
   return (a == 1 || a == 5 || a == 8) ? 1 : ((a == 3 || a == 6 || a == 7) ? -1 : 0);
@@ -108,14 +75,6 @@ __host__ __device__ constexpr int opp(int a) {
 template <typename T>
 __host__ __device__ constexpr T wgt(int a) {
   return a == 0 ? T(4.0 / 9.0) : (a <= 4 ? T(1.0 / 9.0) : T(1.0 / 36.0));
-}
-
-// Element offset of the direction-0 pair of node (x, y) within its lattice's population block
-// (pitch is a multiple of 32); the pair of direction a is kDir * a further.
-constexpr int kDir = 64;          // elements between the pairs of consecutive directions
-constexpr int kSeg = 9 * kDir;    // elements of a 32-node row segment
-__host__ __device__ __forceinline__ int pop_node(int x, int y, int pitch) {
-  return (y * (pitch >> 5) + (x >> 5)) * kSeg + (x & 31) * 2;
 }
 
 // ------------------------------------------------------------------ storage traits
