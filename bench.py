@@ -163,7 +163,7 @@ def measured_peaks():
 
 def kernel_source_digest() -> str:
     h = hashlib.sha256()
-    for f in ("lbcg_kernels.cu", "lbcg_device.cuh"):
+    for f in ("lbcg_kernels.cu", "lbcg_device.cuh", "lbcg_geom.h"):
         h.update(open(os.path.join(ROOT, "paper_1707_00198_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
