@@ -55,7 +55,12 @@ typedef enum {
  *   LBCG_FP64: populations f_R, f_B stored and computed in double.
  *   LBCG_FP32: populations f_R, f_B stored and computed in float.
  *   LBCG_FP16_STORE / LBCG_BF16_STORE: 16-bit storage of d = f_R + f_B - w_a rho0 (deviation
- *     from the rest state) and g = f_R - f_B, all arithmetic in float. */
+ *     from the rest state) and g = f_R - f_B, all arithmetic in float.  FP16 stores 1024 d and
+ *     1024 g (an exact power of two that keeps small deviations out of FP16's subnormal range).
+ *     A step stores them with stochastic rounding (up or down with the probability of the
+ *     distance, keyed by a hash of the stored slot and the step), so that changes smaller than
+ *     half a unit in the last place accumulate instead of being rounded away; the initial
+ *     state and lbcg_set_populations round to nearest. */
 typedef enum { LBCG_FP64 = 0, LBCG_FP32 = 1, LBCG_FP16_STORE = 2, LBCG_BF16_STORE = 3 } lbcg_precision;
 
 /* x boundaries: periodic; closed (columns 0 and nx-1 must be solid); or a Zou-He velocity

@@ -101,9 +101,40 @@ template <> struct Store<float> {
   }
   __device__ static void stp(float* p, float lo, float hi) { *reinterpret_cast<float2*>(p) = make_float2(lo, hi); }
 };
+// ------------------------------------------------------------------ stochastic rounding
+// The 16-bit forms round each stored value up or down at random with the probability of its
+// distance to the two neighbouring representable values, so that the stored value is exact in
+// expectation: per-step changes of a population smaller than half a unit in the last place
+// then accumulate instead of being rounded away every step (round-to-nearest stagnation).
+// The random bits come from a counter-based hash of (stored slot, step); the hash is
+// C. Wellons' "lowbias32" integer hash.
+__host__ __device__ __forceinline__ uint32_t hash32(uint32_t x) {
+  x ^= x >> 16;
+  x *= 0x7feb352dU;
+  x ^= x >> 15;
+  x *= 0x846ca68bU;
+  x ^= x >> 16;
+  return x;
+}
+// two floats to packed FP16 rounded toward zero (lo in the low half)
+__device__ __forceinline__ uint32_t cvt_rz_f16x2(float lo, float hi) {
+  uint32_t d;
+  asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+// key of one step of one lattice: epoch counts graph replays (device counter), step the
+// launch within them (or the absolute step of a direct launch)
+__device__ __forceinline__ uint32_t sr_key(const uint32_t* epoch, uint32_t step, long long pop_off) {
+  return hash32(hash32(*epoch ^ 0x9E3779B9u) + step) + uint32_t(pop_off);
+}
+
+// FP16 keeps d and g scaled by 2^10: an exact power of two that leaves the rounding of
+// normal values unchanged and moves FP16's subnormal range (below 2^-14) down to deviations
+// under 2^-24, so that small deviations keep their relative precision.
 template <> struct Store<__half> {
   using T = float;
   static constexpr bool kDeviation = true;
+  static constexpr float kScale = 1024.0f;
   __device__ static void ldp(const __half* p, float& lo, float& hi) {
     const float2 v = __half22float2(__ldg(reinterpret_cast<const __half2*>(p)));
     lo = v.x;
@@ -111,6 +142,13 @@ template <> struct Store<__half> {
   }
   __device__ static void stp(__half* p, float lo, float hi) {
     *reinterpret_cast<__half2*>(p) = __floats2half2_rn(lo, hi);
+  }
+  // stochastic rounding: 13 random bits added below the kept bits of each FP32 pattern (FP16
+  // keeps 10 of its 23 mantissa bits), then truncation; exact for the FP16 normal range
+  __device__ static void stp_sr(__half* p, float lo, float hi, uint32_t r) {
+    const float a = __uint_as_float(__float_as_uint(lo) + (r & 0x1FFFu));
+    const float b = __uint_as_float(__float_as_uint(hi) + ((r >> 16) & 0x1FFFu));
+    *reinterpret_cast<uint32_t*>(p) = cvt_rz_f16x2(a, b);
   }
   __device__ static void unpack(uint32_t w, float& lo, float& hi) {
     __half2 h;
@@ -123,6 +161,7 @@ template <> struct Store<__half> {
 template <> struct Store<__nv_bfloat16> {
   using T = float;
   static constexpr bool kDeviation = true;
+  static constexpr float kScale = 1.0f;
   __device__ static void ldp(const __nv_bfloat16* p, float& lo, float& hi) {
     const float2 v = __bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162*>(p)));
     lo = v.x;
@@ -130,6 +169,13 @@ template <> struct Store<__nv_bfloat16> {
   }
   __device__ static void stp(__nv_bfloat16* p, float lo, float hi) {
     *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(lo, hi);
+  }
+  // stochastic rounding: 16 random bits added below the kept 16 bits of each FP32 pattern,
+  // then truncation (the magnitude rounds up with the probability of the dropped fraction)
+  __device__ static void stp_sr(__nv_bfloat16* p, float lo, float hi, uint32_t r) {
+    const uint32_t a = __float_as_uint(lo) + (r & 0xFFFFu);
+    const uint32_t b = __float_as_uint(hi) + (r >> 16);
+    *reinterpret_cast<uint32_t*>(p) = __byte_perm(a, b, 0x7632);
   }
   __device__ static void unpack(uint32_t w, float& lo, float& hi) {
     __nv_bfloat162 h;
@@ -144,9 +190,11 @@ template <> struct Store<__nv_bfloat16> {
 template <typename S, typename T>
 __device__ __forceinline__ void decode(T lo, T hi, T wr0, T& fr, T& fb) {
   if constexpr (Store<S>::kDeviation) {
-    const T f = wr0 + lo;
-    fr = T(0.5) * (f + hi);
-    fb = T(0.5) * (f - hi);
+    constexpr float inv = 1.0f / Store<S>::kScale, hinv = 0.5f / Store<S>::kScale;
+    const T f = fmaf(lo, inv, wr0);
+    const T hf = T(0.5) * f;
+    fr = fmaf(hi, hinv, hf);
+    fb = fmaf(-hi, hinv, hf);
   } else {
     fr = lo;
     fb = hi;
@@ -155,8 +203,8 @@ __device__ __forceinline__ void decode(T lo, T hi, T wr0, T& fr, T& fb) {
 template <typename S, typename T>
 __device__ __forceinline__ void encode(T fr, T fb, T wr0, T& lo, T& hi) {
   if constexpr (Store<S>::kDeviation) {
-    lo = (fr + fb) - wr0;
-    hi = fr - fb;
+    lo = ((fr + fb) - wr0) * Store<S>::kScale;
+    hi = (fr - fb) * Store<S>::kScale;
   } else {
     lo = fr;
     hi = fb;
@@ -261,6 +309,20 @@ __device__ __forceinline__ void store_pair(S* p, typename Store<S>::T fr, typena
   T lo, hi;
   encode<S, T>(fr, fb, wr0, lo, hi);
   Store<S>::stp(p, lo, hi);
+}
+
+// store_pair at base + off, with stochastic rounding for 16-bit storage (key: sr_key)
+template <typename S>
+__device__ __forceinline__ void store_pair_sr(S* base, int off, typename Store<S>::T fr, typename Store<S>::T fb,
+                                              typename Store<S>::T wr0, uint32_t key) {
+  using T = typename Store<S>::T;
+  if constexpr (Store<S>::kDeviation) {
+    T lo, hi;
+    encode<S, T>(fr, fb, wr0, lo, hi);
+    Store<S>::stp_sr(base + off, lo, hi, hash32(uint32_t(off) + key));
+  } else {
+    store_pair<S>(base + off, fr, fb, wr0);
+  }
 }
 
 // A node's nine stored pairs as loaded, before decoding: for 16-bit storage each pair is one

@@ -70,6 +70,7 @@ struct lbcg_handle {
   uint8_t* d_nbmask = nullptr;
   int scheme_b = 0;        // some lattice uses wetting scheme (b)
   int* d_err = nullptr;    // device error word (a sweep block's bounded wait ran out)
+  uint32_t* d_sr_epoch = nullptr;     // 16-bit storage: graph replays so far (stochastic-rounding keys)
   double* d_usnap = nullptr;          // velocity stored by lbcg_diagnostics ([2][node_total])
   std::vector<int64_t> snap_step;     // per lattice: step of that velocity, -1 = none
   void* d_wall = nullptr;
@@ -222,6 +223,8 @@ LaunchStep make_launch(lbcg_handle* h, int src, double* macro, int tile_begin, i
   p.flags = h->d_flags;
   p.nbmask = h->d_nbmask;
   p.err = h->d_err;
+  p.sr_epoch = h->d_sr_epoch;
+  p.sr_step = uint32_t(h->step);
   p.scheme_b = h->scheme_b;
   p.wall = h->d_wall;
   p.node_total = h->node_total;
@@ -238,7 +241,7 @@ void free_handle(lbcg_handle* h) {
   for (cudaEvent_t e : h->events) cudaEventDestroy(e);
   void* ptrs[] = {h->pool[0], h->pool[1], h->d_flags,  h->d_wall,  h->d_macro, h->d_lats,
                   h->d_tiles, h->d_groups, h->d_wband, h->d_wvirt, h->d_wsten, h->d_ofb,
-                  h->d_obs,   h->d_strips, h->d_nbmask, h->d_err, h->d_usnap};
+                  h->d_obs,   h->d_strips, h->d_nbmask, h->d_err, h->d_usnap, h->d_sr_epoch};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -421,7 +424,7 @@ lbcg_status lbcg_create_batch(int32_t n, const lbcg_geometry* geoms, const lbcg_
   auto alloc = [&](void** p, size_t bytes) { return cudaMalloc(p, std::max<size_t>(bytes, 16)) == cudaSuccess; };
   bool ok = alloc(&h->pool[0], 18 * (size_t)node_total * es) && alloc(&h->pool[1], 18 * (size_t)node_total * es) &&
             alloc((void**)&h->d_flags, (size_t)node_total) && alloc((void**)&h->d_nbmask, (size_t)node_total) &&
-            alloc((void**)&h->d_err, sizeof(int)) &&
+            alloc((void**)&h->d_err, sizeof(int)) && alloc((void**)&h->d_sr_epoch, sizeof(uint32_t)) &&
             alloc(&h->d_wall, 4 * (size_t)node_total * cs) && alloc((void**)&h->d_lats, n * sizeof(LatDev)) &&
             alloc((void**)&h->d_groups, groups.size() * sizeof(WallGroup)) &&
             alloc((void**)&h->d_wband, wband.size() * sizeof(int)) &&
@@ -445,6 +448,7 @@ lbcg_status lbcg_create_batch(int32_t n, const lbcg_geometry* geoms, const lbcg_
   CKC(cudaMemcpy(h->d_flags, h->flags_host.data(), (size_t)node_total, cudaMemcpyHostToDevice));
   CKC(cudaMemcpy(h->d_nbmask, mask_host.data(), (size_t)node_total, cudaMemcpyHostToDevice));
   CKC(cudaMemset(h->d_err, 0, sizeof(int)));
+  CKC(cudaMemset(h->d_sr_epoch, 0, sizeof(uint32_t)));
   CKC(prepare_kernels(precision));
 
   CKC(cudaMemcpy(h->d_lats, ld.data(), n * sizeof(LatDev), cudaMemcpyHostToDevice));
@@ -534,8 +538,14 @@ lbcg_status lbcg_step(lbcg_handle* h, int64_t nsteps) {
         cudaGraph_t g = nullptr;
         CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
         cudaError_t le = cudaSuccess;
-        for (int k = 0; k < kGraphSteps && le == cudaSuccess; ++k)
-          le = launch_step(h->prec, make_launch(h, k & 1, nullptr, 0, h->ntiles), h->stream);
+        // 16-bit storage: each replay advances the counter that keys the stochastic rounding,
+        // and the 32 captured steps carry their index within the replay
+        if (h->prec >= 2) le = launch_sr_tick(h->d_sr_epoch, h->stream);
+        for (int k = 0; k < kGraphSteps && le == cudaSuccess; ++k) {
+          LaunchStep q = make_launch(h, k & 1, nullptr, 0, h->ntiles);
+          q.sr_step = uint32_t(k);
+          le = launch_step(h->prec, q, h->stream);
+        }
         cudaError_t ee = cudaStreamEndCapture(h->stream, &g);
         if (le != cudaSuccess) return cuda_fail(h, le, "launch during capture");
         if (ee != cudaSuccess) return cuda_fail(h, ee, "cudaStreamEndCapture");

@@ -34,9 +34,13 @@ struct LaunchStep {
   double* macro;          // non-null: write macroscopic fields instead of stepping (tiles)
   cudaEvent_t* ev;        // non-null: 4 events recorded around k_wall and the step kernel
   int* err;               // device error word: a sweep block's bounded wait ran out
+  const uint32_t* sr_epoch;   // 16-bit storage: stochastic-rounding replay counter (device)
+  uint32_t sr_step;           // and the step within the replay / the absolute step
 };
 
 cudaError_t launch_step(int prec, const LaunchStep& p, cudaStream_t st);
+// Advances the stochastic-rounding replay counter (one single-thread launch).
+cudaError_t launch_sr_tick(uint32_t* epoch, cudaStream_t st);
 // One-time kernel attributes for a precision (the sweep's dynamic shared memory); called
 // before any launch or graph capture of that precision.
 cudaError_t prepare_kernels(int prec);

@@ -28,6 +28,8 @@ struct StepArgs {
   void* wall;             // 4 planes of node arrays: g_x, g_y, n_x, n_y (compute type)
   long long node_total;   // elements per node-array plane
   double* macro;          // 4 planes of doubles: rho_R, rho_B, u_x, u_y (macro mode)
+  const uint32_t* sr_epoch;   // stochastic rounding of 16-bit stores: replay counter
+  uint32_t sr_step;           // and the step within the replay (sr_key)
 };
 
 // ------------------------------------------------------------------ k_wall
@@ -508,6 +510,8 @@ __global__ void __launch_bounds__(32 * TY, sizeof(typename Store<S>::T) == 4 ? 1
     const T cR = rhoR * irho, cB = rhoB * irho;
     const T pc = T(sL.beta) * rhoR * rhoB * irho;
     S* __restrict__ dst = static_cast<S*>(A.dst) + sL.pop_off;
+    uint32_t srk = 0;
+    if constexpr (Store<S>::kDeviation) srk = sr_key(A.sr_epoch, A.sr_step, sL.pop_off);
     const int c3x = lx + 3, c3y = ly + 3;
     const int pn_own = pop_node(xs, ys, pitch);
 #pragma unroll
@@ -528,7 +532,7 @@ __global__ void __launch_bounds__(32 * TY, sizeof(typename Store<S>::T) == 4 ? 1
           k = pop_node(sxm[c3x + ex(a)], sym[c3y + ey(a)], pitch);
         }
       }
-      store_pair<S>(dst + k + slot * kDir, oR, oB, wgt<T>(a) * r0);
+      store_pair_sr<S>(dst, k + slot * kDir, oR, oB, wgt<T>(a) * r0, srk);
     }
   }
 }
@@ -572,6 +576,8 @@ struct SweepArgs {
   const void* wall;
   long long node_total;
   int* err;               // set to 1 by a block whose wait for a staged row ran out (k_sweepf)
+  const uint32_t* sr_epoch;   // stochastic rounding of 16-bit stores (sr_key)
+  uint32_t sr_step;
 };
 
 template <typename S, int NTH>
@@ -968,6 +974,8 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
   const uint8_t* __restrict__ nbm = A.nbmask + sL.node_off;
   const S* __restrict__ src = static_cast<const S*>(A.src) + sL.pop_off;
   S* __restrict__ dst = static_cast<S*>(A.dst) + sL.pop_off;
+  uint32_t srk = 0;
+  if constexpr (Store<S>::kDeviation) srk = sr_key(A.sr_epoch, A.sr_step, sL.pop_off);
 
   const int cx = sp.y - 2 + t;
   const int xm = wrap_or_clamp(cx, nx, px);
@@ -1260,7 +1268,7 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
 #pragma unroll
       for (int a = 0; a < 9; ++a) {
         const T oR = fmaf(cR, fp[a], pert[a]);
-        store_pair<S>(dst + rowk[ey(a) + 1] + colk[ex(a) + 1] + a * kDir, oR, fp[a] - oR, wgt<T>(a) * r0);
+        store_pair_sr<S>(dst, rowk[ey(a) + 1] + colk[ex(a) + 1] + a * kDir, oR, fp[a] - oR, wgt<T>(a) * r0, srk);
       }
     } else {
       const bool okx[3] = {px || cx - 1 >= 0, true, px || cx + 1 < nx};
@@ -1274,7 +1282,7 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
           if (mask & (1u << (a - 1))) k = kn + opp(a) * kDir;
           else k = rowk[ey(a) + 1] + colk[ex(a) + 1] + a * kDir;
         }
-        store_pair<S>(dst + k, oR, fp[a] - oR, wgt<T>(a) * r0);
+        store_pair_sr<S>(dst, k, oR, fp[a] - oR, wgt<T>(a) * r0, srk);
       }
     }
     }
@@ -1339,6 +1347,9 @@ __global__ void k_from_storage(const LatDev* __restrict__ lats, int lat, const S
 }
 
 // ------------------------------------------------------------------ launchers
+// advances the replay counter of the stochastic-rounding keys (once per replayed graph)
+__global__ void k_sr_tick(uint32_t* epoch) { *epoch += 1u; }
+
 template <typename S>
 static cudaError_t launch_all(const LaunchStep& p, cudaStream_t st) {
   using T = typename Store<S>::T;
@@ -1354,7 +1365,8 @@ static cudaError_t launch_all(const LaunchStep& p, cudaStream_t st) {
   rec(2);
   if (p.sweep && p.macro == nullptr) {
     if (p.nstrips > 0) {
-      SweepArgs B{p.lats, p.strips, p.src, p.dst, p.flags, p.nbmask, p.wall, p.node_total, p.err};
+      SweepArgs B{p.lats, p.strips, p.src, p.dst, p.flags, p.nbmask, p.wall, p.node_total, p.err, p.sr_epoch,
+                  p.sr_step};
       if constexpr (sizeof(T) == 4)
       {
         if (p.scheme_b) k_sweepf<S, kSweepThreads, true><<<p.nstrips, kSweepThreads, sweepf_dyn_smem<S>(), st>>>(B);
@@ -1363,7 +1375,7 @@ static cudaError_t launch_all(const LaunchStep& p, cudaStream_t st) {
       else k_sweep<S, kSweepThreads><<<p.nstrips, kSweepThreads, 0, st>>>(B);
     }
   } else if (p.ntiles > 0) {
-    StepArgs A{p.lats, p.tiles, p.src, p.dst, p.flags, p.wall, p.node_total, p.macro};
+    StepArgs A{p.lats, p.tiles, p.src, p.dst, p.flags, p.wall, p.node_total, p.macro, p.sr_epoch, p.sr_step};
     const bool macro = p.macro != nullptr;
     switch (p.ty) {
       case 4:
@@ -1411,6 +1423,11 @@ cudaError_t launch_step(int prec, const LaunchStep& p, cudaStream_t st) {
     case 3: return launch_all<__nv_bfloat16>(p, st);
   }
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_sr_tick(uint32_t* epoch, cudaStream_t st) {
+  k_sr_tick<<<1, 1, 0, st>>>(epoch);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_to_storage(int prec, const LatDev* lats, int lat, long long nn, const double* in,
