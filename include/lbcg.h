@@ -58,7 +58,7 @@ typedef enum {
  *     from the rest state) and g = f_R - f_B, all arithmetic in float.  FP16 stores 1024 d and
  *     1024 g (an exact power of two that keeps small deviations out of FP16's subnormal range).
  *     A step stores them with stochastic rounding (up or down with the probability of the
- *     distance, keyed by a hash of the stored slot and the step), so that changes smaller than
+ *     distance, keyed by a hash of the node and the step), so that changes smaller than
  *     half a unit in the last place accumulate instead of being rounded away; the initial
  *     state and lbcg_set_populations round to nearest. */
 typedef enum { LBCG_FP64 = 0, LBCG_FP32 = 1, LBCG_FP16_STORE = 2, LBCG_BF16_STORE = 3 } lbcg_precision;

@@ -106,7 +106,7 @@ template <> struct Store<float> {
 // distance to the two neighbouring representable values, so that the stored value is exact in
 // expectation: per-step changes of a population smaller than half a unit in the last place
 // then accumulate instead of being rounded away every step (round-to-nearest stagnation).
-// The random bits come from a counter-based hash of (stored slot, step); the hash is
+// The random bits come from a counter-based hash of (node, step); the hash is
 // C. Wellons' "lowbias32" integer hash.
 __host__ __device__ __forceinline__ uint32_t hash32(uint32_t x) {
   x ^= x >> 16;
@@ -311,17 +311,23 @@ __device__ __forceinline__ void store_pair(S* p, typename Store<S>::T fr, typena
   Store<S>::stp(p, lo, hi);
 }
 
-// store_pair at base + off, with stochastic rounding for 16-bit storage (key: sr_key)
+// Random word of a node for one step (16-bit storage; key: sr_key, node: its own population
+// offset); direction a of the node uses it rotated by 7a bits (sr_bits).  The directions of a
+// node share the word: that correlates their roundings but leaves each one unbiased.
+__device__ __forceinline__ uint32_t sr_node(uint32_t key, int node) { return hash32(uint32_t(node) + key); }
+__device__ __forceinline__ uint32_t sr_bits(uint32_t h, int a) { return __funnelshift_l(h, h, 7 * a); }
+
+// store_pair with stochastic rounding for 16-bit storage (r: random bits, sr_bits)
 template <typename S>
-__device__ __forceinline__ void store_pair_sr(S* base, int off, typename Store<S>::T fr, typename Store<S>::T fb,
-                                              typename Store<S>::T wr0, uint32_t key) {
+__device__ __forceinline__ void store_pair_sr(S* p, typename Store<S>::T fr, typename Store<S>::T fb,
+                                              typename Store<S>::T wr0, uint32_t r) {
   using T = typename Store<S>::T;
   if constexpr (Store<S>::kDeviation) {
     T lo, hi;
     encode<S, T>(fr, fb, wr0, lo, hi);
-    Store<S>::stp_sr(base + off, lo, hi, hash32(uint32_t(off) + key));
+    Store<S>::stp_sr(p, lo, hi, r);
   } else {
-    store_pair<S>(base + off, fr, fb, wr0);
+    store_pair<S>(p, fr, fb, wr0);
   }
 }
 

@@ -514,6 +514,8 @@ __global__ void __launch_bounds__(32 * TY, sizeof(typename Store<S>::T) == 4 ? 1
     if constexpr (Store<S>::kDeviation) srk = sr_key(A.sr_epoch, A.sr_step, sL.pop_off);
     const int c3x = lx + 3, c3y = ly + 3;
     const int pn_own = pop_node(xs, ys, pitch);
+    uint32_t srh = 0;
+    if constexpr (Store<S>::kDeviation) srh = sr_node(srk, pn_own);
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
       const T en = T(ex(a)) * nxo + T(ey(a)) * nyo;
@@ -532,7 +534,7 @@ __global__ void __launch_bounds__(32 * TY, sizeof(typename Store<S>::T) == 4 ? 1
           k = pop_node(sxm[c3x + ex(a)], sym[c3y + ey(a)], pitch);
         }
       }
-      store_pair_sr<S>(dst, k + slot * kDir, oR, oB, wgt<T>(a) * r0, srk);
+      store_pair_sr<S>(dst + k + slot * kDir, oR, oB, wgt<T>(a) * r0, sr_bits(srh, a));
     }
   }
 }
@@ -1264,11 +1266,14 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
     pert[6] = -pert[8];
     const int kn = ym2 * rowseg + colk[1];
     const int rowk[3] = {ym3 * rowseg, ym2 * rowseg, ym1 * rowseg};
+    uint32_t srh = 0;
+    if constexpr (Store<S>::kDeviation) srh = sr_node(srk, kn);
     if (mask == 0 && !(myf & F_EDGE)) {
 #pragma unroll
       for (int a = 0; a < 9; ++a) {
         const T oR = fmaf(cR, fp[a], pert[a]);
-        store_pair_sr<S>(dst, rowk[ey(a) + 1] + colk[ex(a) + 1] + a * kDir, oR, fp[a] - oR, wgt<T>(a) * r0, srk);
+        store_pair_sr<S>(dst + rowk[ey(a) + 1] + colk[ex(a) + 1] + a * kDir, oR, fp[a] - oR, wgt<T>(a) * r0,
+                         sr_bits(srh, a));
       }
     } else {
       const bool okx[3] = {px || cx - 1 >= 0, true, px || cx + 1 < nx};
@@ -1282,7 +1287,7 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
           if (mask & (1u << (a - 1))) k = kn + opp(a) * kDir;
           else k = rowk[ey(a) + 1] + colk[ex(a) + 1] + a * kDir;
         }
-        store_pair_sr<S>(dst, k, oR, fp[a] - oR, wgt<T>(a) * r0, srk);
+        store_pair_sr<S>(dst + k, oR, fp[a] - oR, wgt<T>(a) * r0, sr_bits(srh, a));
       }
     }
     }
