@@ -38,7 +38,7 @@ __host__ __device__ constexpr int sweep_width(bool /*fp64*/) { return kSweepThre
 // resident k_sweepf blocks per SM it is compiled for (registers <= 65536 / (128 * this)),
 // FP32 storage and 16-bit storage
 constexpr int kSweepFMinBlocks = 5;
-constexpr int kSweepFMinBlocks16 = 6;
+constexpr int kSweepFMinBlocks16 = 7;
 
 // Per-lattice constants, resident in global memory, one entry per lattice of a handle.
 struct LatDev {
@@ -185,6 +185,13 @@ template <> struct Store<__nv_bfloat16> {
     hi = v.y;
   }
 };
+
+// scale of the stored deviations (1 for direct storage)
+template <typename S>
+__host__ __device__ constexpr float store_scale() {
+  if constexpr (Store<S>::kDeviation) return Store<S>::kScale;
+  else return 1.0f;
+}
 
 // stored pair (lo = k 0, hi = k 1) <-> (f_R, f_B)
 template <typename S, typename T>

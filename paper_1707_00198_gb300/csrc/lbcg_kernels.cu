@@ -1082,6 +1082,30 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
       const uint8_t f_r = fo >= 0 ? sfg[slot][0][fo] : fl[ym0 * pitch + xm];
       snb[s0][t] = fo >= 0 ? sfg[slot][1][fo] : nbm[ym0 * pitch + xm];
       if (!(f_r & F_SOLID)) {
+        T sr, sb;
+        bool done = false;
+        if constexpr (Store<S>::kDeviation) {
+          // deviation storage, staged, not a Zou-He column: the totals f = w rho0 + d / K and
+          // the colour difference sum(g) / K come straight from the stored pairs
+          if (soff >= 0 && !edge) {
+            constexpr float inv = 1.0f / store_scale<S>(), hinv = 0.5f / store_scale<S>();
+            const S* row = sraw + slot * (kStageSegs * kSeg) + soff;
+            T rho = T(0), gsum = T(0);
+#pragma unroll
+            for (int a = 0; a < 9; ++a) {
+              T lo, hi;
+              staged_pair<S>(row, a, lo, hi);
+              ft[a] = fmaf(lo, inv, wgt<T>(a) * r0);
+              rho += ft[a];
+              gsum += hi;
+            }
+            const T hr = T(0.5) * rho;
+            sr = fmaf(gsum, hinv, hr);
+            sb = fmaf(-gsum, hinv, hr);
+            done = true;
+          }
+        }
+        if (!done) {
         T fr[9], fb[9];
         if (soff >= 0) {
           const S* row = sraw + slot * (kStageSegs * kSeg) + soff;
@@ -1100,8 +1124,10 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
         for (int a = 2; a < 9; ++a) srb_ = P::add(srb_, P::mk(fr[a], fb[a]));
 #pragma unroll
         for (int a = 0; a < 9; ++a) ft[a] = fr[a] + fb[a];
-        rbt = srb_;
-        const T sr = srb_.x, sb = srb_.y;
+        sr = srb_.x;
+        sb = srb_.y;
+        }
+        rbt = P::mk(sr, sb);
         const T w = (sr - sb) * rcp_(sr + sb);
         v = sb == T(0) ? T(1) : (sr == T(0) ? T(-1) : w);
       }
@@ -1251,9 +1277,13 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
     fp[6] = (f[6] - Qm) + XmY;
     fp[8] = (f[8] - Qm) - XmY;
     // recolouring (Eq. 14): oR = (rho_R / rho) f' + beta (rho_R rho_B / rho) w_a e_a.n, oB = f' - oR
+    // 16-bit storage stores d = K (f' - w rho0) and g = K (oR - oB) = K ((2 cR - 1) f' + 2 pert),
+    // formed from f' directly: the perturbation is scaled by 2K here
+    constexpr float kK = store_scale<S>();
+    constexpr float kP = Store<S>::kDeviation ? 2.0f * kK : 1.0f;
     const T cR = rhoR * irho;
     const T pc = beta * rhoR * (rhoB * irho);
-    const T c1 = pc * T(1.0 / 9.0), c2 = pc * T(1.0 / 36.0);
+    const T c1 = pc * T(kP / 9.0), c2 = pc * T(kP / 36.0);
     T pert[9];
     pert[0] = T(0);
     pert[1] = c1 * nxo;
@@ -1268,26 +1298,32 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
     const int rowk[3] = {ym3 * rowseg, ym2 * rowseg, ym1 * rowseg};
     uint32_t srh = 0;
     if constexpr (Store<S>::kDeviation) srh = sr_node(srk, kn);
+    const T cg = fmaf(cR, T(2.0f * kK), T(-kK));   // K (2 cR - 1), deviation storage only
+    const T nkr0 = T(-kK) * r0;
+    // the stored pair of direction a at q
+    auto emit = [&](S* q, int a) {
+      if constexpr (Store<S>::kDeviation) {
+        Store<S>::stp_sr(q, fmaf(fp[a], T(kK), nkr0 * wgt<T>(a)), fmaf(cg, fp[a], pert[a]), sr_bits(srh, a));
+      } else {
+        const T oR = fmaf(cR, fp[a], pert[a]);
+        store_pair<S>(q, oR, fp[a] - oR, wgt<T>(a) * r0);
+      }
+    };
     if (mask == 0 && !(myf & F_EDGE)) {
 #pragma unroll
-      for (int a = 0; a < 9; ++a) {
-        const T oR = fmaf(cR, fp[a], pert[a]);
-        store_pair_sr<S>(dst + rowk[ey(a) + 1] + colk[ex(a) + 1] + a * kDir, oR, fp[a] - oR, wgt<T>(a) * r0,
-                         sr_bits(srh, a));
-      }
+      for (int a = 0; a < 9; ++a) emit(dst + rowk[ey(a) + 1] + colk[ex(a) + 1] + a * kDir, a);
     } else {
       const bool okx[3] = {px || cx - 1 >= 0, true, px || cx + 1 < nx};
       const bool oky[3] = {py || p - 1 >= 0, true, py || p + 1 < ny};
 #pragma unroll
       for (int a = 0; a < 9; ++a) {
-        const T oR = fmaf(cR, fp[a], pert[a]);
         int k = kn + a * kDir;
         if (a != 0) {
           if (!(okx[ex(a) + 1] && oky[ey(a) + 1])) continue;
           if (mask & (1u << (a - 1))) k = kn + opp(a) * kDir;
           else k = rowk[ey(a) + 1] + colk[ex(a) + 1] + a * kDir;
         }
-        store_pair_sr<S>(dst + k, oR, fp[a] - oR, wgt<T>(a) * r0, sr_bits(srh, a));
+        emit(dst + k, a);
       }
     }
     }
