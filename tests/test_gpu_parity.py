@@ -200,8 +200,11 @@ def test_16bit_storage_one_step(prec, tol, kind, ty, rows):
 STORE16_OBS = {"fp16": {"theta": 0.5, "mass": 1e-3}, "bf16": {"theta": 0.5, "mass": 6e-3}}
 
 
+@pytest.mark.parametrize("schedule", ["default", "sweep"])
 @pytest.mark.parametrize("prec", ["fp16", "bf16"])
-def test_16bit_storage_observables_after_2000_steps(prec):
+def test_16bit_storage_observables_after_2000_steps(prec, schedule):
+    """The droplet is small enough to take the tile kernel by default; "sweep" forces the
+    y-sweep kernel, whose 16-bit path forms the totals and the stored pairs differently."""
     g, p = I.config_static_droplet()
     from paper_1707_00198_gb300.lbcg import Lattice
     ref = Lattice(g, p, "fp64")
@@ -212,6 +215,8 @@ def test_16bit_storage_observables_after_2000_steps(prec):
     # FP64 conserves each colour's mass to rounding
     assert abs(oref["mass_R"] - o0["mass_R"]) <= 1e-12 * o0["mass_R"]
     L = Lattice(g, p, prec)
+    if schedule == "sweep":
+        L.set_sweep(0)
     L.step(2000)
     o = L.observables(wall_y=0.5)
     L.close()
