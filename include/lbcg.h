@@ -47,7 +47,7 @@ typedef enum {
   LBCG_E_CUDA = 4,            /* a CUDA call failed; the handle is dead               */
   LBCG_E_DIVERGED = 5,        /* non-finite density found by lbcg_observables         */
   LBCG_E_TIMEOUT = 6,         /* reserved for bounded device waits                    */
-  LBCG_E_UNSUPPORTED = 7,     /* request outside what this build supports             */
+  LBCG_E_UNSUPPORTED = 7,     /* request outside what this library supports           */
   LBCG_E_NOMEM = 8            /* device or host allocation failed                     */
 } lbcg_status;
 
