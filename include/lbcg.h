@@ -191,9 +191,11 @@ lbcg_status lbcg_set_tile(lbcg_handle* h, int32_t ty);
  * derivative is taken at the crossing cells found at T; LBCG_OBJ_RED_MASS, J = the red
  * (invading) fluid's mass sum_x rho_R(x), i.e. the displaced mass plus its initial value.
  * Single-lattice FP64 or FP32 handles (else LBCG_E_UNSUPPORTED).  On an FP32 handle the
- * forward steps, checkpoints and segment recomputation are the FP32 step; the reverse kernels
- * read those states and run in FP64 (the gradient of the FP32 trajectory's map, evaluated in
- * double).  Device memory for nsteps/checkpoint + checkpoint states and the FP64 adjoint
+ * forward steps, checkpoints and segment recomputation are the FP32 step.  The reverse kernels
+ * read those states and run in FP64 (reverse_fp32 = 0: the gradient of the trajectory's map
+ * evaluated in double) or in FP32 (reverse_fp32 = 1: several times faster on this GPU, whose
+ * FP64 latency dominates the reverse sweep); the per-node parameter adjoints are summed in
+ * double either way.  Device memory for nsteps/checkpoint + checkpoint states and the adjoint
  * arrays is allocated for the call and freed before it returns. */
 enum { LBCG_OBJ_WEIGHTED = 0, LBCG_OBJ_FINGER_LENGTH = 1, LBCG_OBJ_RED_MASS = 2 };
 typedef struct {
@@ -201,6 +203,7 @@ typedef struct {
   int32_t objective;
   const double* weight;
   int32_t tip_row0, tip_row1, cl_row0, cl_row1;
+  int32_t reverse_fp32;   /* 1: reverse kernels in FP32 arithmetic; 0: FP64 */
 } lbcg_adjoint_spec;
 typedef struct {
   double J, dJ_dsigma, dJ_dnu_R, dJ_dnu_B, dJ_dtheta;

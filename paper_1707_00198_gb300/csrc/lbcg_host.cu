@@ -796,10 +796,11 @@ bool crossing_derivative(const std::vector<double>& prof, int& i0, double& x, do
 
 }  // namespace
 
-extern "C" {
+namespace {
 
-lbcg_status lbcg_adjoint(lbcg_handle* h, const lbcg_adjoint_spec* spec, lbcg_grads* out) {
-  Range range_("lbcg_adjoint");
+// lbcg_adjoint with the reverse kernels in arithmetic R (double or float)
+template <typename R>
+lbcg_status adjoint_run(lbcg_handle* h, const lbcg_adjoint_spec* spec, lbcg_grads* out) {
   lbcg_status s = check_handle(h);
   if (s != LBCG_OK) return s;
   if (!spec || !out) return fail(LBCG_E_ARG, "NULL spec or output");
@@ -818,33 +819,38 @@ lbcg_status lbcg_adjoint(lbcg_handle* h, const lbcg_adjoint_spec* spec, lbcg_gra
   const int64_t nseg = (T + K - 1) / K;
   const size_t sb = lbcg_state_bytes(h);
   AdjBuffers B;
-  double *ckpt, *seg, *lamA, *lamB, *work, *c_dev;
-  double *nsx, *nsy, *ct, *st;
+  constexpr size_t r8 = sizeof(R);
+  double *ckpt, *seg, *pwork;
+  R *lamA, *lamB, *work, *c_dev;
+  R *nsx, *nsy, *ct, *st;
   int* pick;
-  // N-sized arrays: fr, fb, rr/rb/rn, gr, gc, n, dn, lf_r, lf_b, ln, lnt, lg, lrn/lrnt, 4 parameter adjoints
-  const int kWork = 9 + 9 + 3 + 2 + 2 + 2 + 4 + 9 + 9 + 2 + 2 + 2 + 2 + 4;
-  if (!B.get(&ckpt, sb * (size_t)nseg) || !B.get(&seg, sb * (size_t)K) || !B.get(&lamA, 18 * (size_t)N * 8) ||
-      !B.get(&lamB, 18 * (size_t)N * 8) || !B.get(&work, (size_t)kWork * N * 8) || !B.get(&c_dev, (size_t)N * 8) ||
-      !B.get(&nsx, (size_t)N * 8) || !B.get(&nsy, (size_t)N * 8) || !B.get(&ct, (size_t)N * 8) ||
-      !B.get(&st, (size_t)N * 8) || !B.get(&pick, (size_t)N * 4))
+  // N-sized arrays in R: fr, fb, rr/rb/rn, gr, gc, n, dn, lf_r, lf_b, ln, lnt, lg, lrn/lrnt;
+  // in double: the 4 parameter adjoints
+  const int kWork = 9 + 9 + 3 + 2 + 2 + 2 + 4 + 9 + 9 + 2 + 2 + 2 + 2;
+  if (!B.get(&ckpt, sb * (size_t)nseg) || !B.get(&seg, sb * (size_t)K) || !B.get(&lamA, 18 * (size_t)N * r8) ||
+      !B.get(&lamB, 18 * (size_t)N * r8) || !B.get(&work, (size_t)kWork * N * r8) ||
+      !B.get(&pwork, 4 * (size_t)N * 8) || !B.get(&c_dev, (size_t)N * r8) || !B.get(&nsx, (size_t)N * r8) ||
+      !B.get(&nsy, (size_t)N * r8) || !B.get(&ct, (size_t)N * r8) || !B.get(&st, (size_t)N * r8) ||
+      !B.get(&pick, (size_t)N * 4))
     return fail(LBCG_E_NOMEM, "adjoint buffers (%lld checkpoints of %zu bytes)", (long long)nseg, sb);
   // compact normals and angles of the outermost fluid nodes
   {
-    std::vector<double> a(N, 0.0), b(N, 0.0), c(N, 1.0), d(N, 0.0);
+    std::vector<R> a(N, R(0)), b(N, R(0)), c(N, R(1)), d(N, R(0));
     for (const OfbEntry& e : h->ofb_host) {
       const int i = e.y * nx + e.x;
-      a[i] = e.nsx;
-      b[i] = e.nsy;
-      c[i] = e.cos_t;
-      d[i] = e.sin_t;
+      a[i] = R(e.nsx);
+      b[i] = R(e.nsy);
+      c[i] = R(e.cos_t);
+      d[i] = R(e.sin_t);
     }
-    CK(h, cudaMemcpy(nsx, a.data(), N * 8, cudaMemcpyHostToDevice));
-    CK(h, cudaMemcpy(nsy, b.data(), N * 8, cudaMemcpyHostToDevice));
-    CK(h, cudaMemcpy(ct, c.data(), N * 8, cudaMemcpyHostToDevice));
-    CK(h, cudaMemcpy(st, d.data(), N * 8, cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(nsx, a.data(), N * r8, cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(nsy, b.data(), N * r8, cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(ct, c.data(), N * r8, cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(st, d.data(), N * r8, cudaMemcpyHostToDevice));
   }
-  CK(h, cudaMemsetAsync(work, 0, (size_t)kWork * N * 8, h->stream));
-  AdjDev A{};
+  CK(h, cudaMemsetAsync(work, 0, (size_t)kWork * N * r8, h->stream));
+  CK(h, cudaMemsetAsync(pwork, 0, 4 * (size_t)N * 8, h->stream));
+  AdjDevT<R> A{};
   {
     LatDev ld;
     CK(h, cudaMemcpy(&ld, h->d_lats, sizeof(LatDev), cudaMemcpyDeviceToHost));
@@ -854,15 +860,16 @@ lbcg_status lbcg_adjoint(lbcg_handle* h, const lbcg_adjoint_spec* spec, lbcg_gra
   A.N = N;
   A.flags = h->d_flags;
   A.src_fp32 = h->prec == LBCG_FP32 ? 1 : 0;
-  A.n_eps = h->prec == LBCG_FP32 ? std::max(1e-5, L.prm.grad_eps) : L.prm.grad_eps;
+  // FP32 states or FP32 reverse arithmetic: pure phases carry |grad rho^N| ~ 1e-7 of rounding noise
+  A.n_eps = (h->prec == LBCG_FP32 || sizeof(R) == 4) ? std::max(1e-5, L.prm.grad_eps) : L.prm.grad_eps;
   A.nsx = nsx;
   A.nsy = nsy;
   A.cos_t = ct;
   A.sin_t = st;
   A.pick = pick;
-  double* w = work;
+  R* w = work;
   auto take = [&](int n) {
-    double* p = w;
+    R* p = w;
     w += (size_t)n * N;
     return p;
   };
@@ -888,10 +895,10 @@ lbcg_status lbcg_adjoint(lbcg_handle* h, const lbcg_adjoint_spec* spec, lbcg_gra
   A.lg_y = take(1);
   A.lrn = take(1);
   A.lrnt = take(1);
-  A.p_sigma = take(1);
-  A.p_hR = take(1);
-  A.p_hB = take(1);
-  A.p_theta = take(1);
+  A.p_sigma = pwork;
+  A.p_hR = pwork + N;
+  A.p_hB = pwork + 2 * (size_t)N;
+  A.p_theta = pwork + 3 * (size_t)N;
   // ---- forward with checkpoints (the handle ends at step T)
   for (int64_t k = 0; k < nseg; ++k) {
     CK(h, cudaMemcpyAsync(reinterpret_cast<char*>(ckpt) + sb * k, h->pool[h->cur], sb, cudaMemcpyDeviceToDevice,
@@ -952,10 +959,13 @@ lbcg_status lbcg_adjoint(lbcg_handle* h, const lbcg_adjoint_spec* spec, lbcg_gra
       cw[ii[q] + 1] -= dd1[q] / found;
     }
   }
-  CK(h, cudaMemcpyAsync(c_dev, cw.data(), N * 8, cudaMemcpyHostToDevice, h->stream));
+  {
+    std::vector<R> cr(cw.begin(), cw.end());
+    CK(h, cudaMemcpy(c_dev, cr.data(), N * r8, cudaMemcpyHostToDevice));
+  }
   A.src = h->pool[h->cur];
   A.lam = lamA;
-  CK(h, adjoint_seed(A, c_dev, spec->objective == LBCG_OBJ_RED_MASS, h->stream));
+  CK(h, adjoint_seed<R>(A, c_dev, spec->objective == LBCG_OBJ_RED_MASS, h->stream));
   // ---- reverse, one checkpoint segment at a time.  A segment's work (recompute its states
   // from the checkpoint, then reverse its steps) is captured once per (length, adjoint
   // buffer parity) as a CUDA graph and replayed; only the checkpoint copy is outside.
@@ -968,14 +978,14 @@ lbcg_status lbcg_adjoint(lbcg_handle* h, const lbcg_adjoint_spec* spec, lbcg_gra
       cudaError_t e = launch_step(h->prec, p, h->stream);
       if (e != cudaSuccess) return e;
     }
-    double* lc = lam_in_a ? lamA : lamB;
-    double* ln = lam_in_a ? lamB : lamA;
+    R* lc = lam_in_a ? lamA : lamB;
+    R* ln = lam_in_a ? lamB : lamA;
     for (int64_t j = ns - 1; j >= 0; --j) {
-      AdjDev a = A;
+      AdjDevT<R> a = A;
       a.src = reinterpret_cast<char*>(seg) + sb * j;
       a.lam_next = lc;
       a.lam = ln;
-      cudaError_t e = adjoint_step(a, h->stream);
+      cudaError_t e = adjoint_step<R>(a, h->stream);
       if (e != cudaSuccess) return e;
       std::swap(lc, ln);
     }
@@ -1038,6 +1048,16 @@ lbcg_status lbcg_adjoint(lbcg_handle* h, const lbcg_adjoint_spec* spec, lbcg_gra
   out->dJ_dtheta = gth;
   if (out->dJ_dtheta_node) memcpy(out->dJ_dtheta_node, pth.data(), N * 8);
   return LBCG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbcg_status lbcg_adjoint(lbcg_handle* h, const lbcg_adjoint_spec* spec, lbcg_grads* out) {
+  Range range_("lbcg_adjoint");
+  if (spec && spec->reverse_fp32) return adjoint_run<float>(h, spec, out);
+  return adjoint_run<double>(h, spec, out);
 }
 
 lbcg_status lbcg_set_sweep(lbcg_handle* h, int32_t rows) {

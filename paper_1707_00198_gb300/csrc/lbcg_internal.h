@@ -68,43 +68,48 @@ cudaError_t launch_observables(const LatDev* lats, int lat, int nx, int ny, cons
 
 // Device pointers of one reverse step of the adjoint (lbcg_adjoint.cu); node arrays are
 // compact [ny][nx], FP64.
-struct AdjDev {
+template <typename R>
+struct AdjDevT {
   LatDev L;
   int N;
   const void* src;       // stored state (population pool of the lattice), FP64 or FP32
-  int src_fp32;          // 1: the state is stored in FP32 (an FP32 forward; FP64 reverse)
+  int src_fp32;          // 1: the state is stored in FP32 (an FP32 forward)
   // |grad rho^N| at or below which the reverse sweep takes n = g/|g| as constant.  FP64
   // states: the forward's own guard.  FP32 states: 1e-5 -- their pure phases carry rounding
   // noise |grad rho^N| ~ 1e-7 whose normals the forward only ever multiplies by ~0, but whose
   // 1/|g| ~ 1e8 would give the linearised map a spurious growing mode.
   double n_eps;
   const uint8_t* flags;  // node flags (pitch layout)
-  const double* nsx;     // solid normal at outermost fluid nodes (compact, 0 elsewhere)
-  const double* nsy;
-  const double* cos_t;   // cos and sin of the contact angle per node (compact)
-  const double* sin_t;
+  const R* nsx;     // solid normal at outermost fluid nodes (compact, 0 elsewhere)
+  const R* nsy;
+  const R* cos_t;   // cos and sin of the contact angle per node (compact)
+  const R* sin_t;
   // forward intermediates (compact)
-  double *fr, *fb;       // [9][N] post-streaming populations after the Zou-He columns
-  double *rr, *rb, *rn;  // colour densities, rho^N (fluid nodes; 0 on solid nodes)
-  double *grx, *gry;     // raw gradient (Eq. 28)
-  double *gcx, *gcy;     // corrected gradient (Eq. 31; = raw off Omega_Fb)
-  double *nxv, *nyv;     // n on fluid nodes (0 on solid nodes)
-  double *dn;            // [4][N] d_x n_x, d_y n_x, d_x n_y, d_y n_y
+  R *fr, *fb;       // [9][N] post-streaming populations after the Zou-He columns
+  R *rr, *rb, *rn;  // colour densities, rho^N (fluid nodes; 0 on solid nodes)
+  R *grx, *gry;     // raw gradient (Eq. 28)
+  R *gcx, *gcy;     // corrected gradient (Eq. 31; = raw off Omega_Fb)
+  R *nxv, *nyv;     // n on fluid nodes (0 on solid nodes)
+  R *dn;            // [4][N] d_x n_x, d_y n_x, d_x n_y, d_y n_y
   int *pick;             // 1 or 2: the candidate Eq. 36 chose (0 off Omega_Fb / below guard)
   // adjoints
-  const double* lam_next;  // [18][N] adjoint of the stored state after the step: (fr, fb) pairs
-  double* lam;             // [18][N] adjoint of the stored state before the step
-  double *lf_r, *lf_b;     // [9][N] adjoint of the post-Zou-He populations
-  double *ln_x, *ln_y;     // adjoint of n (local part)
-  double *lnt_x, *lnt_y;   // adjoint of n through the neighbours' grad n (scatter target)
-  double *lg_x, *lg_y;     // adjoint of the corrected gradient (force path)
-  double *lrn, *lrnt;      // adjoint of rho^N: local part, and through the neighbours' gradient
+  const R* lam_next;  // [18][N] adjoint of the stored state after the step: (fr, fb) pairs
+  R* lam;             // [18][N] adjoint of the stored state before the step
+  R *lf_r, *lf_b;     // [9][N] adjoint of the post-Zou-He populations
+  R *ln_x, *ln_y;     // adjoint of n (local part)
+  R *lnt_x, *lnt_y;   // adjoint of n through the neighbours' grad n (scatter target)
+  R *lg_x, *lg_y;     // adjoint of the corrected gradient (force path)
+  R *lrn, *lrnt;      // adjoint of rho^N: local part, and through the neighbours' gradient
   double *p_sigma, *p_hR, *p_hB, *p_theta;  // per-node parameter adjoints (accumulated)
 };
 
-cudaError_t adjoint_step(const AdjDev& A, cudaStream_t st);
+// R: the arithmetic of the reverse kernels (double, or float for the FP32 reverse sweep);
+// the per-node parameter adjoints accumulate in double either way
+template <typename R>
+cudaError_t adjoint_step(const AdjDevT<R>& A, cudaStream_t st);
 // seed lam = dJ/d(state): J = sum weight * rho^N (red_mass false) or the red mass (true)
-cudaError_t adjoint_seed(const AdjDev& A, const double* weight, bool red_mass, cudaStream_t st);
+template <typename R>
+cudaError_t adjoint_seed(const AdjDevT<R>& A, const R* weight, bool red_mass, cudaStream_t st);
 
 // Sets the calling thread's message returned by lbcg_last_error() (lbcg_host.cu).
 void set_last_error(const char* msg);

@@ -53,7 +53,7 @@ class lbcg_obs(C.Structure):
 class lbcg_adjoint_spec(C.Structure):
     _fields_ = [("nsteps", C.c_int64), ("checkpoint", C.c_int64), ("objective", C.c_int32),
                 ("weight", C.POINTER(C.c_double)), ("tip_row0", C.c_int32), ("tip_row1", C.c_int32),
-                ("cl_row0", C.c_int32), ("cl_row1", C.c_int32)]
+                ("cl_row0", C.c_int32), ("cl_row1", C.c_int32), ("reverse_fp32", C.c_int32)]
 
 
 class lbcg_grads(C.Structure):
@@ -283,17 +283,18 @@ def lbcg_field_moments_noalloc(fields_ptr: int, mask_ptr: int, nx: int, ny: int,
 
 
 def lbcg_adjoint(h: int, nx: int, ny: int, nsteps: int, checkpoint: int, weight: Optional[np.ndarray] = None,
-                 tip_rows=None, cl_rows=None, objective: Optional[str] = None) -> dict:
+                 tip_rows=None, cl_rows=None, objective: Optional[str] = None, reverse_fp32: bool = False) -> dict:
     """Run nsteps forward, then the reverse sweep; returns J and its gradients.  With `weight`
     ([ny, nx]) J = sum weight * rho^N at the last step; otherwise `objective` selects
-    "finger_length" (the default) or "red_mass"."""
+    "finger_length" (the default) or "red_mass".  reverse_fp32 runs the reverse kernels in FP32."""
     if weight is not None:
         w = np.ascontiguousarray(weight, dtype=np.float64).reshape(ny, nx)
         obj, wp = LBCG_OBJ_WEIGHTED, _dptr(w)
     else:
         w, obj, wp = None, OBJECTIVES[objective or "finger_length"], None
     o = obs_spec(ny=ny, tip_rows=tip_rows, cl_rows=cl_rows)
-    spec = lbcg_adjoint_spec(nsteps, checkpoint, obj, wp, o.tip_row0, o.tip_row1, o.cl_row0, o.cl_row1)
+    spec = lbcg_adjoint_spec(nsteps, checkpoint, obj, wp, o.tip_row0, o.tip_row1, o.cl_row0, o.cl_row1,
+                             1 if reverse_fp32 else 0)
     dth = np.zeros((ny, nx), dtype=np.float64)
     out = lbcg_grads(0, 0, 0, 0, 0, _dptr(dth))
     _check(library().lbcg_adjoint(h, C.byref(spec), C.byref(out)))
