@@ -331,19 +331,19 @@ def observable_errors(lbcg, stream) -> dict:
     return out
 
 
-def adjoint_rate(lbcg, stream, T: int, K: int, precision: str = "fp32"):
+def adjoint_rate(lbcg, stream, T: int, K: int, precision: str = "fp32", reverse: str = "fp64"):
     """Wall time of lbcg_adjoint (forward with checkpoints + reverse sweep) for the finger
     length of a 400x42 displacement channel, M=10, Ca=0.05, theta=60 deg; the forward steps
-    and checkpoints in `precision`, the reverse sweep in FP64."""
+    and checkpoints in `precision`, the reverse sweep in `reverse`."""
     g, p = I.config_adjoint()
     L = lbcg.Lattice(g, p, precision, stream=stream.cuda_stream)
     try:
-        L.adjoint(2 * K, K)          # warm-up: first launches, allocations
+        L.adjoint(2 * K, K, reverse_fp32=reverse == "fp32")   # warm-up: first launches, allocations
         L.close()
         L = lbcg.Lattice(g, p, precision, stream=stream.cuda_stream)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        out = L.adjoint(T, K)
+        out = L.adjoint(T, K, reverse_fp32=reverse == "fp32")
         torch.cuda.synchronize()
         t = time.perf_counter() - t0
     except Exception as e:  # noqa: BLE001 -- reported, not hidden
@@ -352,7 +352,7 @@ def adjoint_rate(lbcg, stream, T: int, K: int, precision: str = "fp32"):
         L.close()
     nf = int((g.solid == 0).sum())
     return {"workload": f"displacement channel {g.nx}x{g.ny}, M=10, Ca=0.05, theta=60deg, J = finger length",
-            "precision": f"{precision} forward, fp64 reverse", "steps": T, "checkpoint": K, "seconds": t,
+            "precision": f"{precision} forward, {reverse} reverse", "steps": T, "checkpoint": K, "seconds": t,
             "s_per_step": t / T,
             "mlups_forward_plus_reverse": nf * T / t / 1e6, "J": out["J"], "dJ_dtheta": out["dtheta"],
             "dJ_dsigma": out["dsigma"], "dJ_dnu_R": out["dnu_R"], "dJ_dnu_B": out["dnu_B"],
@@ -466,8 +466,9 @@ def run_ours(args):
     # ---- the discrete adjoint on the 400x42 channel (FP64, rank 0)
     adj = None
     if rank == 0 and not args.no_adjoint:
-        adj = adjoint_rate(lbcg, stream, args.adjoint_steps, args.adjoint_checkpoint, "fp32")
-        adj["fp64"] = adjoint_rate(lbcg, stream, args.adjoint_steps, args.adjoint_checkpoint, "fp64")
+        adj = adjoint_rate(lbcg, stream, args.adjoint_steps, args.adjoint_checkpoint, "fp32", "fp32")
+        adj["fp32_fp64_reverse"] = adjoint_rate(lbcg, stream, args.adjoint_steps, args.adjoint_checkpoint, "fp32", "fp64")
+        adj["fp64"] = adjoint_rate(lbcg, stream, args.adjoint_steps, args.adjoint_checkpoint, "fp64", "fp64")
 
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N=1 only)
     cpu = None
