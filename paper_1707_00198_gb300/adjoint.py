@@ -31,6 +31,7 @@ class ObjectiveSpec:
     objective: str = "finger_length"       # "finger_length", "red_mass" or "weighted"
     weight: Optional[np.ndarray] = None    # [ny, nx], for "weighted"
     precision: str = "fp64"                # "fp64" or "fp32" (forward steps and checkpoints)
+    reverse: str = "fp64"                  # "fp64" or "fp32" (arithmetic of the reverse sweep)
 
 
 class WettingObjective(torch.autograd.Function):
@@ -42,10 +43,11 @@ class WettingObjective(torch.autograd.Function):
                                 theta=float(th.mean()))
         L = Lattice(g, p, spec.precision)
         try:
+            rev = spec.reverse == "fp32"
             if spec.objective == "weighted":
-                out = L.adjoint(spec.nsteps, spec.checkpoint, weight=spec.weight)
+                out = L.adjoint(spec.nsteps, spec.checkpoint, weight=spec.weight, reverse_fp32=rev)
             else:
-                out = L.adjoint(spec.nsteps, spec.checkpoint, objective=spec.objective)
+                out = L.adjoint(spec.nsteps, spec.checkpoint, objective=spec.objective, reverse_fp32=rev)
         finally:
             L.close()
         f64 = dict(dtype=torch.float64)
