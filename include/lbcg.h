@@ -60,7 +60,10 @@ typedef enum {
  *     A step stores them with stochastic rounding (up or down with the probability of the
  *     distance, keyed by a hash of the node and the step), so that changes smaller than
  *     half a unit in the last place accumulate instead of being rounded away; the initial
- *     state and lbcg_set_populations round to nearest. */
+ *     state and lbcg_set_populations round to nearest.  The keys count graph replays and the
+ *     steps within them, so a 16-bit trajectory repeats exactly for the same sequence of
+ *     lbcg_step calls on a fresh handle (lbcg_step(h, 64) and 64 calls of lbcg_step(h, 1)
+ *     round differently; both are unbiased). */
 typedef enum { LBCG_FP64 = 0, LBCG_FP32 = 1, LBCG_FP16_STORE = 2, LBCG_BF16_STORE = 3 } lbcg_precision;
 
 /* x boundaries: periodic; closed (columns 0 and nx-1 must be solid); or a Zou-He velocity
