@@ -181,12 +181,13 @@ void build_strips(lbcg_handle* h, std::vector<int4>& strips) {
   const int W = sweep_width(h->prec == LBCG_FP64);
   long long nx_strips = 0;
   for (const LatHost& L : h->lats) nx_strips += (L.nx + W - 1) / W;
-  // automatic segment height: split the strips into about 16 blocks per SM (FP64: 8), with
+  // automatic segment height: split the strips into about 32 blocks per SM (FP64: 8), with
   // at least 24 rows per segment (FP64: 8), since each segment also sweeps 4 warm-up rows.
   // Blocks are launched in lattice / strip / segment order, so neighbouring segments run
-  // together and their shared halo rows stay in L2.
+  // together and their shared halo rows stay in L2.  (Measured on a 64-channel batch and an
+  // 8192 x 4096 box: 32 blocks per SM beat 16 by 1.5-5 %; segments under 24 rows lose.)
   const bool fp64 = h->prec == LBCG_FP64;
-  const long long target = fp64 ? 152LL * 8 : 152LL * 16;
+  const long long target = fp64 ? 152LL * 8 : 152LL * 32;
   const int min_rows = fp64 ? 8 : 24;
   for (size_t l = 0; l < h->lats.size(); ++l) {
     const LatHost& L = h->lats[l];
