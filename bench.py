@@ -225,6 +225,9 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------- our arm
+AUTOTUNE_PROBE = 20   # launches per candidate schedule in lbcg_autotune
+
+
 def timed_steps(lat, stream, K, flush_buf):
     """K steps; returns total device ms (per-step events when flushing L2 between steps).
     Without flushing the K steps are one lbcg_step call, which replays the handle's CUDA graph
@@ -252,6 +255,8 @@ def measure_form(geoms, prms, precision, K, W, stream, with_profile=False, ty=0)
     lat = lbcg.Lattice(geoms, prms, precision, stream=stream.cuda_stream)
     if ty:
         lat.set_tile(ty)
+    else:
+        lat.autotune(AUTOTUNE_PROBE)
     lat.step(W)
     torch.cuda.synchronize()
     flush = None
@@ -269,11 +274,12 @@ def measure_form(geoms, prms, precision, K, W, stream, with_profile=False, ty=0)
 
 def sequential_rate(lbcg, geoms, prms, precision: str, K: int, W: int, stream) -> dict:
     """The same channels as independent single-lattice handles, stepped one after another
-    (each with its own default schedule and CUDA-graph replay): the baseline the batched
-    launch is compared with."""
+    (each with the schedule lbcg_autotune picks for it and CUDA-graph replay): the baseline
+    the batched launch is compared with."""
     hs = [lbcg.Lattice(g, p, precision, stream=stream.cuda_stream) for g, p in zip(geoms, prms)]
     try:
         for L in hs:
+            L.autotune(AUTOTUNE_PROBE)
             L.step(W)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -289,7 +295,7 @@ def sequential_rate(lbcg, geoms, prms, precision: str, K: int, W: int, stream) -
             L.close()
     nf = fluid_nodes(geoms)
     return {"MLUPS": nf * K / (ms / 1e3) / 1e6, "steps": K, "handles": len(geoms),
-            "schedules": "each handle's default (lattices this small take 32x8 tiles)"}
+            "schedules": "each handle's own lbcg_autotune choice"}
 
 
 def observable_errors(lbcg, stream) -> dict:
@@ -380,6 +386,9 @@ def run_ours(args):
     lat = lbcg.Lattice(geoms, prms, args.precision, stream=stream.cuda_stream)
     if args.ty:
         lat.set_tile(args.ty)
+    else:
+        lat.autotune(AUTOTUNE_PROBE)   # sweep segment heights and tile shapes, on the initial state
+    sched = lat.schedule
     lat.step(args.warmup)
     torch.cuda.synchronize()
     flush = torch.zeros(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda") if lat.state_bytes < 2 * L2_BYTES \
@@ -410,8 +419,8 @@ def run_ours(args):
     achieved = alg_bytes / (step_ms / 1e3) / 1e9
     peaks = measured_peaks()
     peak, peak_src = (peaks["hbm_gbs"], "measured") if peaks and "hbm_gbs" in peaks else (6800.0, "fallback")
-    if args.ty:
-        kname = f"k_step<{args.precision},ty{args.ty}>"
+    if sched:
+        kname = f"k_step<{args.precision},ty{sched}>"
     else:
         kname = "k_sweep<fp64>" if args.precision == "fp64" else f"k_sweepf<{args.precision}>"
     traffic = recorded_traffic(kname, nf)
@@ -482,7 +491,8 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
                 "config": {"workload": args.workload, "description": desc, "lattices": len(geoms), "nodes": nodes,
-                           "schedule": f"tiles 32x{args.ty}" if args.ty else "y-sweep, 124-column strips",
+                           "schedule": (f"tiles 32x{sched}" if sched else "y-sweep, 124-column strips") +
+                           ("" if args.ty else " (chosen by lbcg_autotune)"),
                            "fluid_nodes_per_gpu": nf, "precision": args.precision,
                            "state_bytes": sb, "l2": "flushed before every timed step" if flush is not None
                            else "inputs larger than L2", "mlups_counts": "fluid-node updates"},

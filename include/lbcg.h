@@ -217,9 +217,10 @@ lbcg_status lbcg_adjoint(lbcg_handle* h, const lbcg_adjoint_spec* spec, lbcg_gra
 /* Schedule of the step kernel.  lbcg_create picks the y-sweep over 124-column strips when
  * the strips give each of the 152 SMs a block, else 32-wide tiles (height 4 for FP64,
  * 8 otherwise); lbcg_set_sweep / lbcg_set_tile choose one explicitly.  lbcg_autotune times
- * `probe_steps` launches of each candidate (sweep, tiles 4, 8, 16) on the current state
- * without advancing it, keeps the fastest and writes it to *schedule (0 = sweep, else the
- * tile height; schedule may be NULL).  It synchronises the handle's stream.  The candidates
+ * `probe_steps` launches of each candidate (the sweep with automatic segments and with
+ * segments of 24, 32, 48 and 64 rows; tiles 4, 8, 16) on the current state without advancing
+ * it, keeps the fastest and writes it to *schedule (0 = sweep, else the tile height;
+ * schedule may be NULL).  It synchronises the handle's stream.  The candidates
  * give the same result up to rounding order (FP32: a few ulp per step; FP64 within 1e-13).
  * lbcg_schedule reports the current choice with the same encoding. */
 lbcg_status lbcg_autotune(lbcg_handle* h, int32_t probe_steps, int32_t* schedule);

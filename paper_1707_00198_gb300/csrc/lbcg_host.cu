@@ -1101,18 +1101,22 @@ lbcg_status lbcg_autotune(lbcg_handle* h, int32_t probe_steps, int32_t* schedule
     cudaGraphExecDestroy(h->graph);
     h->graph = nullptr;
   }
+  // the y-sweep at the automatic segment height and at fixed heights, then the tiles
   struct Cand {
-    int sweep, ty;
+    int sweep, ty, rows;
   };
-  const Cand cand[4] = {{1, h->ty}, {0, 4}, {0, 8}, {0, 16}};
+  const Cand cand[8] = {{1, h->ty, 0}, {1, h->ty, 24}, {1, h->ty, 32}, {1, h->ty, 48},
+                        {1, h->ty, 64}, {0, 4, 0},     {0, 8, 0},     {0, 16, 0}};
+  const int ncand = 8;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   CK(h, cudaEventCreate(&e0));
   cudaError_t e = cudaEventCreate(&e1);
   int best = 0;
   float best_ms = 0.f;
-  for (int c = 0; c < 4 && e == cudaSuccess; ++c) {
+  for (int c = 0; c < ncand && e == cudaSuccess; ++c) {
     h->sweep = cand[c].sweep;
     h->ty = cand[c].ty;
+    h->sweep_rows = cand[c].rows;
     s = upload_tiles(h);
     if (s != LBCG_OK) break;
     // src = current state, dst = the other buffer: repeated launches rewrite the same next
@@ -1136,6 +1140,7 @@ lbcg_status lbcg_autotune(lbcg_handle* h, int32_t probe_steps, int32_t* schedule
   if (s != LBCG_OK) return s;
   h->sweep = cand[best].sweep;
   h->ty = cand[best].ty;
+  h->sweep_rows = cand[best].rows;
   s = upload_tiles(h);
   if (s != LBCG_OK) return s;
   if (schedule) *schedule = h->sweep ? 0 : h->ty;
