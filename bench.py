@@ -162,9 +162,13 @@ def measured_peaks():
 
 
 def kernel_source_digest() -> str:
+    """Digest of the kernel sources' code: // comments and whitespace are left out, so that a
+    comment edit does not invalidate counters taken from the same code."""
     h = hashlib.sha256()
     for f in ("lbcg_kernels.cu", "lbcg_device.cuh", "lbcg_geom.h"):
-        h.update(open(os.path.join(ROOT, "paper_1707_00198_gb300", "csrc", f), "rb").read())
+        text = open(os.path.join(ROOT, "paper_1707_00198_gb300", "csrc", f), encoding="utf-8").read()
+        code = "\n".join(" ".join(line.split("//", 1)[0].split()) for line in text.splitlines())
+        h.update(code.encode())
     return h.hexdigest()[:16]
 
 

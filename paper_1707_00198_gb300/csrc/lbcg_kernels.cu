@@ -882,12 +882,17 @@ __global__ void __launch_bounds__(NTH, sizeof(typename Store<S>::T) == 4 ? 1024 
 // ------------------------------------------------------------------ k_sweepf (FP32 arithmetic)
 // The y-sweep of k_sweep for the storage forms that compute in FP32, arranged so that no
 // value is fetched from memory twice and no load is waited on right after it is issued:
-//  - the populations of row r + 1 are loaded into registers while row r is processed (the
-//    row loop is unrolled twice, so the two register buffers alternate without copies);
+//  - one thread issues bulk copies (cp.async.bulk, completing on an mbarrier) of row r + 1's
+//    32-node population segments and of its flag and neighbour-mask bytes into the other of
+//    two shared-memory slots while row r is processed; every thread waits with a bound;
 //  - stage 1 keeps what the collision of the row needs, the nine totals f_a = f_a,R + f_a,B
-//    and (rho_R, rho_B), in a three-row ring in shared memory that only the owning thread
-//    reads, so the collision two rows later neither reloads nor re-sums the populations;
-//  - the moment sums and the back-transform share partial sums (fewer FP32 operations).
+//    and (rho_R, rho_B), in registers until the end of the iteration and then in a two-row
+//    ring in shared memory that only the owning thread reads, so the collision two rows later
+//    neither reloads nor re-sums the populations; the thread's colour gradient is carried to
+//    that collision in registers (42 KB of shared memory per block: 5 blocks per SM in FP32);
+//  - the moment sums and the back-transform share partial sums (fewer FP32 operations);
+//  - 16-bit storage takes the totals straight from the stored deviations and forms the stored
+//    pairs from f' directly, with stochastic rounding (store_scale, stp_sr).
 // ---- bulk asynchronous copies (global -> shared) completing on an mbarrier
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return static_cast<unsigned>(__cvta_generic_to_shared(p)); }
 __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
