@@ -267,8 +267,8 @@ lbcg_status lbcg_destroy(lbcg_handle* h);
  * point exists for callers that cannot call cudaMalloc -- code that runs under a fixed
  * device-memory budget or a custom allocator that forbids new allocations, or a thread that
  * must not take the driver's allocation locks -- and that hold the macroscopic fields of a
- * lattice in their own device buffers.  It performs the same reduction lbcg_observables
- * performs internally, with the per-block partial sums kept in a file-scope device array of
+ * lattice in their own device buffers.  It runs the same reduction lbcg_observables runs
+ * internally, with the per-block partial sums kept in a file-scope device array of
  * 304 x 17 doubles (41,344 bytes) that every GPU loading the library holds until exit.
  *
  *   fields : DEVICE pointer, double [4][ny][nx]: rho_R, rho_B, u_x, u_y (caller-owned);
@@ -277,14 +277,23 @@ lbcg_status lbcg_destroy(lbcg_handle* h);
  *   nx, ny : 1 <= nx*ny <= LBCG_NOALLOC_MAX_NODES, else LBCG_E_ARG with a message;
  *   stream : cudaStream_t the two kernels are enqueued on (asynchronous, no synchronisation);
  *   out    : DEVICE pointer to 17 doubles (caller-owned): mass_R, mass_B, |u|max, the nine
- *            interface moments (as lbcg_obs.moments), sum and count of rho/3 over
- *            rho^N > 0.9, sum and count over rho^N < -0.9, non-finite flag.
+ *            interface moments (as lbcg_obs.moments: n, Sx, Sy, Sxx, Syy, Sxy, Szx, Szy, Sz
+ *            about (nx/2, ny/2)), sum and count of rho/3 over rho^N > 0.9, sum and count over
+ *            rho^N < -0.9, non-finite flag.
+ * The values are raw sums; lbcg_observables derives its outputs from the same 17 values:
+ * dp_laplace = out[12]/out[13] - out[14]/out[15], and the contact angle from the algebraic
+ * circle fit through the moments out[3..11] (the 3x3 normal equations of x^2 + y^2 + D x +
+ * E y + F = 0, centre (-D/2 + nx/2, -E/2 + ny/2)).  Interface links that cross a periodic
+ * seam are not counted, as in lbcg_observables.
  *
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress,
- * with that device current); make that first call before any stream capture.  All calls on
- * a device share the array; calls whose kernels overlap on the GPU race and must be
- * serialised by the caller.  Each call overwrites every partial before reading it, so no
- * state carries over between calls.  Errors are reported through lbcg_last_error(). */
+ * Every call looks up the array's device address in the current context
+ * (cudaGetSymbolAddress); the first call on a device may load the library's device code, so
+ * make it before any stream capture.  All calls on a device share the array; calls whose
+ * kernels overlap on the GPU race and must be serialised by the caller.  Each call overwrites
+ * every partial before reading it, so no state carries over between calls.  Errors found at
+ * the call (arguments, a CUDA error pending from earlier work, a failed launch) are returned
+ * with a message in lbcg_last_error(); a fault while the kernels run (e.g. a bad caller
+ * pointer) surfaces at the caller's next synchronisation. */
 #define LBCG_MASK_SOLID 1
 #define LBCG_MASK_NO_FIT 8
 #define LBCG_NOALLOC_MAX_NODES 2147483647LL

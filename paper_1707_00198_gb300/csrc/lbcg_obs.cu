@@ -2,120 +2,23 @@
 // length and contact-line displacement of Sec. III.D) over one lattice's macroscopic fields
 // rho_R, rho_B, u_x, u_y, in FP64: warp-shuffle, then shared-memory, then a one-block pass
 // over the per-block partials (a fixed order, so the result is deterministic).
-#include "lbcg_internal.h"
+#include "lbcg_obs_reduce.cuh"
 
 namespace lbcg {
 
 size_t obs_partials_doubles() { return size_t(kObsBlocks) * kObsQ; }
 
-namespace {
-
-struct Acc {
-  double q[kObsQ];
-};
-
-__device__ __forceinline__ double rn_of(double r, double b) { return (r - b) / (r + b); }
-
-__device__ __forceinline__ void add_point(Acc& A, double x, double y) {
-  const double z = x * x + y * y;
-  A.q[3] += 1.0;
-  A.q[4] += x;
-  A.q[5] += y;
-  A.q[6] += x * x;
-  A.q[7] += y * y;
-  A.q[8] += x * y;
-  A.q[9] += z * x;
-  A.q[10] += z * y;
-  A.q[11] += z;
-}
-
-__device__ __forceinline__ bool is_max_slot(int q) { return q == 2 || q == 16; }
-
-}  // namespace
-
 __global__ void __launch_bounds__(256) k_obs_partial(const LatDev* __restrict__ lats, int lat,
                                                      const double* __restrict__ macro, long long node_total,
                                                      const uint8_t* __restrict__ flags, double* __restrict__ partials) {
   const LatDev& L = lats[lat];
-  const int nx = L.nx, ny = L.ny;
-  const long long nn = (long long)nx * ny;
-  const uint8_t* fl = flags + L.node_off;
-  const double* rR = macro + L.node_off;
-  const double* rB = macro + node_total + L.node_off;
-  const double* uX = macro + 2 * node_total + L.node_off;
-  const double* uY = macro + 3 * node_total + L.node_off;
-  Acc A;
-#pragma unroll
-  for (int q = 0; q < kObsQ; ++q) A.q[q] = 0.0;
-  const double hx = 0.5 * nx, hy = 0.5 * ny;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += (long long)gridDim.x * blockDim.x) {
-    const int x = int(i % nx), y = int(i / nx);
-    const long long k = (long long)y * L.pitch + x;
-    const uint8_t f = fl[k];
-    if (f & F_SOLID) continue;
-    const double r = rR[k], b = rB[k];
-    A.q[0] += r;
-    A.q[1] += b;
-    const double u = sqrt(uX[k] * uX[k] + uY[k] * uY[k]);
-    A.q[2] = fmax(A.q[2], u);
-    const double rho = r + b;
-    if (!isfinite(rho)) A.q[16] = 1.0;
-    const double rn = rn_of(r, b);
-    if (rn > 0.9) {
-      A.q[12] += rho / 3.0;
-      A.q[13] += 1.0;
-    } else if (rn < -0.9) {
-      A.q[14] += rho / 3.0;
-      A.q[15] += 1.0;
-    }
-    if (f & F_NEAR) continue;
-    if (x + 1 < nx) {
-      const long long k2 = k + 1;
-      if (!(fl[k2] & (F_SOLID | F_NEAR))) {
-        const double b2 = rn_of(rR[k2], rB[k2]);
-        if ((rn >= 0) != (b2 >= 0)) add_point(A, x + rn / (rn - b2) - hx, y - hy);
-      }
-    }
-    if (y + 1 < ny) {
-      const long long k2 = k + L.pitch;
-      if (!(fl[k2] & (F_SOLID | F_NEAR))) {
-        const double b2 = rn_of(rR[k2], rB[k2]);
-        if ((rn >= 0) != (b2 >= 0)) add_point(A, x - hx, y + rn / (rn - b2) - hy);
-      }
-    }
-  }
-  // warp, then block reduction
-  __shared__ double sh[kObsQ][8];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int q = 0; q < kObsQ; ++q) {
-    double v = A.q[q];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const double w = __shfl_down_sync(0xffffffffu, v, o);
-      v = is_max_slot(q) ? fmax(v, w) : v + w;
-    }
-    if (lane == 0) sh[q][warp] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x < kObsQ) {
-    const int q = threadIdx.x;
-    double v = sh[q][0];
-    for (int w = 1; w < int(blockDim.x >> 5); ++w) v = is_max_slot(q) ? fmax(v, sh[q][w]) : v + sh[q][w];
-    partials[blockIdx.x * kObsQ + q] = v;
-  }
+  obs_block_partials(macro + L.node_off, macro + node_total + L.node_off, macro + 2 * node_total + L.node_off,
+                     macro + 3 * node_total + L.node_off, flags + L.node_off, L.nx, L.ny, L.pitch, partials);
 }
 
 __global__ void __launch_bounds__(32) k_obs_final(const double* __restrict__ partials, int nblocks,
                                                   double* __restrict__ out) {
-  const int q = threadIdx.x;
-  if (q >= kObsQ) return;
-  double v = partials[q];
-  for (int b = 1; b < nblocks; ++b) {
-    const double w = partials[b * kObsQ + q];
-    v = is_max_slot(q) ? fmax(v, w) : v + w;
-  }
-  out[q] = v;
+  obs_final(partials, nblocks, out);
 }
 
 // First rho^N >= 0 -> rho^N < 0 change along a row (block 0: mean of rows r0, r1 -> the finger
@@ -133,7 +36,7 @@ __global__ void __launch_bounds__(256) k_obs_rows(const LatDev* __restrict__ lat
   const double* rB = macro + node_total + L.node_off;
   auto rn_at = [&](int x, int y) {
     const long long k = (long long)y * L.pitch + x;
-    return (fl[k] & F_SOLID) ? 0.0 : rn_of(rR[k], rB[k]);
+    return (fl[k] & F_SOLID) ? 0.0 : obs_rn(rR[k], rB[k]);
   };
   auto prof = [&](int x) { return 0.5 * (rn_at(x, ra) + rn_at(x, rb)); };
   int best = 0x7fffffff;

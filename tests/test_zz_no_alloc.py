@@ -98,3 +98,76 @@ def test_noalloc_rejects_sizes_beyond_the_maximum():
         lbcg.lbcg_field_moments_noalloc(buf.data_ptr(), buf.data_ptr(), 65536, 65536, 0, buf.data_ptr())
     with pytest.raises(lbcg.LBCGError, match="nx\\*ny"):
         lbcg.lbcg_field_moments_noalloc(buf.data_ptr(), buf.data_ptr(), 0, 5, 0, buf.data_ptr())
+
+
+def _numpy_sums(fields, mask):
+    """The 17 sums of the entry point written out node by node (dense [ny][nx] layout)."""
+    rR, rB, ux, uy = fields
+    ny, nx = rR.shape
+    q = np.zeros(17)
+    pts = []
+    rn = (rR - rB) / (rR + rB)
+    for y in range(ny):
+        for x in range(nx):
+            if mask[y, x] & 1:
+                continue
+            q[0] += rR[y, x]
+            q[1] += rB[y, x]
+            q[2] = max(q[2], math.hypot(ux[y, x], uy[y, x]))
+            rho = rR[y, x] + rB[y, x]
+            q[16] = max(q[16], 0.0 if math.isfinite(rho) else 1.0)
+            if rn[y, x] > 0.9:
+                q[12] += rho / 3
+                q[13] += 1
+            elif rn[y, x] < -0.9:
+                q[14] += rho / 3
+                q[15] += 1
+            if mask[y, x] & 8:
+                continue
+            for dx, dy in ((1, 0), (0, 1)):
+                x2, y2 = x + dx, y + dy
+                if x2 < nx and y2 < ny and not (mask[y2, x2] & 9) and ((rn[y, x] >= 0) != (rn[y2, x2] >= 0)):
+                    t = rn[y, x] / (rn[y, x] - rn[y2, x2])
+                    pts.append((x + dx * t - nx / 2, y + dy * t - ny / 2))
+    for px, py in pts:
+        z = px * px + py * py
+        q[3:12] += (1, px, py, px * px, py * py, px * py, z * px, z * py, z)
+    return q
+
+
+def test_noalloc_tiny_lattices_and_the_nonfinite_flag():
+    """A 3 x 2 lattice, far smaller than one block's stride (most blocks write all-zero
+    partials), with and without a NaN density: the sums equal a node-by-node evaluation and
+    the non-finite slot is set exactly when a density is not finite."""
+    import __graft_entry__ as ge
+    ge.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1707_00198_gb300 import lbcg
+
+    rng = np.random.default_rng(5)
+    rR = rng.uniform(0.0, 1.0, (2, 3))
+    rR[0, 0], rR[1, 2] = 1.0, 0.97          # one red-rich node each side of the crossings
+    rB = 1.0 - rR + rng.uniform(0.0, 0.01, (2, 3))
+    ux, uy = rng.uniform(-0.1, 0.1, (2, 3)), rng.uniform(-0.1, 0.1, (2, 3))
+    mask = np.zeros((2, 3), np.uint8)
+    mask[1, 0] = 1                          # a solid node, skipped
+    stream = torch.cuda.current_stream().cuda_stream
+    for nan in (False, True):
+        f = np.stack([rR, rB, ux, uy]).copy()
+        if nan:
+            f[0, 0, 1] = float("nan")
+        ref = _numpy_sums(f, mask)
+        dev = torch.tensor(f, dtype=torch.float64, device="cuda").contiguous()
+        dmask = torch.tensor(mask, device="cuda").contiguous()
+        out = torch.full((17,), -7.0, dtype=torch.float64, device="cuda")
+        lbcg.lbcg_field_moments_noalloc(dev.data_ptr(), dmask.data_ptr(), 3, 2, stream, out.data_ptr())
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        assert got[16] == (1.0 if nan else 0.0)
+        if nan:
+            assert math.isnan(got[0]) and abs(got[1] - ref[1]) <= 1e-14
+        else:
+            assert np.allclose(got, ref, rtol=1e-12, atol=1e-14), (got, ref)
+            assert ref[3] >= 1        # the case has interface points
+        assert abs(got[2] - ref[2]) <= 1e-15
