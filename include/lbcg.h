@@ -46,7 +46,7 @@ typedef enum {
   LBCG_E_UNSTABLE_PARAM = 3,  /* nu <= 0, theta outside (0, pi), |u_in| >= 1, ...     */
   LBCG_E_CUDA = 4,            /* a CUDA call failed; the handle is dead               */
   LBCG_E_DIVERGED = 5,        /* non-finite density found by lbcg_observables         */
-  LBCG_E_TIMEOUT = 6,         /* reserved for bounded device waits                    */
+  LBCG_E_TIMEOUT = 6,         /* a bounded device wait ran out (lbcg_set_poll_limit)  */
   LBCG_E_UNSUPPORTED = 7,     /* request outside what this library supports           */
   LBCG_E_NOMEM = 8            /* device or host allocation failed                     */
 } lbcg_status;
@@ -181,6 +181,20 @@ lbcg_status lbcg_download_state(lbcg_handle* h, void* host_out, size_t bytes);
  * rounding; the choice only changes speed.  Both calls synchronise and drop captured graphs. */
 lbcg_status lbcg_set_sweep(lbcg_handle* h, int32_t rows);
 lbcg_status lbcg_set_tile(lbcg_handle* h, int32_t ty);
+
+/* Failure detection of the y-sweep's only device-side wait.  In the FP32 and 16-bit y-sweep a
+ * block stages each row in shared memory with bulk asynchronous copies that complete on an
+ * mbarrier, and every thread waits for the row with a bounded number of polls (default 2^22,
+ * about a second; a wait that healthy hardware always finishes in microseconds).  When a wait
+ * gives up, the block stops at that row without writing it or any later row, waits (with the
+ * default bound) for the copies it already issued, and sets the handle's device error word;
+ * the next synchronising call (lbcg_observables, lbcg_get_populations, lbcg_get_fields,
+ * lbcg_download_state, lbcg_diagnostics) returns LBCG_E_TIMEOUT, clears the word and leaves
+ * the handle usable: the state of the steps since the previous check is unreliable and should
+ * be replaced (lbcg_set_populations, lbcg_upload_state).  lbcg_set_poll_limit sets the number
+ * of polls (polls < 0 restores the default; 0 makes every wait give up at once, which tests
+ * the path without any fault).  Synchronises and drops captured graphs. */
+lbcg_status lbcg_set_poll_limit(lbcg_handle* h, int32_t polls);
 
 /* Gradients by the discrete adjoint (reverse mode) of the step.  From the handle's current
  * state, lbcg_adjoint runs `nsteps` steps forward (storing the state every `checkpoint`

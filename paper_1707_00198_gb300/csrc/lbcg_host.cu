@@ -70,6 +70,7 @@ struct lbcg_handle {
   uint8_t* d_nbmask = nullptr;
   int scheme_b = 0;        // some lattice uses wetting scheme (b)
   int* d_err = nullptr;    // device error word (a sweep block's bounded wait ran out)
+  int poll_limit = 1 << 22;   // polls of a sweep block's wait for a staged row (about a second)
   uint32_t* d_sr_epoch = nullptr;     // 16-bit storage: graph replays so far (stochastic-rounding keys)
   double* d_usnap = nullptr;          // velocity stored by lbcg_diagnostics ([2][node_total])
   std::vector<int64_t> snap_step;     // per lattice: step of that velocity, -1 = none
@@ -224,6 +225,7 @@ LaunchStep make_launch(lbcg_handle* h, int src, double* macro, int tile_begin, i
   p.flags = h->d_flags;
   p.nbmask = h->d_nbmask;
   p.err = h->d_err;
+  p.poll_limit = h->poll_limit;
   p.sr_epoch = h->d_sr_epoch;
   p.sr_step = uint32_t(h->step);
   p.scheme_b = h->scheme_b;
@@ -277,13 +279,22 @@ lbcg_status ensure_macro(lbcg_handle* h) {
   return LBCG_OK;
 }
 
-// After a synchronisation: a sweep block gave up waiting for a staged row (the data of that
-// step is then unreliable).  The word stays set; the handle should be recreated.
+// After a synchronisation: a sweep block gave up waiting for a staged row, so the state of
+// the steps since the last check is unreliable (that block stopped without writing the rest
+// of its rows).  The word is cleared once reported: the handle stays usable, and a state set
+// or uploaded afterwards steps correctly again.
 lbcg_status check_device_error(lbcg_handle* h) {
   int e = 0;
   if (cudaMemcpy(&e, h->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
     return cuda_fail(h, cudaGetLastError(), "reading the device error word");
-  if (e) return fail(LBCG_E_TIMEOUT, "a sweep kernel's bounded wait for a staged row ran out");
+  if (e) {
+    if (cudaMemset(h->d_err, 0, sizeof(int)) != cudaSuccess)
+      return cuda_fail(h, cudaGetLastError(), "clearing the device error word");
+    return fail(LBCG_E_TIMEOUT,
+                "a sweep kernel's bounded wait for a staged row ran out%s; the state since the last check is "
+                "unreliable",
+                (e & 2) ? " and its copies could not be drained" : "");
+  }
   return LBCG_OK;
 }
 
@@ -727,6 +738,8 @@ lbcg_status lbcg_get_fields(lbcg_handle* h, int32_t lattice, double* host_out) {
     CK(h, cudaMemcpyAsync(buf.data() + q * L.plane, h->d_macro + q * h->node_total + L.node_off,
                           L.plane * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
+  s = check_device_error(h);
+  if (s != LBCG_OK) return s;
   for (int y = 0; y < L.ny; ++y)
     for (int x = 0; x < L.nx; ++x) {
       const size_t k = (size_t)y * L.pitch + x, i = (size_t)y * L.nx + x;
@@ -1073,6 +1086,19 @@ lbcg_status lbcg_set_sweep(lbcg_handle* h, int32_t rows) {
     h->graph = nullptr;
   }
   return upload_tiles(h);
+}
+
+lbcg_status lbcg_set_poll_limit(lbcg_handle* h, int32_t polls) {
+  lbcg_status s = check_handle(h);
+  if (s != LBCG_OK) return s;
+  if (polls < 0) polls = 1 << 22;
+  CK(h, cudaStreamSynchronize(h->stream));
+  h->poll_limit = polls;
+  if (h->graph) {
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  return LBCG_OK;
 }
 
 lbcg_status lbcg_set_tile(lbcg_handle* h, int32_t ty) {

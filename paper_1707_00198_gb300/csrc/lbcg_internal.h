@@ -34,6 +34,7 @@ struct LaunchStep {
   double* macro;          // non-null: write macroscopic fields instead of stepping (tiles)
   cudaEvent_t* ev;        // non-null: 4 events recorded around k_wall and the step kernel
   int* err;               // device error word: a sweep block's bounded wait ran out
+  int poll_limit;         // polls before a sweep block's wait for a staged row gives up
   const uint32_t* sr_epoch;   // 16-bit storage: stochastic-rounding replay counter (device)
   uint32_t sr_step;           // and the step within the replay / the absolute step
 };

@@ -577,9 +577,11 @@ struct SweepArgs {
   const uint8_t* nbmask;  // bit a-1 set: the neighbour in direction a (1..8) is solid
   const void* wall;
   long long node_total;
-  int* err;               // set to 1 by a block whose wait for a staged row ran out (k_sweepf)
+  int* err;               // k_sweepf: bit 0 set by a block whose wait for a staged row ran out,
+                          // bit 1 if its copies could not be drained before it returned
   const uint32_t* sr_epoch;   // stochastic rounding of 16-bit stores (sr_key)
   uint32_t sr_step;
+  int poll_limit;         // k_sweepf: polls of a staged row's barrier before a wait gives up
 };
 
 template <typename S, int NTH>
@@ -919,11 +921,12 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsign
                "l"(src), "r"(bytes), "r"(smem_addr(bar))
                : "memory");
 }
-// bounded wait: gives up after about a second of polling and reports it through *err
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int* err) {
-  for (int i = 0; i < (1 << 22); ++i)
+// bounded wait for the completion of the barrier phase of the given parity: false after
+// `polls` unsuccessful polls (the default bound, kMbarPolls, is about a second)
+constexpr int kMbarPolls = 1 << 22;
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int polls) {
+  for (int i = 0; i < polls; ++i)
     if (mbar_try_wait(bar, parity)) return true;
-  atomicOr(err, 1);
   return false;
 }
 // segments of a staged row: the (at most 5) contiguous ones holding the strip's columns; the
@@ -1026,6 +1029,8 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
   T ft[9];
   V rbt = P::mk(T(0), T(0)), g_new = P::mk(T(0), T(0)), g_old = P::mk(T(0), T(0));
   bool ft_ok = false;
+  unsigned phase = 0;     // bit s: parity of the next completion of slot s
+  bool lost = false;      // this thread's wait for a staged row ran out
   // issue the bulk copies of (mapped) row y into staging slot `slot` (one thread)
   auto stage_row = [&](int y, int slot) {
     S* d = sraw + slot * (kStageSegs * kSeg);
@@ -1036,8 +1041,6 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
     bulk_copy_g2s(&sfg[slot][0][0], fl + (long long)y * pitch + fx0, fbytes, &sbar[slot]);
     bulk_copy_g2s(&sfg[slot][1][0], nbm + (long long)y * pitch + fx0, fbytes, &sbar[slot]);
   };
-  unsigned phase = 0;   // bit s: parity of the next completion of slot s
-  bool lost = false;    // a wait ran out: copies may still be in flight at the end
   if (t == 0) {
     mbar_init(&sbar[0], 1);
     mbar_init(&sbar[1], 1);
@@ -1046,7 +1049,8 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
   __syncthreads();
   if (t == 0) stage_row(map_row(ys - 2), (ys - 2) & 1);
 
-  auto body = [&](const int r) {
+  // one row of the sweep; false once some thread of the block lost its wait for the row
+  auto body = [&](const int r) -> bool {
     {
       const int t4 = s4;
       s4 = s3;
@@ -1082,7 +1086,8 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
     {
       T v = T(0);
       const int slot = r & 1;
-      if (!mbar_wait(&sbar[slot], (phase >> slot) & 1u, A.err)) lost = true;
+      // (after a lost wait this row's values are garbage: the block stops at the barrier below)
+      if (!mbar_wait(&sbar[slot], (phase >> slot) & 1u, A.poll_limit)) lost = true;
       phase ^= 1u << slot;
       const uint8_t f_r = fo >= 0 ? sfg[slot][0][fo] : fl[ym0 * pitch + xm];
       snb[s0][t] = fo >= 0 ? sfg[slot][1][fo] : nbm[ym0 * pitch + xm];
@@ -1140,7 +1145,9 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
       srn[s0][t] = v;
       sfl[s0][t] = f_r;
     }
-    __syncthreads();
+    // every thread has seen row r, or the block stops here (before it writes anything of
+    // this row or the rows after it)
+    if (__syncthreads_or(lost)) return false;
     // ---- stage 2: grad rho^N and n of row r - 1
     {
       const int tn = n2;
@@ -1337,14 +1344,23 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
       for (int a = 0; a < 9; ++a) sf[q2][a][t] = ft[a];
       srb[q2][t] = rbt;
     }
+    return true;
   };
 
-  for (int r = ys - 2; r <= ye + 1; ++r) {
-    body(r);
+  int r = ys - 2;
+  while (r <= ye + 1 && body(r)) ++r;
+  if (r <= ye + 1 && t == 0) {
+    // Some thread lost its wait for row r: report it, issue no further copies, and do not
+    // return with copies into this block's shared memory in flight.  This thread issued
+    // row r + 1 into the other slot (if the sweep goes that far) and has not waited for it;
+    // row r's slot is outstanding if this thread's own wait for it ran out (its parity bit
+    // was flipped regardless, so flip it back).  Wait for each with the default bound.
+    int e = 1;
+    const int sr = r & 1, sn = sr ^ 1;
+    if (lost && !mbar_wait(&sbar[sr], ((phase >> sr) & 1u) ^ 1u, kMbarPolls)) e |= 2;
+    if (r + 1 <= ye + 1 && !mbar_wait(&sbar[sn], (phase >> sn) & 1u, kMbarPolls)) e |= 2;
+    atomicOr(A.err, e);
   }
-  // after a lost wait, do not leave with copies into this block's shared memory in flight
-  if (lost)
-    for (int j = 0; j < 2; ++j) mbar_wait(&sbar[j], (phase >> j) & 1u, A.err);
 }
 
 // ------------------------------------------------------------------ layout conversion
@@ -1412,7 +1428,7 @@ static cudaError_t launch_all(const LaunchStep& p, cudaStream_t st) {
   if (p.sweep && p.macro == nullptr) {
     if (p.nstrips > 0) {
       SweepArgs B{p.lats, p.strips, p.src, p.dst, p.flags, p.nbmask, p.wall, p.node_total, p.err, p.sr_epoch,
-                  p.sr_step};
+                  p.sr_step, p.poll_limit};
       if constexpr (sizeof(T) == 4)
       {
         if (p.scheme_b) k_sweepf<S, kSweepThreads, true><<<p.nstrips, kSweepThreads, sweepf_dyn_smem<S>(), st>>>(B);

@@ -108,6 +108,7 @@ def library():
         "lbcg_download_state": (C.c_int, [H, C.c_void_p, C.c_size_t]),
         "lbcg_set_tile": (C.c_int, [H, C.c_int32]),
         "lbcg_set_sweep": (C.c_int, [H, C.c_int32]),
+        "lbcg_set_poll_limit": (C.c_int, [H, C.c_int32]),
         "lbcg_profile": (C.c_int, [H, C.c_int32]),
         "lbcg_kernel_times": (C.c_int, [H, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
         "lbcg_launches_per_step": (C.c_int32, [H]),
@@ -133,7 +134,8 @@ def exported_symbols() -> list:
     return ["lbcg_create", "lbcg_create_batch", "lbcg_step", "lbcg_observables", "lbcg_get_populations",
             "lbcg_set_populations", "lbcg_get_fields", "lbcg_state_bytes", "lbcg_upload_state",
             "lbcg_download_state", "lbcg_set_sweep", "lbcg_set_tile", "lbcg_profile", "lbcg_kernel_times", "lbcg_launches_per_step", "lbcg_total_nodes", "lbcg_destroy",
-            "lbcg_last_error", "lbcg_field_moments_noalloc", "lbcg_adjoint", "lbcg_autotune", "lbcg_schedule", "lbcg_diagnostics"]
+            "lbcg_last_error", "lbcg_field_moments_noalloc", "lbcg_adjoint", "lbcg_autotune", "lbcg_schedule", "lbcg_diagnostics",
+            "lbcg_set_poll_limit"]
 
 
 def _check(status: int):
@@ -225,6 +227,11 @@ def lbcg_set_tile(h: int, ty: int):
 
 def lbcg_set_sweep(h: int, rows: int = 0):
     _check(library().lbcg_set_sweep(h, rows))
+
+
+def lbcg_set_poll_limit(h: int, polls: int = -1):
+    """Polls of the sweep's bounded wait for a staged row (-1: the default, 0: give up at once)."""
+    _check(library().lbcg_set_poll_limit(h, polls))
 
 
 def lbcg_autotune(h: int, probe_steps: int = 10) -> int:
@@ -350,6 +357,9 @@ class Lattice:
 
     def set_sweep(self, rows: int = 0):
         lbcg_set_sweep(self.h, rows)
+
+    def set_poll_limit(self, polls: int = -1):
+        lbcg_set_poll_limit(self.h, polls)
 
     def diagnostics(self, circle, inside_red: bool = True, lattice: int = 0) -> dict:
         return lbcg_diagnostics(self.h, lattice, circle, inside_red)
