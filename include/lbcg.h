@@ -23,7 +23,8 @@
  *     e7=(-1,-1), e8=(1,-1).
  *   - Contact angles are in radians, measured through the red fluid.
  *   - All pointers in the structs below are HOST pointers, read during the call and not
- *     kept; the handle owns every device allocation it makes.
+ *     kept; the handle owns every device allocation it makes (from cudaMalloc, or from the
+ *     caller's allocator, lbcg_set_allocator).
  *   - Every function returns an lbcg_status; no exception or abort crosses the ABI.  After
  *     an error lbcg_last_error() returns a message for the calling thread.  A failed CUDA
  *     call marks the handle dead (later calls return LBCG_E_CUDA).
@@ -134,6 +135,26 @@ typedef struct {
 } lbcg_obs;
 
 typedef struct lbcg_handle lbcg_handle;
+
+/* Device memory.  By default a handle allocates its device buffers (the two population pools,
+ * node arrays, work lists, reduction scratch, and the temporaries of lbcg_set_populations,
+ * lbcg_get_populations, lbcg_diagnostics and lbcg_adjoint) with cudaMalloc and frees them with
+ * cudaFree.  A caller that manages device memory itself -- e.g. through PyTorch's caching
+ * allocator, so that its accounting sees the pools -- installs callbacks with
+ * lbcg_set_allocator; every handle created afterwards takes all its device memory from them
+ * and returns it to them (a handle keeps the allocator it was created with, also across later
+ * lbcg_set_allocator calls).  alloc(bytes, stream, ctx) returns device memory of the current
+ * device aligned to 256 bytes, or NULL (the call then fails with LBCG_E_NOMEM); stream is the
+ * handle's cudaStream_t, on which the memory is used; release(ptr, stream, ctx) takes back a
+ * block after the work of the handle on it has completed.  The callbacks are not called during
+ * lbcg_step (nor during a CUDA graph capture).  lbcg_set_allocator(NULL) restores
+ * cudaMalloc / cudaFree.  The setting is process-wide and thread-safe. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* stream, void* ctx);
+  void (*release)(void* ptr, void* stream, void* ctx);
+  void* ctx;
+} lbcg_allocator;
+lbcg_status lbcg_set_allocator(const lbcg_allocator* allocator);
 
 /* Create a handle with ONE lattice.  `stream` is the cudaStream_t on which all later work
  * of the handle is enqueued; with NULL the handle creates (and later destroys) its own

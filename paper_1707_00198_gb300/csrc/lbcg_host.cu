@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -37,6 +38,10 @@ lbcg_status fail(lbcg_status s, const char* fmt, ...) {
   return s;
 }
 
+// device allocator of new handles (lbcg_set_allocator); null callbacks = cudaMalloc / cudaFree
+std::mutex g_alloc_mutex;
+lbcg_allocator g_allocator = {nullptr, nullptr, nullptr};
+
 constexpr int kGraphSteps = 32;   // steps per captured graph (even: the graph starts and ends on pool A)
 constexpr int kDefaultTY = 8;
 constexpr int kSMs = 152;
@@ -57,6 +62,7 @@ struct LatHost {
 
 struct lbcg_handle {
   int prec = 1;
+  lbcg_allocator allocator = {nullptr, nullptr, nullptr};   // the allocator at create
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   bool dead = false;
@@ -111,6 +117,29 @@ lbcg_status cuda_fail(lbcg_handle* h, cudaError_t e, const char* what) {
     cudaError_t e_ = (call);                          \
     if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
   } while (0)
+
+// Device buffers of a handle: from the allocator the handle was created with, else cudaMalloc.
+// A caller's allocator must return memory aligned to 256 bytes (the bulk copies of the sweep
+// need 16); a misaligned block is handed back and counts as a failed allocation.
+bool dev_alloc(const lbcg_handle* h, void** p, size_t bytes) {
+  bytes = std::max<size_t>(bytes, 16);
+  *p = nullptr;
+  if (h->allocator.alloc) {
+    void* q = h->allocator.alloc(bytes, h->stream, h->allocator.ctx);
+    if (q && (reinterpret_cast<uintptr_t>(q) & 255u)) {
+      h->allocator.release(q, h->stream, h->allocator.ctx);
+      q = nullptr;
+    }
+    *p = q;
+    return q != nullptr;
+  }
+  return cudaMalloc(p, bytes) == cudaSuccess;
+}
+void dev_free(const lbcg_handle* h, void* p) {
+  if (!p) return;
+  if (h->allocator.alloc) h->allocator.release(p, h->stream, h->allocator.ctx);
+  else cudaFree(p);
+}
 
 lbcg_status validate(const lbcg_geometry* g, const lbcg_params* p, int idx) {
   if (!g || !p) return fail(LBCG_E_ARG, "lattice %d: NULL geometry or params", idx);
@@ -245,8 +274,8 @@ void free_handle(lbcg_handle* h) {
   void* ptrs[] = {h->pool[0], h->pool[1], h->d_flags,  h->d_wall,  h->d_macro, h->d_lats,
                   h->d_tiles, h->d_groups, h->d_wband, h->d_wvirt, h->d_wsten, h->d_ofb,
                   h->d_obs,   h->d_strips, h->d_nbmask, h->d_err, h->d_usnap, h->d_sr_epoch};
-  for (void* p : ptrs)
-    if (p) cudaFree(p);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (void* p : ptrs) dev_free(h, p);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }
@@ -254,17 +283,19 @@ void free_handle(lbcg_handle* h) {
 lbcg_status upload_tiles(lbcg_handle* h) {
   std::vector<int4> tiles;
   build_tiles(h, tiles);
-  if (h->d_tiles) cudaFree(h->d_tiles);
+  dev_free(h, h->d_tiles);
   h->d_tiles = nullptr;
   h->ntiles = int(tiles.size());
-  CK(h, cudaMalloc(&h->d_tiles, std::max<size_t>(1, tiles.size()) * sizeof(int4)));
+  if (!dev_alloc(h, (void**)&h->d_tiles, std::max<size_t>(1, tiles.size()) * sizeof(int4)))
+    return fail(LBCG_E_NOMEM, "cannot allocate the tile list");
   if (!tiles.empty()) CK(h, cudaMemcpy(h->d_tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice));
   std::vector<int4> strips;
   build_strips(h, strips);
-  if (h->d_strips) cudaFree(h->d_strips);
+  dev_free(h, h->d_strips);
   h->d_strips = nullptr;
   h->nstrips = int(strips.size());
-  CK(h, cudaMalloc(&h->d_strips, std::max<size_t>(1, strips.size()) * sizeof(int4)));
+  if (!dev_alloc(h, (void**)&h->d_strips, std::max<size_t>(1, strips.size()) * sizeof(int4)))
+    return fail(LBCG_E_NOMEM, "cannot allocate the strip list");
   if (!strips.empty())
     CK(h, cudaMemcpy(h->d_strips, strips.data(), strips.size() * sizeof(int4), cudaMemcpyHostToDevice));
   return LBCG_OK;
@@ -272,7 +303,7 @@ lbcg_status upload_tiles(lbcg_handle* h) {
 
 lbcg_status ensure_macro(lbcg_handle* h) {
   if (!h->d_macro) {
-    if (cudaMalloc(&h->d_macro, 4 * (size_t)h->node_total * sizeof(double)) != cudaSuccess)
+    if (!dev_alloc(h, (void**)&h->d_macro, 4 * (size_t)h->node_total * sizeof(double)))
       return fail(LBCG_E_NOMEM, "cannot allocate the macroscopic fields");
     CK(h, cudaMemsetAsync(h->d_macro, 0, 4 * (size_t)h->node_total * sizeof(double), h->stream));
   }
@@ -321,6 +352,14 @@ extern "C" {
 
 const char* lbcg_last_error(void) { return g_err.c_str(); }
 
+lbcg_status lbcg_set_allocator(const lbcg_allocator* a) {
+  g_err.clear();
+  if (a && (!a->alloc || !a->release)) return fail(LBCG_E_ARG, "an allocator needs both alloc and release");
+  std::lock_guard<std::mutex> lock(g_alloc_mutex);
+  g_allocator = a ? *a : lbcg_allocator{nullptr, nullptr, nullptr};
+  return LBCG_OK;
+}
+
 lbcg_status lbcg_create_batch(int32_t n, const lbcg_geometry* geoms, const lbcg_params* prms, int32_t precision,
                               void* stream, lbcg_handle** out) {
   Range range_("lbcg_create_batch");
@@ -335,6 +374,10 @@ lbcg_status lbcg_create_batch(int32_t n, const lbcg_geometry* geoms, const lbcg_
   }
   lbcg_handle* h = new lbcg_handle();
   h->prec = precision;
+  {
+    std::lock_guard<std::mutex> lock(g_alloc_mutex);
+    h->allocator = g_allocator;
+  }
   if (stream) {
     h->stream = static_cast<cudaStream_t>(stream);
   } else {
@@ -433,7 +476,7 @@ lbcg_status lbcg_create_batch(int32_t n, const lbcg_geometry* geoms, const lbcg_
   }
   h->ngroups = int(groups.size());
   const size_t es = elem_size(precision), cs = compute_size(precision);
-  auto alloc = [&](void** p, size_t bytes) { return cudaMalloc(p, std::max<size_t>(bytes, 16)) == cudaSuccess; };
+  auto alloc = [&](void** p, size_t bytes) { return dev_alloc(h, p, bytes); };
   bool ok = alloc(&h->pool[0], 18 * (size_t)node_total * es) && alloc(&h->pool[1], 18 * (size_t)node_total * es) &&
             alloc((void**)&h->d_flags, (size_t)node_total) && alloc((void**)&h->d_nbmask, (size_t)node_total) &&
             alloc((void**)&h->d_err, sizeof(int)) && alloc((void**)&h->d_sr_epoch, sizeof(uint32_t)) &&
@@ -504,11 +547,14 @@ lbcg_status lbcg_create_batch(int32_t n, const lbcg_geometry* geoms, const lbcg_
       }
     }
     double* tmp = nullptr;
-    CKC(cudaMalloc(&tmp, 18 * nn * sizeof(double)));
+    if (!dev_alloc(h, (void**)&tmp, 18 * nn * sizeof(double))) {
+      free_handle(h);
+      return fail(LBCG_E_NOMEM, "staging allocation");
+    }
     cudaError_t e = cudaMemcpy(tmp, host.data(), 18 * nn * sizeof(double), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = launch_to_storage(precision, h->d_lats, l, (long long)nn, tmp, h->d_flags, h->pool[0], 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
-    cudaFree(tmp);
+    dev_free(h, tmp);
     CKC(e);
   }
   CKC(cudaMemcpy(h->pool[1], h->pool[0], 18 * (size_t)node_total * es, cudaMemcpyDeviceToDevice));
@@ -662,7 +708,7 @@ lbcg_status lbcg_diagnostics(lbcg_handle* h, int32_t lattice, const lbcg_diag_sp
   if (lattice < 0 || lattice >= int(h->lats.size())) return fail(LBCG_E_ARG, "bad lattice index %d", lattice);
   if (!(spec->r > 0)) return fail(LBCG_E_ARG, "the circle needs a radius > 0");
   if (!h->d_usnap) {
-    if (cudaMalloc(&h->d_usnap, 2 * (size_t)h->node_total * sizeof(double)) != cudaSuccess)
+    if (!dev_alloc(h, (void**)&h->d_usnap, 2 * (size_t)h->node_total * sizeof(double)))
       return fail(LBCG_E_NOMEM, "cannot allocate the velocity snapshot");
     h->snap_step.assign(h->lats.size(), -1);
   }
@@ -700,11 +746,11 @@ lbcg_status lbcg_get_populations(lbcg_handle* h, int32_t lattice, double* host_o
   const LatHost& L = h->lats[lattice];
   const size_t nn = (size_t)L.nx * L.ny;
   double* tmp = nullptr;
-  if (cudaMalloc(&tmp, 18 * nn * sizeof(double)) != cudaSuccess) return fail(LBCG_E_NOMEM, "staging allocation");
+  if (!dev_alloc(h, (void**)&tmp, 18 * nn * sizeof(double))) return fail(LBCG_E_NOMEM, "staging allocation");
   cudaError_t e = launch_from_storage(h->prec, h->d_lats, lattice, (long long)nn, h->pool[h->cur], h->d_flags, tmp, h->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, tmp, 18 * nn * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  cudaFree(tmp);
+  dev_free(h, tmp);
   if (e != cudaSuccess) return cuda_fail(h, e, "get_populations");
   return check_device_error(h);
 }
@@ -716,11 +762,11 @@ lbcg_status lbcg_set_populations(lbcg_handle* h, int32_t lattice, const double* 
   const LatHost& L = h->lats[lattice];
   const size_t nn = (size_t)L.nx * L.ny;
   double* tmp = nullptr;
-  if (cudaMalloc(&tmp, 18 * nn * sizeof(double)) != cudaSuccess) return fail(LBCG_E_NOMEM, "staging allocation");
+  if (!dev_alloc(h, (void**)&tmp, 18 * nn * sizeof(double))) return fail(LBCG_E_NOMEM, "staging allocation");
   cudaError_t e = cudaMemcpyAsync(tmp, host_in, 18 * nn * sizeof(double), cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = launch_to_storage(h->prec, h->d_lats, lattice, (long long)nn, tmp, h->d_flags, h->pool[h->cur], h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  cudaFree(tmp);
+  dev_free(h, tmp);
   if (e != cudaSuccess) return cuda_fail(h, e, "set_populations");
   return LBCG_OK;
 }
@@ -778,16 +824,19 @@ lbcg_status lbcg_download_state(lbcg_handle* h, void* host_out, size_t bytes) {
 
 namespace {
 
-// device buffers of one adjoint run, freed on every exit path
+// device buffers of one adjoint run (from the handle's allocator), freed on every exit path
 struct AdjBuffers {
+  const lbcg_handle* h;
   std::vector<void*> ptrs;
+  explicit AdjBuffers(const lbcg_handle* h_) : h(h_) {}
   ~AdjBuffers() {
-    for (void* p : ptrs) cudaFree(p);
+    if (!ptrs.empty()) cudaStreamSynchronize(h->stream);
+    for (void* p : ptrs) dev_free(h, p);
   }
   template <typename P>
   bool get(P** p, size_t bytes) {
     void* q = nullptr;
-    if (cudaMalloc(&q, std::max<size_t>(bytes, 16)) != cudaSuccess) return false;
+    if (!dev_alloc(h, &q, bytes)) return false;
     ptrs.push_back(q);
     *p = static_cast<P*>(q);
     return true;
@@ -832,7 +881,7 @@ lbcg_status adjoint_run(lbcg_handle* h, const lbcg_adjoint_spec* spec, lbcg_grad
   const int64_t T = spec->nsteps, K = spec->checkpoint;
   const int64_t nseg = (T + K - 1) / K;
   const size_t sb = lbcg_state_bytes(h);
-  AdjBuffers B;
+  AdjBuffers B(h);
   constexpr size_t r8 = sizeof(R);
   double *ckpt, *seg, *pwork;
   R *lamA, *lamB, *work, *c_dev;

@@ -74,6 +74,14 @@ LBCG_OBJ_WEIGHTED, LBCG_OBJ_FINGER_LENGTH, LBCG_OBJ_RED_MASS = 0, 1, 2
 OBJECTIVES = {"weighted": LBCG_OBJ_WEIGHTED, "finger_length": LBCG_OBJ_FINGER_LENGTH, "red_mass": LBCG_OBJ_RED_MASS}
 
 
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+RELEASE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+
+class lbcg_allocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("release", RELEASE_FN), ("ctx", C.c_void_p)]
+
+
 class LBCGError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -109,6 +117,7 @@ def library():
         "lbcg_set_tile": (C.c_int, [H, C.c_int32]),
         "lbcg_set_sweep": (C.c_int, [H, C.c_int32]),
         "lbcg_set_poll_limit": (C.c_int, [H, C.c_int32]),
+        "lbcg_set_allocator": (C.c_int, [C.POINTER(lbcg_allocator)]),
         "lbcg_profile": (C.c_int, [H, C.c_int32]),
         "lbcg_kernel_times": (C.c_int, [H, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
         "lbcg_launches_per_step": (C.c_int32, [H]),
@@ -135,7 +144,7 @@ def exported_symbols() -> list:
             "lbcg_set_populations", "lbcg_get_fields", "lbcg_state_bytes", "lbcg_upload_state",
             "lbcg_download_state", "lbcg_set_sweep", "lbcg_set_tile", "lbcg_profile", "lbcg_kernel_times", "lbcg_launches_per_step", "lbcg_total_nodes", "lbcg_destroy",
             "lbcg_last_error", "lbcg_field_moments_noalloc", "lbcg_adjoint", "lbcg_autotune", "lbcg_schedule", "lbcg_diagnostics",
-            "lbcg_set_poll_limit"]
+            "lbcg_set_poll_limit", "lbcg_set_allocator"]
 
 
 def _check(status: int):
@@ -232,6 +241,40 @@ def lbcg_set_sweep(h: int, rows: int = 0):
 def lbcg_set_poll_limit(h: int, polls: int = -1):
     """Polls of the sweep's bounded wait for a staged row (-1: the default, 0: give up at once)."""
     _check(library().lbcg_set_poll_limit(h, polls))
+
+
+_allocator_keepalive = []   # every installed allocator: handles keep the one they were created with
+
+
+def lbcg_set_allocator(alloc=None, release=None):
+    """Device allocator of handles created afterwards: alloc(nbytes, stream) -> device pointer
+    (int, 256-byte aligned; 0 on failure) and release(ptr, stream); no arguments restores
+    cudaMalloc / cudaFree."""
+    if alloc is None:
+        _check(library().lbcg_set_allocator(None))
+        return
+    a = ALLOC_FN(lambda nbytes, stream, ctx: alloc(int(nbytes), int(stream or 0)) or None)
+    r = RELEASE_FN(lambda ptr, stream, ctx: release(int(ptr), int(stream or 0)))
+    spec = lbcg_allocator(a, r, None)
+    _check(library().lbcg_set_allocator(C.byref(spec)))
+    _allocator_keepalive.append((a, r, spec))   # the callbacks outlive every handle using them
+
+
+def use_torch_allocator(enable: bool = True):
+    """Take the device memory of handles created afterwards from PyTorch's caching allocator
+    (so torch.cuda.memory_allocated() counts it); enable=False restores cudaMalloc."""
+    if not enable:
+        lbcg_set_allocator()
+        return
+    import torch
+
+    def _alloc(nbytes, stream):
+        return torch.cuda.caching_allocator_alloc(nbytes, stream=stream)
+
+    def _release(ptr, stream):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    lbcg_set_allocator(_alloc, _release)
 
 
 def lbcg_autotune(h: int, probe_steps: int = 10) -> int:

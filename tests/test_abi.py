@@ -1,6 +1,7 @@
 """Host-side checks of the C ABI that need no GPU: the library builds and loads, it exports
 every function include/lbcg.h declares, and argument validation fails with the documented
 status codes before any CUDA call."""
+import ctypes as C
 import math
 import os
 import re
@@ -79,3 +80,11 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.lbcg_step(None, 1) == 1
     assert lib.lbcg_destroy(None) == 0
     assert lib.lbcg_state_bytes(None) == 0
+
+
+def test_allocator_needs_both_callbacks(lib):
+    from paper_1707_00198_gb300 import lbcg
+    a = lbcg.lbcg_allocator(lbcg.ALLOC_FN(lambda n, s, c: None), lbcg.RELEASE_FN(), None)
+    assert lib.lbcg_set_allocator(C.byref(a)) == 1            # LBCG_E_ARG: no release callback
+    assert "alloc and release" in lib.lbcg_last_error().decode()
+    assert lib.lbcg_set_allocator(None) == 0

@@ -74,11 +74,36 @@ def _edge_and_all(got, ref):
     return float(err.max()), float(max(err[..., 0].max(), err[..., -1].max()))
 
 
+_CONDITIONING = {}
+
+
+def _fp32_conditioning(g, p, n):
+    """How far the FP64 oracle itself moves in n steps when its initial populations are
+    perturbed by half an FP32 ulp (relative 2^-24, random signs): the spread that FP32 rounding
+    alone must be allowed to cause.  On channels with noisy initial fields it is far above the
+    droplet's: the choice between the two rotated normals of Eq. 36 (D1 <= D2) is
+    discontinuous, and on outermost fluid nodes where the noisy gradient is nearly equidistant
+    from both, a rounding-level change picks the other candidate and changes n there by O(1)."""
+    if (g.name, n) in _CONDITIONING:
+        return _CONDITIONING[(g.name, n)]
+    lat = O.make_lattice(g, p.theta)
+    fR, fB = O.init_state(lat, g.rhoN0, p.rho0, p)
+    rng = np.random.default_rng(0)
+    sR = torch.from_numpy(rng.choice([-1.0, 1.0], size=tuple(fR.shape)))
+    sB = torch.from_numpy(rng.choice([-1.0, 1.0], size=tuple(fB.shape)))
+    aR, aB = O.run(lat, p, fR, fB, n)
+    bR, bB = O.run(lat, p, fR * (1 + 2.0 ** -24 * sR), fB * (1 + 2.0 ** -24 * sB), n)
+    _CONDITIONING[(g.name, n)] = max(float((aR - bR).abs().max()), float((aB - bB).abs().max()))
+    return _CONDITIONING[(g.name, n)]
+
+
 @pytest.mark.parametrize("kind,ty,rows", SCHEDULES, ids=[s[0] for s in SCHEDULES])
 @pytest.mark.parametrize("name,g,p", CASES, ids=[c[0] for c in CASES])
 def test_fp32_open_columns_one_step_and_100_steps(name, g, p, kind, ty, rows):
-    """FP32 one step from the oracle's state at step 50 within 2e-6 of the oracle's step, and
-    100 steps from the initial state within 5e-5, at every node of every column."""
+    """FP32 one step from the oracle's state at step 50 within 2e-6 of the oracle's step at
+    every node of every column; and 100 steps from the initial state within 5e-5 or, where the
+    problem amplifies rounding more (see _fp32_conditioning), within twice the oracle's own
+    spread under FP32-level perturbations of its initial state."""
     _, s50 = _oracle(g, p, 50)
     _, ref1 = _oracle(g, p, 1, state=s50)
     got1 = _gpu(g, p, 1, "fp32", ty, rows, state=s50)
@@ -87,7 +112,9 @@ def test_fp32_open_columns_one_step_and_100_steps(name, g, p, kind, ty, rows):
     _, ref = _oracle(g, p, 100)
     got = _gpu(g, p, 100, "fp32", ty, rows)
     err, edge = _edge_and_all(got, ref)
-    assert err <= 5e-5, (name, kind, err, edge)
+    tol = max(5e-5, 2 * _fp32_conditioning(g, p, 100))
+    assert err <= tol, (name, kind, err, edge, tol)
+    assert edge <= 5e-5, (name, kind, edge)      # the open columns themselves stay tight
 
 
 # one step from a common state: within four half-ulps at 4/9 (see the derivation beside the
