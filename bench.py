@@ -184,6 +184,24 @@ def recorded_traffic(kernel: str, n_fluid: int):
     return rec["dram_bytes_per_fluid_node"] * n_fluid
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the CPU-baseline record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def cpu_oracle_rate(geoms, prms, budget_s: float = 15.0, max_steps: int = 100000):
     """Time the FP64 oracle (as it stands) on a bounded sample; returns (MLUPS, steps, nodes, cores)."""
     from oracle import lbcg_oracle as O
@@ -201,29 +219,71 @@ def cpu_oracle_rate(geoms, prms, budget_s: float = 15.0, max_steps: int = 100000
     return nf * n / dt / 1e6, n, (g.nx, g.ny, nf), torch.get_num_threads()
 
 
+def c_step_rate(g, p, threads: int, budget_s: float = 2.0, steps: int = 0, warmup: int = 1):
+    """Time the plain C/OpenMP step (oracle/lbcg_cpu.c, as it stands) on lattice g with the given
+    number of threads (0 = all).  Returns (MLUPS, steps timed, seconds)."""
+    from oracle import cpu_step as CS
+    C = CS.CpuLattice(g, p)
+    f = C.init_state()
+    f = C.run(*f, warmup, threads=threads)
+    nf = int((g.solid == 0).sum())
+    if steps <= 0:
+        t0 = time.perf_counter()
+        f = C.run(*f, 1, threads=threads)
+        steps = int(max(2, min(100000, budget_s / max(time.perf_counter() - t0, 1e-6))))
+    t0 = time.perf_counter()
+    C.run(*f, steps, threads=threads)
+    dt = time.perf_counter() - t0
+    C.close()
+    return nf * steps / dt / 1e6, steps, dt
+
+
+def cpu_baseline_record(geoms, prms, desc):
+    """The CPU baseline: the C step on the first lattice of the workload, on all host cores
+    (the reported value) and on one core, plus the same for the static-droplet (100 x 50) and
+    fingering (2000 x 102, M = 1, Ca = 0.05, theta = 90 deg) configurations, and the PyTorch
+    oracle's rate on a section for context.  About 20 s of CPU time."""
+    from oracle import cpu_step as CS
+    g, p = geoms[0], prms[0]
+    cores = len(os.sched_getaffinity(0))
+    v_all, n_all, _ = c_step_rate(g, p, cores)
+    v_one, _, _ = c_step_rate(g, p, 1)
+    cfg = {}
+    for name, (gg, pp) in (("static_droplet_100x50", I.config_static_droplet()),
+                           ("fingering_2000x102", I.config_fingering(M=1.0, Ca=0.05, theta_deg=90.0))):
+        cfg[name] = {"all_cores": c_step_rate(gg, pp, cores)[0], "one_core": c_step_rate(gg, pp, 1, budget_s=1.0)[0]}
+    ov, on, (sx, sy, snf), ocores = cpu_oracle_rate(geoms, prms, budget_s=4.0)
+    return {"value": v_all, "unit": "MLUPS", "cores": CS.threads_used(cores), "kind": "oracle",
+            "impl": "plain C/OpenMP FP64 step (oracle/lbcg_cpu.c)", "cpu_model": cpu_model(),
+            "cores_available": cores, "one_core": v_one,
+            "sample": f"{n_all} FP64 steps of the first lattice ({g.nx}x{g.ny}, {int((g.solid == 0).sum())} fluid "
+                      f"nodes) of: {desc}",
+            "configs_MLUPS": cfg,
+            "pytorch_oracle": {"value": ov, "cores": ocores,
+                               "sample": f"{on} steps of a {sx}x{sy} section ({snf} fluid nodes)"}}
+
+
 # ----------------------------------------------------------------------------- reference arm
 def run_reference(args):
+    """The reference arm: the plain C/OpenMP step of oracle/ (as it stands) on the host cores,
+    each step one step of the first lattice of the workload."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    from oracle import lbcg_oracle as O
+    from oracle import cpu_step as CS
     (geoms, prms), desc = workload(args.workload, rank=0, lattices=args.lattices)
-    g, p = reference_sample(geoms, prms)
-    lat = O.make_lattice(g, p.theta)
-    fR, fB = O.init_state(lat, g.rhoN0, p.rho0, p)
+    g, p = geoms[0], prms[0]
+    cores = len(os.sched_getaffinity(0))
     nf = int((g.solid == 0).sum())
-    fR, fB = O.run(lat, p, fR, fB, args.warmup)
-    t0 = time.perf_counter()
-    fR, fB = O.run(lat, p, fR, fB, args.steps)
-    dt = time.perf_counter() - t0
-    v = nf * args.steps / dt / 1e6
-    sample = f"{g.nx}x{g.ny} section ({nf} fluid nodes) of the first lattice of: {desc}"
+    v, n, dt = c_step_rate(g, p, cores, steps=args.steps, warmup=args.warmup)
+    sample = f"the first lattice ({g.nx}x{g.ny}, {nf} fluid nodes) of: {desc}"
     line = {"impl": "reference", "metric": "MLUPS", "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "description": desc, "precision": "fp64 (CPU oracle)"},
-            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": torch.get_num_threads(), "kind": "oracle",
-                             "sample": sample},
+            "config": {"workload": args.workload, "description": desc, "precision": "fp64 (CPU, plain C/OpenMP)"},
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": CS.threads_used(cores), "kind": "oracle",
+                             "impl": "plain C/OpenMP FP64 step (oracle/lbcg_cpu.c)", "cpu_model": cpu_model(),
+                             "cores_available": cores, "sample": sample},
             "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -453,18 +513,32 @@ def run_ours(args):
            "path": "lbcg_upload_state (pinned) + lbcg_step(1) + lbcg_download_state per step"}
     lat.close()
 
-    # ---- the other storage forms on the same workload (shorter)
+    # ---- the other storage forms on the same workload, the same number of timed steps, each with
+    # the roofline of its step kernel (algorithmic bytes / CUDA-event kernel time)
     forms = {}
     if not args.no_forms:
         for prec in ("fp32", "fp16", "bf16"):
             if prec == args.precision:
-                forms[prec] = {"MLUPS": value / ws, "hbm_gbs_alg": whole_gbs}
+                forms[prec] = {"MLUPS": value / ws, "ms_per_step": ms / args.steps, "steps": args.steps,
+                               "hbm_gbs_alg": whole_gbs,
+                               "roofline": {"kernel": kname, "avg_launch_ms": step_ms, "achieved": achieved,
+                                            "peak": peak, "frac": achieved / peak, "unit": "GB/s"}}
                 continue
-            Kf = max(10, args.steps // 4)
-            L2, msf, _, _ = measure_form(geoms, prms, prec, Kf, args.warmup, stream, ty=args.ty)
+            L2, msf, _, _ = measure_form(geoms, prms, prec, args.steps, args.warmup, stream, ty=args.ty)
+            lbcg.lbcg_profile(L2.h, True)
+            timed_steps(L2, stream, Kp, None)
+            kf, kn = lbcg.lbcg_kernel_times(L2.h)
+            lbcg.lbcg_profile(L2.h, False)
+            sched_f = L2.schedule
             L2.close()
-            forms[prec] = {"MLUPS": nf * Kf / (msf / 1e3) / 1e6,
-                           "hbm_gbs_alg": 36 * STORE_BYTES[prec] * nf * Kf / (msf / 1e3) / 1e9}
+            kms_f = kf[1] / max(kn, 1)
+            alg_f = 36 * STORE_BYTES[prec] * nf
+            forms[prec] = {"MLUPS": nf * args.steps / (msf / 1e3) / 1e6, "ms_per_step": msf / args.steps,
+                           "steps": args.steps,
+                           "hbm_gbs_alg": alg_f * args.steps / (msf / 1e3) / 1e9,
+                           "roofline": {"kernel": f"k_step<{prec},ty{sched_f}>" if sched_f else f"k_sweepf<{prec}>",
+                                        "avg_launch_ms": kms_f, "achieved": alg_f / (kms_f / 1e3) / 1e9,
+                                        "peak": peak, "frac": alg_f / (kms_f / 1e3) / 1e9 / peak, "unit": "GB/s"}}
 
     # ---- batched launch against the same channels as sequential single-lattice runs
     seq = None
@@ -486,9 +560,7 @@ def run_ours(args):
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N=1 only)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
-        v, n, (sx, sy, snf), cores = cpu_oracle_rate(geoms, prms)
-        cpu = {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle",
-               "sample": f"{n} FP64 steps of a {sx}x{sy} section ({snf} fluid nodes) of the first lattice"}
+        cpu = cpu_baseline_record(geoms, prms, desc)
 
     if rank == 0:
         line = {"metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
