@@ -116,10 +116,19 @@ __host__ __device__ __forceinline__ uint32_t hash32(uint32_t x) {
   x ^= x >> 16;
   return x;
 }
-// two floats to packed FP16 rounded toward zero (lo in the low half)
-__device__ __forceinline__ uint32_t cvt_rz_f16x2(float lo, float hi) {
+// Two floats to a packed 16-bit pair (lo in the low half) with stochastic rounding by the
+// conversion itself (cvt.rs): the random bits of the high value are r[31:16], those of the low
+// value r[15:0] (FP16 uses the low 13 bits of each half, the bits below its 10-bit mantissa;
+// BF16 all 16).  That is exactly "add the random bits below the kept bits of the FP32
+// pattern, then truncate", in one instruction per pair.
+__device__ __forceinline__ uint32_t cvt_rs_f16x2(float lo, float hi, uint32_t r) {
   uint32_t d;
-  asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(r));
+  return d;
+}
+__device__ __forceinline__ uint32_t cvt_rs_bf16x2(float lo, float hi, uint32_t r) {
+  uint32_t d;
+  asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(r));
   return d;
 }
 // key of one step of one lattice: epoch counts graph replays (device counter), step the
@@ -143,12 +152,9 @@ template <> struct Store<__half> {
   __device__ static void stp(__half* p, float lo, float hi) {
     *reinterpret_cast<__half2*>(p) = __floats2half2_rn(lo, hi);
   }
-  // stochastic rounding: 13 random bits added below the kept bits of each FP32 pattern (FP16
-  // keeps 10 of its 23 mantissa bits), then truncation; exact for the FP16 normal range
+  // stochastic rounding: 13 random bits below the kept 10 of each FP32 mantissa, truncated
   __device__ static void stp_sr(__half* p, float lo, float hi, uint32_t r) {
-    const float a = __uint_as_float(__float_as_uint(lo) + (r & 0x1FFFu));
-    const float b = __uint_as_float(__float_as_uint(hi) + ((r >> 16) & 0x1FFFu));
-    *reinterpret_cast<uint32_t*>(p) = cvt_rz_f16x2(a, b);
+    *reinterpret_cast<uint32_t*>(p) = cvt_rs_f16x2(lo, hi, r);
   }
   __device__ static void unpack(uint32_t w, float& lo, float& hi) {
     __half2 h;
@@ -170,12 +176,10 @@ template <> struct Store<__nv_bfloat16> {
   __device__ static void stp(__nv_bfloat16* p, float lo, float hi) {
     *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(lo, hi);
   }
-  // stochastic rounding: 16 random bits added below the kept 16 bits of each FP32 pattern,
-  // then truncation (the magnitude rounds up with the probability of the dropped fraction)
+  // stochastic rounding: 16 random bits below the kept 16 bits of each FP32 pattern, truncated
+  // (the magnitude rounds up with the probability of the dropped fraction)
   __device__ static void stp_sr(__nv_bfloat16* p, float lo, float hi, uint32_t r) {
-    const uint32_t a = __float_as_uint(lo) + (r & 0xFFFFu);
-    const uint32_t b = __float_as_uint(hi) + (r >> 16);
-    *reinterpret_cast<uint32_t*>(p) = __byte_perm(a, b, 0x7632);
+    *reinterpret_cast<uint32_t*>(p) = cvt_rs_bf16x2(lo, hi, r);
   }
   __device__ static void unpack(uint32_t w, float& lo, float& hi) {
     __nv_bfloat162 h;
