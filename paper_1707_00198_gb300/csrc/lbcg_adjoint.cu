@@ -3,7 +3,7 @@
 // node), the interfacial tension sigma and the two viscosities (Sec. II; Eq. 1-18, 28-36).
 //
 // One reverse step, from the adjoint lambda' of the stored post-streaming state after the
-// step to the adjoint lambda of the state before it, runs six kernels:
+// step to the adjoint lambda of the state before it, has six stages:
 //   fwd_local   : forward intermediates recomputed from the stored state: post-Zou-He
 //                 populations, colour densities and rho^N (Eq. 12, 16); clears the scatter
 //                 targets of this step;
@@ -16,6 +16,10 @@
 //   adj_normal  : reverse of n = g/|g|, of Eq. 30-36 (d|g| and d theta), and the transpose of
 //                 Eq. 28/29 applied to rho^N (a scatter);
 //   adj_rho     : reverse of Eq. 12 and 16, then of the Zou-He columns -> lambda.
+// The three forward stages of step j - 1 have the same neighbour dependencies as the three
+// reverse stages of step j, so a reverse step runs as three kernels, each doing one reverse
+// stage of step j and one forward stage of step j - 1 (double-buffered intermediates); only
+// the first reversed step of a checkpoint segment needs the three forward kernels alone.
 // A value that a stencil reads on a solid neighbour is that node's Eq. 29 virtual value, a
 // weighted mean of its own fluid neighbours; the transpose scatters straight through that
 // mean onto those fluid nodes.  The kernels are templates on their arithmetic R: double, or
@@ -49,9 +53,7 @@ __device__ __forceinline__ int mapy(const AdjDevT<R>& A, int v) { return wrap_or
 
 // ------------------------------------------------------------------ forward intermediates
 template <typename R>
-__global__ void __launch_bounds__(kAdjThreads) fwd_local(AdjDevT<R> A) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= A.N) return;
+__device__ __forceinline__ void fwd_local_body(const AdjDevT<R>& A, const int i) {
   const int x = i % A.L.nx, y = i / A.L.nx;
   const int N = A.N;
   A.lnt_x[i] = A.lnt_y[i] = A.lrnt[i] = R(0.0);
@@ -134,9 +136,7 @@ __device__ void scatter_field(const AdjDevT<R>& A, R* acc0, R* acc1, int x, int 
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kAdjThreads) fwd_grad(AdjDevT<R> A) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= A.N) return;
+__device__ __forceinline__ void fwd_grad_body(const AdjDevT<R>& A, const int i) {
   const int x = i % A.L.nx, y = i / A.L.nx;
   const uint8_t f = flag_at(A, x, y);
   A.pick[i] = 0;
@@ -182,9 +182,7 @@ __global__ void __launch_bounds__(kAdjThreads) fwd_grad(AdjDevT<R> A) {
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kAdjThreads) fwd_dn(AdjDevT<R> A) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= A.N) return;
+__device__ __forceinline__ void fwd_dn_body(const AdjDevT<R>& A, const int i) {
   const int x = i % A.L.nx, y = i / A.L.nx;
   const int N = A.N;
   R d[4] = {0, 0, 0, 0};
@@ -206,9 +204,7 @@ __global__ void __launch_bounds__(kAdjThreads) fwd_dn(AdjDevT<R> A) {
 // Transpose of the push (Eq. 15, half-way bounce-back, open edges) and the reverse of the
 // node-local part of the step.
 template <typename R>
-__global__ void __launch_bounds__(kAdjThreads) adj_collide(AdjDevT<R> A) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= A.N) return;
+__device__ __forceinline__ void adj_collide_body(const AdjDevT<R>& A, const int i) {
   const int x = i % A.L.nx, y = i / A.L.nx;
   const int N = A.N;
   const LatDev& L = A.L;
@@ -416,9 +412,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_collide(AdjDevT<R> A) {
 // Omega_Fb, g_c = g_r elsewhere), and the transpose of the raw gradient (Eq. 28 on the
 // Eq. 29-filled rho^N), scattered onto rho^N.
 template <typename R>
-__global__ void __launch_bounds__(kAdjThreads) adj_normal(AdjDevT<R> A) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= A.N) return;
+__device__ __forceinline__ void adj_normal_body(const AdjDevT<R>& A, const int i) {
   const int x = i % A.L.nx, y = i / A.L.nx;
   if (is_solid(A, x, y)) return;
   const R lnx = A.ln_x[i] + A.lnt_x[i], lny = A.ln_y[i] + A.lnt_y[i];
@@ -465,9 +459,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_normal(AdjDevT<R> A) {
 
 // reverse of rho^N = (rhoR - rhoB)/(rhoR + rhoB) and of the Zou-He columns
 template <typename R>
-__global__ void __launch_bounds__(kAdjThreads) adj_rho(AdjDevT<R> A) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= A.N) return;
+__device__ __forceinline__ void adj_rho_body(const AdjDevT<R>& A, const int i) {
   const int x = i % A.L.nx, y = i / A.L.nx;
   const int N = A.N;
   for (int a = 0; a < 18; ++a) A.lam[a * N + i] = R(0.0);
@@ -553,6 +545,56 @@ __global__ void __launch_bounds__(kAdjThreads) adj_rho(AdjDevT<R> A) {
 
 inline int nblk(int n) { return (n + kAdjThreads - 1) / kAdjThreads; }
 
+// Forward intermediates of one state (the prologue of a segment's reverse sweep).
+template <typename R>
+__global__ void __launch_bounds__(kAdjThreads) k_fwd_local(AdjDevT<R> A) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < A.N) fwd_local_body(A, i);
+}
+template <typename R>
+__global__ void __launch_bounds__(kAdjThreads) k_fwd_grad(AdjDevT<R> A) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < A.N) fwd_grad_body(A, i);
+}
+template <typename R>
+__global__ void __launch_bounds__(kAdjThreads) k_fwd_dn(AdjDevT<R> A) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < A.N) fwd_dn_body(A, i);
+}
+
+// The reverse of step j (A) in three stages, each fused with the stage of the forward
+// intermediates of the state before it (B, step j - 1) that has the same dependency on the
+// neighbours: (adj_collide, fwd_local), (adj_normal, fwd_grad), (adj_rho, fwd_dn).  A and B
+// share the reverse arrays and parameter adjoints but have their own forward intermediates
+// and scatter targets, so the two halves of a kernel touch disjoint data.  fwd = 0 for the
+// first step of a segment (the state before it is not recomputed yet).
+template <typename R>
+__global__ void __launch_bounds__(kAdjThreads) k_rev_collide(AdjDevT<R> A, AdjDevT<R> B, int fwd) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.N) return;
+  adj_collide_body(A, i);
+  if (fwd) fwd_local_body(B, i);
+}
+template <typename R>
+__global__ void __launch_bounds__(kAdjThreads) k_rev_normal(AdjDevT<R> A, AdjDevT<R> B, int fwd) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.N) return;
+  adj_normal_body(A, i);
+  if (fwd) fwd_grad_body(B, i);
+}
+template <typename R>
+__global__ void __launch_bounds__(kAdjThreads) k_rev_rho(AdjDevT<R> A, AdjDevT<R> B, int fwd) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.N) return;
+  adj_rho_body(A, i);
+  if (fwd) fwd_dn_body(B, i);
+}
+template <typename R>
+__global__ void __launch_bounds__(kAdjThreads) k_adj_rho(AdjDevT<R> A) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < A.N) adj_rho_body(A, i);
+}
+
 // Seed for an objective J = sum_x c(x) rho^N(x) of the stored state: lam = dJ/d(state).
 template <typename R>
 __global__ void __launch_bounds__(kAdjThreads) k_seed_weighted(AdjDevT<R> A, const R* c) {
@@ -581,32 +623,44 @@ __global__ void __launch_bounds__(kAdjThreads) k_seed_red_mass(AdjDevT<R> A) {
 
 }  // namespace
 
-// One reverse step: lam <- (d step / d state)^T lam_next, parameter adjoints accumulated.
-// `A` carries device pointers; the forward intermediates are recomputed from A.src.
+// Forward intermediates of the state A.src (three kernels: the prologue of a segment).
 template <typename R>
-cudaError_t adjoint_step(const AdjDevT<R>& A, cudaStream_t st) {
+cudaError_t adjoint_forward(const AdjDevT<R>& A, cudaStream_t st) {
   const int b = nblk(A.N);
-  fwd_local<R><<<b, kAdjThreads, 0, st>>>(A);
-  fwd_grad<R><<<b, kAdjThreads, 0, st>>>(A);
-  fwd_dn<R><<<b, kAdjThreads, 0, st>>>(A);
-  adj_collide<R><<<b, kAdjThreads, 0, st>>>(A);
-  adj_normal<R><<<b, kAdjThreads, 0, st>>>(A);
-  adj_rho<R><<<b, kAdjThreads, 0, st>>>(A);
+  k_fwd_local<R><<<b, kAdjThreads, 0, st>>>(A);
+  k_fwd_grad<R><<<b, kAdjThreads, 0, st>>>(A);
+  k_fwd_dn<R><<<b, kAdjThreads, 0, st>>>(A);
+  return cudaGetLastError();
+}
+
+// One reverse step: lam <- (d step / d state)^T lam_next, parameter adjoints accumulated,
+// from the forward intermediates of A's state (computed by the previous call, or by
+// adjoint_forward); with B non-null the same three kernels compute B's intermediates.
+template <typename R>
+cudaError_t adjoint_step(const AdjDevT<R>& A, const AdjDevT<R>* B, cudaStream_t st) {
+  const int b = nblk(A.N);
+  const AdjDevT<R>& Bv = B ? *B : A;
+  const int fwd = B ? 1 : 0;
+  k_rev_collide<R><<<b, kAdjThreads, 0, st>>>(A, Bv, fwd);
+  k_rev_normal<R><<<b, kAdjThreads, 0, st>>>(A, Bv, fwd);
+  k_rev_rho<R><<<b, kAdjThreads, 0, st>>>(A, Bv, fwd);
   return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t adjoint_seed(const AdjDevT<R>& A, const R* c, bool red_mass, cudaStream_t st) {
   const int b = nblk(A.N);
-  fwd_local<R><<<b, kAdjThreads, 0, st>>>(A);   // also clears lrnt
+  k_fwd_local<R><<<b, kAdjThreads, 0, st>>>(A);   // also clears lrnt
   if (red_mass) k_seed_red_mass<R><<<b, kAdjThreads, 0, st>>>(A);
   else k_seed_weighted<R><<<b, kAdjThreads, 0, st>>>(A, c);
-  adj_rho<R><<<b, kAdjThreads, 0, st>>>(A);
+  k_adj_rho<R><<<b, kAdjThreads, 0, st>>>(A);
   return cudaGetLastError();
 }
 
-template cudaError_t adjoint_step<double>(const AdjDevT<double>&, cudaStream_t);
-template cudaError_t adjoint_step<float>(const AdjDevT<float>&, cudaStream_t);
+template cudaError_t adjoint_forward<double>(const AdjDevT<double>&, cudaStream_t);
+template cudaError_t adjoint_forward<float>(const AdjDevT<float>&, cudaStream_t);
+template cudaError_t adjoint_step<double>(const AdjDevT<double>&, const AdjDevT<double>*, cudaStream_t);
+template cudaError_t adjoint_step<float>(const AdjDevT<float>&, const AdjDevT<float>*, cudaStream_t);
 template cudaError_t adjoint_seed<double>(const AdjDevT<double>&, const double*, bool, cudaStream_t);
 template cudaError_t adjoint_seed<float>(const AdjDevT<float>&, const float*, bool, cudaStream_t);
 

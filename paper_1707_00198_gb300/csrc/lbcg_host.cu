@@ -886,15 +886,19 @@ lbcg_status adjoint_run(lbcg_handle* h, const lbcg_adjoint_spec* spec, lbcg_grad
   double *ckpt, *seg, *pwork;
   R *lamA, *lamB, *work, *c_dev;
   R *nsx, *nsy, *ct, *st;
-  int* pick;
-  // N-sized arrays in R: fr, fb, rr/rb/rn, gr, gc, n, dn, lf_r, lf_b, ln, lnt, lg, lrn/lrnt;
-  // in double: the 4 parameter adjoints
-  const int kWork = 9 + 9 + 3 + 2 + 2 + 2 + 4 + 9 + 9 + 2 + 2 + 2 + 2;
+  int *pick0, *pick1;
+  // N-sized arrays in R.  Two sets of forward intermediates and scatter targets (a reverse
+  // step computes the intermediates of the state before it): fr, fb, rr/rb/rn, gr, gc, n, dn,
+  // lnt, lrnt; one set of reverse arrays: lf_r, lf_b, ln, lg, lrn.  In double: the 4
+  // parameter adjoints.
+  const int kFwd = 9 + 9 + 3 + 2 + 2 + 2 + 4 + 2 + 1;
+  const int kRev = 9 + 9 + 2 + 2 + 1;
+  const int kWork = 2 * kFwd + kRev;
   if (!B.get(&ckpt, sb * (size_t)nseg) || !B.get(&seg, sb * (size_t)K) || !B.get(&lamA, 18 * (size_t)N * r8) ||
       !B.get(&lamB, 18 * (size_t)N * r8) || !B.get(&work, (size_t)kWork * N * r8) ||
       !B.get(&pwork, 4 * (size_t)N * 8) || !B.get(&c_dev, (size_t)N * r8) || !B.get(&nsx, (size_t)N * r8) ||
       !B.get(&nsy, (size_t)N * r8) || !B.get(&ct, (size_t)N * r8) || !B.get(&st, (size_t)N * r8) ||
-      !B.get(&pick, (size_t)N * 4))
+      !B.get(&pick0, (size_t)N * 4) || !B.get(&pick1, (size_t)N * 4))
     return fail(LBCG_E_NOMEM, "adjoint buffers (%lld checkpoints of %zu bytes)", (long long)nseg, sb);
   // compact normals and angles of the outermost fluid nodes
   {
@@ -929,39 +933,50 @@ lbcg_status adjoint_run(lbcg_handle* h, const lbcg_adjoint_spec* spec, lbcg_grad
   A.nsy = nsy;
   A.cos_t = ct;
   A.sin_t = st;
-  A.pick = pick;
   R* w = work;
   auto take = [&](int n) {
     R* p = w;
     w += (size_t)n * N;
     return p;
   };
-  A.fr = take(9);
-  A.fb = take(9);
-  A.rr = take(1);
-  A.rb = take(1);
-  A.rn = take(1);
-  A.grx = take(1);
-  A.gry = take(1);
-  A.gcx = take(1);
-  A.gcy = take(1);
-  A.nxv = take(1);
-  A.nyv = take(1);
-  A.dn = take(4);
   A.lf_r = take(9);
   A.lf_b = take(9);
   A.ln_x = take(1);
   A.ln_y = take(1);
-  A.lnt_x = take(1);
-  A.lnt_y = take(1);
   A.lg_x = take(1);
   A.lg_y = take(1);
   A.lrn = take(1);
-  A.lrnt = take(1);
+  // the two sets of forward intermediates: view(0) and view(1) differ only in them
+  AdjDevT<R> V[2];
+  for (int q = 0; q < 2; ++q) {
+    V[q] = A;
+    V[q].pick = q ? pick1 : pick0;
+    V[q].fr = take(9);
+    V[q].fb = take(9);
+    V[q].rr = take(1);
+    V[q].rb = take(1);
+    V[q].rn = take(1);
+    V[q].grx = take(1);
+    V[q].gry = take(1);
+    V[q].gcx = take(1);
+    V[q].gcy = take(1);
+    V[q].nxv = take(1);
+    V[q].nyv = take(1);
+    V[q].dn = take(4);
+    V[q].lnt_x = take(1);
+    V[q].lnt_y = take(1);
+    V[q].lrnt = take(1);
+  }
   A.p_sigma = pwork;
   A.p_hR = pwork + N;
   A.p_hB = pwork + 2 * (size_t)N;
   A.p_theta = pwork + 3 * (size_t)N;
+  for (int q = 0; q < 2; ++q) {
+    V[q].p_sigma = A.p_sigma;
+    V[q].p_hR = A.p_hR;
+    V[q].p_hB = A.p_hB;
+    V[q].p_theta = A.p_theta;
+  }
   // ---- forward with checkpoints (the handle ends at step T)
   for (int64_t k = 0; k < nseg; ++k) {
     CK(h, cudaMemcpyAsync(reinterpret_cast<char*>(ckpt) + sb * k, h->pool[h->cur], sb, cudaMemcpyDeviceToDevice,
@@ -1026,9 +1041,10 @@ lbcg_status adjoint_run(lbcg_handle* h, const lbcg_adjoint_spec* spec, lbcg_grad
     std::vector<R> cr(cw.begin(), cw.end());
     CK(h, cudaMemcpy(c_dev, cr.data(), N * r8, cudaMemcpyHostToDevice));
   }
-  A.src = h->pool[h->cur];
-  A.lam = lamA;
-  CK(h, adjoint_seed<R>(A, c_dev, spec->objective == LBCG_OBJ_RED_MASS, h->stream));
+  AdjDevT<R> S0 = V[0];
+  S0.src = h->pool[h->cur];
+  S0.lam = lamA;
+  CK(h, adjoint_seed<R>(S0, c_dev, spec->objective == LBCG_OBJ_RED_MASS, h->stream));
   // ---- reverse, one checkpoint segment at a time.  A segment's work (recompute its states
   // from the checkpoint, then reverse its steps) is captured once per (length, adjoint
   // buffer parity) as a CUDA graph and replayed; only the checkpoint copy is outside.
@@ -1043,14 +1059,28 @@ lbcg_status adjoint_run(lbcg_handle* h, const lbcg_adjoint_spec* spec, lbcg_grad
     }
     R* lc = lam_in_a ? lamA : lamB;
     R* ln = lam_in_a ? lamB : lamA;
+    // prologue: the intermediates of the segment's last state; then each reverse step also
+    // computes those of the state before it, in the other set
+    int q = 0;
+    AdjDevT<R> cur = V[q];
+    cur.src = reinterpret_cast<char*>(seg) + sb * (ns - 1);
+    cudaError_t e = adjoint_forward<R>(cur, h->stream);
+    if (e != cudaSuccess) return e;
     for (int64_t j = ns - 1; j >= 0; --j) {
-      AdjDevT<R> a = A;
-      a.src = reinterpret_cast<char*>(seg) + sb * j;
-      a.lam_next = lc;
-      a.lam = ln;
-      cudaError_t e = adjoint_step<R>(a, h->stream);
+      cur = V[q];
+      cur.src = reinterpret_cast<char*>(seg) + sb * j;
+      cur.lam_next = lc;
+      cur.lam = ln;
+      if (j > 0) {
+        AdjDevT<R> prev = V[q ^ 1];
+        prev.src = reinterpret_cast<char*>(seg) + sb * (j - 1);
+        e = adjoint_step<R>(cur, &prev, h->stream);
+      } else {
+        e = adjoint_step<R>(cur, nullptr, h->stream);
+      }
       if (e != cudaSuccess) return e;
       std::swap(lc, ln);
+      q ^= 1;
     }
     return cudaSuccess;
   };

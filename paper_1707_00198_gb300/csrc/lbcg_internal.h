@@ -105,9 +105,15 @@ struct AdjDevT {
 };
 
 // R: the arithmetic of the reverse kernels (double, or float for the FP32 reverse sweep);
-// the per-node parameter adjoints accumulate in double either way
+// the per-node parameter adjoints accumulate in double either way.
+// adjoint_forward: the forward intermediates of state A.src into A's intermediate arrays.
+// adjoint_step: the reverse of the step from A.src (lam <- J^T lam_next), using A's
+// intermediates; with B non-null it also computes B's (the state before A's), which must use
+// other intermediate and scatter-target arrays than A (the reverse arrays may be shared).
 template <typename R>
-cudaError_t adjoint_step(const AdjDevT<R>& A, cudaStream_t st);
+cudaError_t adjoint_forward(const AdjDevT<R>& A, cudaStream_t st);
+template <typename R>
+cudaError_t adjoint_step(const AdjDevT<R>& A, const AdjDevT<R>* B, cudaStream_t st);
 // seed lam = dJ/d(state): J = sum weight * rho^N (red_mass false) or the red mass (true)
 template <typename R>
 cudaError_t adjoint_seed(const AdjDevT<R>& A, const R* weight, bool red_mass, cudaStream_t st);
