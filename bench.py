@@ -411,6 +411,7 @@ def adjoint_rate(lbcg, stream, T: int, K: int, precision: str = "fp32", reverse:
         L.adjoint(2 * K, K, reverse_fp32=reverse == "fp32")   # warm-up: first launches, allocations
         L.close()
         L = lbcg.Lattice(g, p, precision, stream=stream.cuda_stream)
+        sched = L.autotune(AUTOTUNE_PROBE)   # the forward steps' schedule (the state is kept)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         out = L.adjoint(T, K, reverse_fp32=reverse == "fp32")
@@ -423,6 +424,7 @@ def adjoint_rate(lbcg, stream, T: int, K: int, precision: str = "fp32", reverse:
     nf = int((g.solid == 0).sum())
     return {"workload": f"displacement channel {g.nx}x{g.ny}, M=10, Ca=0.05, theta=60deg, J = finger length",
             "precision": f"{precision} forward, {reverse} reverse", "steps": T, "checkpoint": K, "seconds": t,
+            "forward_schedule": f"tiles 32x{sched}" if sched else "y-sweep",
             "s_per_step": t / T,
             "mlups_forward_plus_reverse": nf * T / t / 1e6, "J": out["J"], "dJ_dtheta": out["dtheta"],
             "dJ_dsigma": out["dsigma"], "dJ_dnu_R": out["dnu_R"], "dJ_dnu_B": out["dnu_B"],

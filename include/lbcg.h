@@ -49,7 +49,8 @@ typedef enum {
   LBCG_E_DIVERGED = 5,        /* non-finite density found by lbcg_observables         */
   LBCG_E_TIMEOUT = 6,         /* a bounded device wait ran out (lbcg_set_poll_limit)  */
   LBCG_E_UNSUPPORTED = 7,     /* request outside what this library supports           */
-  LBCG_E_NOMEM = 8            /* device or host allocation failed                     */
+  LBCG_E_NOMEM = 8,           /* device or host allocation failed                     */
+  LBCG_E_BOUNDS = 9           /* checked build only: a kernel's range check failed    */
 } lbcg_status;
 
 /* Storage and arithmetic of the populations.
@@ -202,6 +203,13 @@ lbcg_status lbcg_download_state(lbcg_handle* h, void* host_out, size_t bytes);
  * rounding; the choice only changes speed.  Both calls synchronise and drop captured graphs. */
 lbcg_status lbcg_set_sweep(lbcg_handle* h, int32_t rows);
 lbcg_status lbcg_set_tile(lbcg_handle* h, int32_t ty);
+
+/* Checked build.  Compiled with -DLBCG_BOUNDS_CHECK (paper_1707_00198_gb300.build.build(
+ * checked=True), which writes liblbcg_checked.so), the step kernels range-check every
+ * population, node-array and staged-row access against the extent of its buffer and skip an
+ * access that fails; the next synchronising call then returns LBCG_E_BOUNDS (and clears the
+ * record).  The checks change no arithmetic: a checked run that reports nothing produces the
+ * same bits as the normal build.  The normal build compiles them out. */
 
 /* Failure detection of the y-sweep's only device-side wait.  In the FP32 and 16-bit y-sweep a
  * block stages each row in shared memory with bulk asynchronous copies that complete on an

@@ -40,7 +40,12 @@ constexpr int kAdjThreads = 64;
 
 template <typename R>
 __device__ __forceinline__ bool is_solid(const AdjDevT<R>& A, int x, int y) {
-  return (A.flags[A.L.node_off + (long long)y * A.L.pitch + x] & F_SOLID) != 0;
+  return A.sol[y * A.L.nx + x] != 0;
+}
+// bit a-1 of node j's mask: its neighbour in direction a (1..8) is solid
+template <typename R>
+__device__ __forceinline__ bool nb_solid(const AdjDevT<R>& A, int j, int a) {
+  return (A.nbm[j] >> (a - 1)) & 1u;
 }
 template <typename R>
 __device__ __forceinline__ uint8_t flag_at(const AdjDevT<R>& A, int x, int y) {
@@ -91,21 +96,24 @@ __device__ __forceinline__ void fwd_local_body(const AdjDevT<R>& A, const int i)
 // Sum of the D2Q9 weights toward the fluid neighbours of a solid node (Eq. 29 denominator)
 template <typename R>
 __device__ R weight_sum(const AdjDevT<R>& A, int x, int y) {
+  const unsigned m = A.nbm[y * A.L.nx + x];
   R den = R(0.0);
   for (int b = 1; b < 9; ++b)
-    if (!is_solid(A, mapx(A, x + ex(b)), mapy(A, y + ey(b)))) den = radd(den, wgt<R>(b));
+    if (!((m >> (b - 1)) & 1u)) den = radd(den, wgt<R>(b));
   return den;
 }
 
 // Value of field v that a stencil reads at (x, y): v itself on a fluid node, the Eq. 29
 // virtual value (the same sums in the same order as the step kernels) on a solid node
+// (solid: whether (x, y) is a solid node, known from the reading node's neighbour mask)
 template <typename R>
-__device__ R read_field(const AdjDevT<R>& A, const R* v, int x, int y) {
-  if (!is_solid(A, x, y)) return v[y * A.L.nx + x];
+__device__ R read_field(const AdjDevT<R>& A, const R* v, int x, int y, bool solid) {
+  if (!solid) return v[y * A.L.nx + x];
+  const unsigned m = A.nbm[y * A.L.nx + x];
   R num = R(0.0), den = R(0.0);
   for (int b = 1; b < 9; ++b) {
-    const int x2 = mapx(A, x + ex(b)), y2 = mapy(A, y + ey(b));
-    if (!is_solid(A, x2, y2)) {
+    if (!((m >> (b - 1)) & 1u)) {
+      const int x2 = mapx(A, x + ex(b)), y2 = mapy(A, y + ey(b));
       num = radd(num, rmul(wgt<R>(b), v[y2 * A.L.nx + x2]));
       den = radd(den, wgt<R>(b));
     }
@@ -115,8 +123,8 @@ __device__ R read_field(const AdjDevT<R>& A, const R* v, int x, int y) {
 
 // Transpose of read_field for one or two fields: add `val` to the adjoint of what was read
 template <typename R>
-__device__ void scatter_field(const AdjDevT<R>& A, R* acc0, R* acc1, int x, int y, R v0, R v1) {
-  if (!is_solid(A, x, y)) {
+__device__ void scatter_field(const AdjDevT<R>& A, R* acc0, R* acc1, int x, int y, bool solid, R v0, R v1) {
+  if (!solid) {
     const int j = y * A.L.nx + x;
     atomicAdd(&acc0[j], v0);
     if (acc1) atomicAdd(&acc1[j], v1);
@@ -125,9 +133,10 @@ __device__ void scatter_field(const AdjDevT<R>& A, R* acc0, R* acc1, int x, int 
   const R den = weight_sum(A, x, y);
   if (!(den > R(0.0))) return;
   const R r = R(1.0) / den;
+  const unsigned m = A.nbm[y * A.L.nx + x];
   for (int b = 1; b < 9; ++b) {
+    if ((m >> (b - 1)) & 1u) continue;
     const int x2 = mapx(A, x + ex(b)), y2 = mapy(A, y + ey(b));
-    if (is_solid(A, x2, y2)) continue;
     const int j = y2 * A.L.nx + x2;
     const R c = wgt<R>(b) * r;
     atomicAdd(&acc0[j], c * v0);
@@ -147,7 +156,7 @@ __device__ __forceinline__ void fwd_grad_body(const AdjDevT<R>& A, const int i) 
   }
   R gx = R(0.0), gy = R(0.0);
   for (int a = 1; a < 9; ++a) {
-    const R t = rmul(wgt<R>(a), read_field(A, A.rn, mapx(A, x + ex(a)), mapy(A, y + ey(a))));
+    const R t = rmul(wgt<R>(a), read_field(A, A.rn, mapx(A, x + ex(a)), mapy(A, y + ey(a)), nb_solid(A, i, a)));
     if (ex(a) == 1) gx = radd(gx, t);
     if (ex(a) == -1) gx = radd(gx, -t);
     if (ey(a) == 1) gy = radd(gy, t);
@@ -189,8 +198,9 @@ __device__ __forceinline__ void fwd_dn_body(const AdjDevT<R>& A, const int i) {
   if (!is_solid(A, x, y)) {
     for (int a = 1; a < 9; ++a) {
       const int x2 = mapx(A, x + ex(a)), y2 = mapy(A, y + ey(a));
-      const R tx = wgt<R>(a) * read_field(A, A.nxv, x2, y2);
-      const R ty = wgt<R>(a) * read_field(A, A.nyv, x2, y2);
+      const bool sn = nb_solid(A, i, a);
+      const R tx = wgt<R>(a) * read_field(A, A.nxv, x2, y2, sn);
+      const R ty = wgt<R>(a) * read_field(A, A.nyv, x2, y2, sn);
       d[0] += ex(a) * tx;
       d[1] += ey(a) * tx;
       d[2] += ex(a) * ty;
@@ -221,7 +231,7 @@ __device__ __forceinline__ void adj_collide_body(const AdjDevT<R>& A, const int 
       const int xr = x + ex(a), yr = y + ey(a);
       if ((!px && (xr < 0 || xr >= L.nx)) || (!py && (yr < 0 || yr >= L.ny))) continue;
       const int xd = mapx(A, xr), yd = mapy(A, yr);
-      if (is_solid(A, xd, yd)) slot = opp(a);
+      if (nb_solid(A, i, a)) slot = opp(a);
       else j = yd * L.nx + xd;
     }
     mR[a] = A.lam_next[(2 * slot) * N + j];
@@ -390,7 +400,8 @@ __device__ __forceinline__ void adj_collide_body(const AdjDevT<R>& A, const int 
     const R lyy = -nxo * nxo * lk;   // d_y n_y
     for (int a = 1; a < 9; ++a) {
       const R w = R(3.0) * wgt<R>(a);
-      scatter_field(A, A.lnt_x, A.lnt_y, mapx(A, x + ex(a)), mapy(A, y + ey(a)), w * (ex(a) * lxx + ey(a) * lxy),
+      scatter_field(A, A.lnt_x, A.lnt_y, mapx(A, x + ex(a)), mapy(A, y + ey(a)), nb_solid(A, i, a),
+                    w * (ex(a) * lxx + ey(a) * lxy),
                     w * (ex(a) * lyx + ey(a) * lyy));
     }
   }
@@ -453,7 +464,7 @@ __device__ __forceinline__ void adj_normal_body(const AdjDevT<R>& A, const int i
   }
   if (lrx != R(0.0) || lry != R(0.0))
     for (int a = 1; a < 9; ++a)
-      scatter_field(A, A.lrnt, static_cast<R*>(nullptr), mapx(A, x + ex(a)), mapy(A, y + ey(a)),
+      scatter_field(A, A.lrnt, static_cast<R*>(nullptr), mapx(A, x + ex(a)), mapy(A, y + ey(a)), nb_solid(A, i, a),
                     R(3.0) * wgt<R>(a) * (ex(a) * lrx + ey(a) * lry), R(0.0));
 }
 

@@ -40,6 +40,34 @@ __host__ __device__ constexpr int sweep_width(bool /*fp64*/) { return kSweepThre
 constexpr int kSweepFMinBlocks = 5;
 constexpr int kSweepFMinBlocks16 = 7;
 
+// ------------------------------------------------------------------ device error word
+// Bits of a handle's device error word: a sweep block's wait for a staged row ran out; its
+// outstanding copies could not be drained; a range check of the checked build failed.
+enum : int { ERR_TIMEOUT = 1, ERR_DRAIN = 2, ERR_BOUNDS = 4 };
+
+// Debug build (-DLBCG_BOUNDS_CHECK): the step kernels check every population, node-array and
+// staged-row access against the extent of its buffer; a failed check sets ERR_BOUNDS in the
+// error word and the access is skipped.  In the normal build checked() is constant true and
+// the range expressions are dead code the compiler removes.
+#ifdef LBCG_BOUNDS_CHECK
+constexpr bool kBoundsCheck = true;
+#else
+constexpr bool kBoundsCheck = false;
+#endif
+// an access of `len` consecutive elements starting at i lies inside [0, n)
+__host__ __device__ __forceinline__ bool in_extent(long long i, long long len, long long n) {
+  return i >= 0 && i + len <= n;
+}
+__device__ __forceinline__ bool checked(bool ok, int* err) {
+  if constexpr (kBoundsCheck) {
+    if (!ok) atomicOr(err, ERR_BOUNDS);
+    return ok;
+  } else {
+    (void)err;
+    return true;
+  }
+}
+
 // Per-lattice constants, resident in global memory, one entry per lattice of a handle.
 struct LatDev {
   int nx, ny, pitch, bcx, bcy, in_prof;   // in_prof: 1 = Poiseuille inlet profile

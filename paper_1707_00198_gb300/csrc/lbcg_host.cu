@@ -321,10 +321,13 @@ lbcg_status check_device_error(lbcg_handle* h) {
   if (e) {
     if (cudaMemset(h->d_err, 0, sizeof(int)) != cudaSuccess)
       return cuda_fail(h, cudaGetLastError(), "clearing the device error word");
+    if (e & ERR_BOUNDS)
+      return fail(LBCG_E_BOUNDS, "a range check of the checked build failed in a step kernel (the access was "
+                                 "skipped; the state since the last check is unreliable)");
     return fail(LBCG_E_TIMEOUT,
                 "a sweep kernel's bounded wait for a staged row ran out%s; the state since the last check is "
                 "unreliable",
-                (e & 2) ? " and its copies could not be drained" : "");
+                (e & ERR_DRAIN) ? " and its copies could not be drained" : "");
   }
   return LBCG_OK;
 }
@@ -887,6 +890,7 @@ lbcg_status adjoint_run(lbcg_handle* h, const lbcg_adjoint_spec* spec, lbcg_grad
   R *lamA, *lamB, *work, *c_dev;
   R *nsx, *nsy, *ct, *st;
   int *pick0, *pick1;
+  uint8_t *sol, *nbm;
   // N-sized arrays in R.  Two sets of forward intermediates and scatter targets (a reverse
   // step computes the intermediates of the state before it): fr, fb, rr/rb/rn, gr, gc, n, dn,
   // lnt, lrnt; one set of reverse arrays: lf_r, lf_b, ln, lg, lrn.  In double: the 4
@@ -898,8 +902,25 @@ lbcg_status adjoint_run(lbcg_handle* h, const lbcg_adjoint_spec* spec, lbcg_grad
       !B.get(&lamB, 18 * (size_t)N * r8) || !B.get(&work, (size_t)kWork * N * r8) ||
       !B.get(&pwork, 4 * (size_t)N * 8) || !B.get(&c_dev, (size_t)N * r8) || !B.get(&nsx, (size_t)N * r8) ||
       !B.get(&nsy, (size_t)N * r8) || !B.get(&ct, (size_t)N * r8) || !B.get(&st, (size_t)N * r8) ||
-      !B.get(&pick0, (size_t)N * 4) || !B.get(&pick1, (size_t)N * 4))
+      !B.get(&pick0, (size_t)N * 4) || !B.get(&pick1, (size_t)N * 4) || !B.get(&sol, (size_t)N) ||
+      !B.get(&nbm, (size_t)N))
     return fail(LBCG_E_NOMEM, "adjoint buffers (%lld checkpoints of %zu bytes)", (long long)nseg, sb);
+  // compact solid flags and solid-neighbour masks of every node (the stencils' neighbour rule)
+  {
+    std::vector<uint8_t> so(N), mk(N);
+    const bool px = L.bcx == LBCG_BCX_PERIODIC, py = L.bcy == LBCG_BCY_PERIODIC;
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        uint8_t m = 0;
+        for (int a = 1; a < 9; ++a)
+          if (L.solid[(size_t)wrap_clamp(y + EYH[a], ny, py) * nx + wrap_clamp(x + EXH[a], nx, px)])
+            m |= uint8_t(1u << (a - 1));
+        so[(size_t)y * nx + x] = L.solid[(size_t)y * nx + x] ? 1 : 0;
+        mk[(size_t)y * nx + x] = m;
+      }
+    CK(h, cudaMemcpy(sol, so.data(), N, cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(nbm, mk.data(), N, cudaMemcpyHostToDevice));
+  }
   // compact normals and angles of the outermost fluid nodes
   {
     std::vector<R> a(N, R(0)), b(N, R(0)), c(N, R(1)), d(N, R(0));
@@ -926,6 +947,8 @@ lbcg_status adjoint_run(lbcg_handle* h, const lbcg_adjoint_spec* spec, lbcg_grad
   }
   A.N = N;
   A.flags = h->d_flags;
+  A.sol = sol;
+  A.nbm = nbm;
   A.src_fp32 = h->prec == LBCG_FP32 ? 1 : 0;
   // FP32 states or FP32 reverse arithmetic: pure phases carry |grad rho^N| ~ 1e-7 of rounding noise
   A.n_eps = (h->prec == LBCG_FP32 || sizeof(R) == 4) ? std::max(1e-5, L.prm.grad_eps) : L.prm.grad_eps;

@@ -81,6 +81,9 @@ struct AdjDevT {
   // 1/|g| ~ 1e8 would give the linearised map a spurious growing mode.
   double n_eps;
   const uint8_t* flags;  // node flags (pitch layout)
+  const uint8_t* sol;    // compact [ny][nx]: 1 on solid nodes
+  const uint8_t* nbm;    // compact [ny][nx], every node: bit a-1 set if its neighbour in
+                         // direction a (periodic wrap, else clamp) is solid
   const R* nsx;     // solid normal at outermost fluid nodes (compact, 0 elsewhere)
   const R* nsy;
   const R* cos_t;   // cos and sin of the contact angle per node (compact)

@@ -30,6 +30,7 @@ struct StepArgs {
   double* macro;          // 4 planes of doubles: rho_R, rho_B, u_x, u_y (macro mode)
   const uint32_t* sr_epoch;   // stochastic rounding of 16-bit stores: replay counter
   uint32_t sr_step;           // and the step within the replay (sr_key)
+  int* err;                   // device error word (range checks of the checked build)
 };
 
 // ------------------------------------------------------------------ k_wall
@@ -107,7 +108,8 @@ __global__ void __launch_bounds__(kWallThreads, sizeof(S) == 8 ? 3 : 5) k_wall(c
                                                           const WallSten* __restrict__ virt,
                                                           const WallSten* __restrict__ sten,
                                                           const OfbEntry* __restrict__ ofb, const S* __restrict__ src,
-                                                          typename Store<S>::T* __restrict__ wall, long long node_total) {
+                                                          typename Store<S>::T* __restrict__ wall, long long node_total,
+                                                          int* __restrict__ err) {
   using T = typename Store<S>::T;
   static_assert(sizeof(OfbEntry) % 16 == 0 && sizeof(WallSten) == 16, "16-byte table entries");
   __shared__ T val[kWallCap];
@@ -118,6 +120,11 @@ __global__ void __launch_bounds__(kWallThreads, sizeof(S) == 8 ? 3 : 5) k_wall(c
   __shared__ LatDev sL;
   const WallGroup G = groups[blockIdx.x];
   const int t = threadIdx.x;
+  // the group's sizes against the shared tables (uniform over the block)
+  if (!checked(G.nwall >= 0 && G.nwall <= kWallMaxNodes && G.nvirt >= 0 && G.nvirt <= kWallVirtCap &&
+                   G.nband >= 1 && (G.nband + 3) / 4 * 4 <= kWallCap && G.nband + G.nvirt <= kWallCap,
+               err))
+    return;
   // the group's tables, copied to shared memory in 16-byte pieces that are all in flight at
   // once (band0 is a multiple of 4 and the band list is padded, so the last piece is in bounds)
   {
@@ -154,7 +161,10 @@ __global__ void __launch_bounds__(kWallThreads, sizeof(S) == 8 ? 3 : 5) k_wall(c
     T fr[UW][9], fb[UW][9];
     int off[UW];
 #pragma unroll
-    for (int v = 0; v < UW; ++v) off[v] = s_band[min(i0 + v * kWallThreads, G.nband - 1)];
+    for (int v = 0; v < UW; ++v) {
+      off[v] = s_band[min(i0 + v * kWallThreads, G.nband - 1)];
+      if (!checked(in_extent(off[v], 8 * kDir + 2, 18 * sL.plane), err)) off[v] = 0;
+    }
 #pragma unroll
     for (int v = 0; v < UW; ++v) load_raw<S>(pop + off[v], r0, fr[v], fb[v]);
 #pragma unroll
@@ -182,7 +192,7 @@ __global__ void __launch_bounds__(kWallThreads, sizeof(S) == 8 ? 3 : 5) k_wall(c
       T num = T(0), den = T(0);
 #pragma unroll
       for (int b = 1; b < 9; ++b)
-        if (q.i[b - 1] != kWallNone) {
+        if (q.i[b - 1] != kWallNone && checked(q.i[b - 1] < G.nband, err)) {
           num = radd(num, rmul(wgt<T>(b), val[q.i[b - 1]]));
           den = radd(den, wgt<T>(b));
         }
@@ -191,7 +201,12 @@ __global__ void __launch_bounds__(kWallThreads, sizeof(S) == 8 ? 3 : 5) k_wall(c
     val[G.nband + j] = v;
   }
   __syncthreads();
-  for (int w = t; w < G.nwall; w += kWallThreads) wall_node<T>(sL, s_ofb[w], s_sten[w], val, wall, node_total);
+  for (int w = t; w < G.nwall; w += kWallThreads) {
+    bool ok = in_extent((long long)s_ofb[w].y * sL.pitch + s_ofb[w].x, 1, sL.plane);
+#pragma unroll
+    for (int a = 0; a < 8; ++a) ok = ok && s_sten[w].i[a] < G.nband + G.nvirt;
+    if (checked(ok, err)) wall_node<T>(sL, s_ofb[w], s_sten[w], val, wall, node_total);
+  }
 }
 
 
@@ -276,12 +291,18 @@ __global__ void __launch_bounds__(32 * TY, sizeof(typename Store<S>::T) == 4 ? 1
   __syncthreads();
   for (int i = tid; i < H3 * W3; i += NT) {
     const int cx = i % W3, cy = i / W3;
-    sfl[i] = fl[sym[cy] * pitch + sxm[cx]];
+    const long long k = (long long)sym[cy] * pitch + sxm[cx];
+    sfl[i] = checked(in_extent(k, 1, sL.plane), A.err) ? fl[k] : uint8_t(F_SOLID);
   }
   __syncthreads();
 
   auto load = [&](int c3x, int c3y, T fr_[9], T fb_[9]) {
     const int x = sxm[c3x];
+    if (!checked(in_extent(pop_node(x, sym[c3y], pitch), 8 * kDir + 2, 18 * sL.plane), A.err)) {
+#pragma unroll
+      for (int a = 0; a < 9; ++a) fr_[a] = fb_[a] = T(0);
+      return;
+    }
     load_raw<S>(src + pop_node(x, sym[c3y], pitch), r0, fr_, fb_);
     if (inout) zou_he<T>(x, nx, inlet_u<T>(sL, sym[c3y]), rho_out, fr_, fb_);
   };
@@ -352,7 +373,7 @@ __global__ void __launch_bounds__(32 * TY, sizeof(typename Store<S>::T) == 4 ? 1
     const int k = sym[c3y] * pitch + sxm[c3x];
     T ax = T(0), ay = T(0), nxv = T(0), nyv = T(0);
     if (!(f & F_SOLID)) {
-      if (f & F_OFB) {
+      if ((f & F_OFB) && checked(in_extent(k, 1, sL.plane), A.err)) {
         ax = wall[k];
         ay = wall[NTOT + k];
         nxv = wall[2 * NTOT + k];
@@ -390,6 +411,7 @@ __global__ void __launch_bounds__(32 * TY, sizeof(typename Store<S>::T) == 4 ? 1
       for (int b = 1; b < 9; ++b) {
         if (!(sfl[(c3y + ey(b)) * W3 + c3x + ex(b)] & F_SOLID)) {
           const int k2 = sym[c3y + ey(b)] * pitch + sxm[c3x + ex(b)];
+          if (!checked(in_extent(k2, 1, sL.plane), A.err)) continue;
           vx += wgt<T>(b) * wall[2 * NTOT + k2];
           vy += wgt<T>(b) * wall[3 * NTOT + k2];
           den += wgt<T>(b);
@@ -458,6 +480,7 @@ __global__ void __launch_bounds__(32 * TY, sizeof(typename Store<S>::T) == 4 ? 1
   const T uy = (jy + T(0.5) * Fy) * irho;
   const int kn = ys * pitch + xs;
   if constexpr (MACRO) {
+    if (!checked(in_extent(kn, 1, sL.plane), A.err)) return;
     const long long k = sL.node_off + kn;
     A.macro[k] = double(rhoR);
     A.macro[NTOT + k] = double(rhoB);
@@ -534,7 +557,8 @@ __global__ void __launch_bounds__(32 * TY, sizeof(typename Store<S>::T) == 4 ? 1
           k = pop_node(sxm[c3x + ex(a)], sym[c3y + ey(a)], pitch);
         }
       }
-      store_pair_sr<S>(dst + k + slot * kDir, oR, oB, wgt<T>(a) * r0, sr_bits(srh, a));
+      if (checked(in_extent((long long)k + slot * kDir, 2, 18 * sL.plane), A.err))
+        store_pair_sr<S>(dst + k + slot * kDir, oR, oB, wgt<T>(a) * r0, sr_bits(srh, a));
     }
   }
 }
@@ -683,13 +707,17 @@ __global__ void __launch_bounds__(NTH, sizeof(typename Store<S>::T) == 4 ? 1024 
     const int kn = ym2 * rowseg + colk[1];
     RawNode<S> pre;
     uint8_t mask = 0;
-    if (collide) {
+    const bool pre_ok = collide && checked(in_extent(kn, 8 * kDir + 2, 18 * sL.plane) &&
+                                               in_extent((long long)ym2 * pitch + xm, 1, sL.plane), A.err);
+    if (pre_ok) {
       pre.load(src + kn);
       mask = nbm[ym2 * pitch + xm];
     }
     // ---- stage 1: rho^N and flags of row r
     {
-      const uint8_t f = fl[ym0 * pitch + xm];
+      const bool f_ok = checked(in_extent((long long)ym0 * pitch + xm, 1, sL.plane) &&
+                                    in_extent((long long)ym0 * rowseg + colk[1], 8 * kDir + 2, 18 * sL.plane), A.err);
+      const uint8_t f = f_ok ? fl[ym0 * pitch + xm] : uint8_t(F_SOLID);
       T v = T(0);
       if (!(f & F_SOLID)) {
         T hr[9], hb[9], a1, a2;
@@ -712,7 +740,7 @@ __global__ void __launch_bounds__(NTH, sizeof(typename Store<S>::T) == 4 ? 1024 
       const uint8_t f = sfl[s1][tc];
       T ax = T(0), ay = T(0), nxv = T(0), nyv = T(0);
       if (!(f & F_SOLID)) {
-        if (f & F_OFB) {
+        if ((f & F_OFB) && checked(in_extent((long long)ym1 * pitch + kxs, 1, sL.plane), A.err)) {
           const int k = ym1 * pitch + kxs;
           ax = wall[k];
           ay = wall[NTOT + k];
@@ -752,6 +780,7 @@ __global__ void __launch_bounds__(NTH, sizeof(typename Store<S>::T) == 4 ? 1024 
         for (int b = 1; b < 9; ++b) {
           if (!(sfl[sr[ey(b) + 1]][tc + ex(b)] & F_SOLID)) {
             const int k2 = yr[ey(b) + 1] * pitch + wrap_or_clamp(sp.y - 2 + tc + ex(b), nx, px);
+            if (!checked(in_extent(k2, 1, sL.plane), A.err)) continue;
             vx += wgt<T>(b) * wall[2 * NTOT + k2];
             vy += wgt<T>(b) * wall[3 * NTOT + k2];
             den += wgt<T>(b);
@@ -857,7 +886,8 @@ __global__ void __launch_bounds__(NTH, sizeof(typename Store<S>::T) == 4 ? 1024 
       for (int a = 0; a < 9; ++a) {
         const T pert = pc * wgt<T>(a) * (T(ex(a)) * nxo + T(ey(a)) * nyo);
         const T oR = cR * fp[a] + pert;   // Eq. 14; the blue share is the rest of f'_a
-        store_pair<S>(dst + rowk[ey(a) + 1] + colk[ex(a) + 1] + a * kDir, oR, fp[a] - oR, wgt<T>(a) * r0);
+        const long long q = (long long)rowk[ey(a) + 1] + colk[ex(a) + 1] + a * kDir;
+        if (checked(in_extent(q, 2, 18 * sL.plane), A.err)) store_pair<S>(dst + q, oR, fp[a] - oR, wgt<T>(a) * r0);
       }
     } else {
       // half-way bounce-back into the opposite slot where the neighbour is solid; dropped
@@ -875,7 +905,7 @@ __global__ void __launch_bounds__(NTH, sizeof(typename Store<S>::T) == 4 ? 1024 
           if (mask & (1u << (a - 1))) k = kn + opp(a) * kDir;
           else k = rowk[ey(a) + 1] + colk[ex(a) + 1] + a * kDir;
         }
-        store_pair<S>(dst + k, oR, oB, wgt<T>(a) * r0);
+        if (checked(in_extent(k, 2, 18 * sL.plane), A.err)) store_pair<S>(dst + k, oR, oB, wgt<T>(a) * r0);
       }
     }
   }
@@ -1009,6 +1039,9 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
   const int fx0 = max(sp.y - 2, 0) & ~15;
   const unsigned fbytes = unsigned((min(sp.y + NTH - 3, nx - 1) - fx0 + 16) & ~15);
   const int fo = (xm >= fx0 && xm < fx0 + int(fbytes)) ? xm - fx0 : -1;
+  // extents of this lattice's populations and node arrays (range checks of the checked build)
+  const long long pop_n = 18 * sL.plane, node_n = sL.plane;
+  int* const err = A.err;
 
   auto map_row = [&](int v) {
     if (py) {
@@ -1035,6 +1068,13 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
   auto stage_row = [&](int y, int slot) {
     S* d = sraw + slot * (kStageSegs * kSeg);
     const S* g = src + (long long)y * rowseg;
+    if (!checked(in_extent((long long)y * rowseg + sA * kSeg, bytesA / sizeof(S), pop_n) &&
+                     bytesA <= unsigned(kStageSegs * kSeg * sizeof(S)) &&
+                     in_extent((long long)y * pitch + fx0, fbytes, node_n) && fbytes <= unsigned(NTH + 32),
+                 err)) {
+      mbar_expect_tx(&sbar[slot], 0);   // completes the phase without data
+      return;
+    }
     fence_proxy_async();
     mbar_expect_tx(&sbar[slot], bytesA + 2 * fbytes);
     bulk_copy_g2s(d, g + sA * kSeg, bytesA, &sbar[slot]);
@@ -1089,8 +1129,9 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
       // (after a lost wait this row's values are garbage: the block stops at the barrier below)
       if (!mbar_wait(&sbar[slot], (phase >> slot) & 1u, A.poll_limit)) lost = true;
       phase ^= 1u << slot;
-      const uint8_t f_r = fo >= 0 ? sfg[slot][0][fo] : fl[ym0 * pitch + xm];
-      snb[s0][t] = fo >= 0 ? sfg[slot][1][fo] : nbm[ym0 * pitch + xm];
+      const bool fl_ok = fo >= 0 || checked(in_extent((long long)ym0 * pitch + xm, 1, node_n), err);
+      const uint8_t f_r = fo >= 0 ? sfg[slot][0][fo] : (fl_ok ? fl[ym0 * pitch + xm] : uint8_t(F_SOLID));
+      snb[s0][t] = fo >= 0 ? sfg[slot][1][fo] : (fl_ok ? nbm[ym0 * pitch + xm] : uint8_t(0));
       if (!(f_r & F_SOLID)) {
         T sr, sb;
         bool done = false;
@@ -1125,8 +1166,11 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
             staged_pair<S>(row, a, lo, hi);
             decode<S, T>(lo, hi, wgt<T>(a) * r0, fr[a], fb[a]);
           }
-        } else {
+        } else if (checked(in_extent((long long)ym0 * rowseg + colk[1], 8 * kDir + 2, pop_n), err)) {
           load_raw<S>(src + ym0 * rowseg + colk[1], r0, fr, fb);
+        } else {
+#pragma unroll
+          for (int a = 0; a < 9; ++a) fr[a] = fb[a] = T(0);
         }
         if (edge) zou_he<T>(xm, nx, inlet_u<T>(sL, ym0), rho_out, fr, fb);
         V srb_ = P::add(P::mk(fr[0], fb[0]), P::mk(fr[1], fb[1]));
@@ -1159,7 +1203,7 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
       const uint8_t f = sfl[s1][tc];
       T ax = T(0), ay = T(0), nxv = T(0), nyv = T(0);
       if (!(f & F_SOLID)) {
-        if (f & F_OFB) {
+        if ((f & F_OFB) && checked(in_extent((long long)ym1 * pitch + kxs, 1, sL.plane), A.err)) {
           const long long NTOT = A.node_total;
           const T* wall = static_cast<const T*>(A.wall) + sL.node_off;
           const int k = ym1 * pitch + kxs;
@@ -1193,6 +1237,7 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
         for (int b = 1; b < 9; ++b) {
           if (!(sfl[sr[ey(b) + 1]][tc + ex(b)] & F_SOLID)) {
             const int k2 = yr[ey(b) + 1] * pitch + wrap_or_clamp(sp.y - 2 + tc + ex(b), nx, px);
+            if (!checked(in_extent(k2, 1, sL.plane), A.err)) continue;
             vx += wgt<T>(b) * wall[2 * NTOT + k2];
             vy += wgt<T>(b) * wall[3 * NTOT + k2];
             den += wgt<T>(b);
@@ -1314,6 +1359,7 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
     const T nkr0 = T(-kK) * r0;
     // the stored pair of direction a at q
     auto emit = [&](S* q, int a) {
+      if (!checked(in_extent(q - dst, 2, pop_n), err)) return;
       if constexpr (Store<S>::kDeviation) {
         Store<S>::stp_sr(q, fmaf(fp[a], T(kK), nkr0 * wgt<T>(a)), fmaf(cg, fp[a], pert[a]), sr_bits(srh, a));
       } else {
@@ -1355,10 +1401,10 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
     // row r + 1 into the other slot (if the sweep goes that far) and has not waited for it;
     // row r's slot is outstanding if this thread's own wait for it ran out (its parity bit
     // was flipped regardless, so flip it back).  Wait for each with the default bound.
-    int e = 1;
+    int e = ERR_TIMEOUT;
     const int sr = r & 1, sn = sr ^ 1;
-    if (lost && !mbar_wait(&sbar[sr], ((phase >> sr) & 1u) ^ 1u, kMbarPolls)) e |= 2;
-    if (r + 1 <= ye + 1 && !mbar_wait(&sbar[sn], (phase >> sn) & 1u, kMbarPolls)) e |= 2;
+    if (lost && !mbar_wait(&sbar[sr], ((phase >> sr) & 1u) ^ 1u, kMbarPolls)) e |= ERR_DRAIN;
+    if (r + 1 <= ye + 1 && !mbar_wait(&sbar[sn], (phase >> sn) & 1u, kMbarPolls)) e |= ERR_DRAIN;
     atomicOr(A.err, e);
   }
 }
@@ -1422,7 +1468,7 @@ static cudaError_t launch_all(const LaunchStep& p, cudaStream_t st) {
   if (p.ngroups > 0)
     k_wall<S><<<p.ngroups, kWallThreads, 0, st>>>(p.lats, p.groups, p.wband, p.wvirt, p.wsten, p.ofb,
                                                   static_cast<const S*>(p.src), static_cast<T*>(p.wall),
-                                                  p.node_total);
+                                                  p.node_total, p.err);
   rec(1);
   rec(2);
   if (p.sweep && p.macro == nullptr) {
@@ -1437,7 +1483,7 @@ static cudaError_t launch_all(const LaunchStep& p, cudaStream_t st) {
       else k_sweep<S, kSweepThreads><<<p.nstrips, kSweepThreads, 0, st>>>(B);
     }
   } else if (p.ntiles > 0) {
-    StepArgs A{p.lats, p.tiles, p.src, p.dst, p.flags, p.wall, p.node_total, p.macro, p.sr_epoch, p.sr_step};
+    StepArgs A{p.lats, p.tiles, p.src, p.dst, p.flags, p.wall, p.node_total, p.macro, p.sr_epoch, p.sr_step, p.err};
     const bool macro = p.macro != nullptr;
     switch (p.ty) {
       case 4:

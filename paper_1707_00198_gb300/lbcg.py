@@ -16,7 +16,9 @@ import numpy as np
 from .inputs import Geometry, Params
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "liblbcg.so")
+# the library this binding loads; LBCG_LIBRARY selects another build of it (e.g. the checked
+# build, liblbcg_checked.so)
+LIB_PATH = os.environ.get("LBCG_LIBRARY") or os.path.join(_HERE, "liblbcg.so")
 
 LBCG_FP64, LBCG_FP32, LBCG_FP16_STORE, LBCG_BF16_STORE = 0, 1, 2, 3
 PRECISIONS = {"fp64": LBCG_FP64, "fp32": LBCG_FP32, "fp16": LBCG_FP16_STORE, "bf16": LBCG_BF16_STORE}
@@ -24,7 +26,7 @@ STORE_BYTES = {LBCG_FP64: 8, LBCG_FP32: 4, LBCG_FP16_STORE: 2, LBCG_BF16_STORE: 
 _BCX = {"periodic": 0, "closed": 1, "inout": 2}
 _BCY = {"periodic": 0, "closed": 1}
 STATUS = {0: "LBCG_OK", 1: "LBCG_E_ARG", 2: "LBCG_E_GEOMETRY", 3: "LBCG_E_UNSTABLE_PARAM", 4: "LBCG_E_CUDA",
-          5: "LBCG_E_DIVERGED", 6: "LBCG_E_TIMEOUT", 7: "LBCG_E_UNSUPPORTED", 8: "LBCG_E_NOMEM"}
+          5: "LBCG_E_DIVERGED", 6: "LBCG_E_TIMEOUT", 7: "LBCG_E_UNSUPPORTED", 8: "LBCG_E_NOMEM", 9: "LBCG_E_BOUNDS"}
 
 
 class lbcg_geometry(C.Structure):

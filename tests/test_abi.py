@@ -88,3 +88,12 @@ def test_allocator_needs_both_callbacks(lib):
     assert lib.lbcg_set_allocator(C.byref(a)) == 1            # LBCG_E_ARG: no release callback
     assert "alloc and release" in lib.lbcg_last_error().decode()
     assert lib.lbcg_set_allocator(None) == 0
+
+
+def test_checked_build_compiles_and_exports_every_symbol():
+    """The checked build (range checks compiled into the step kernels) builds without a GPU and
+    exports the same C ABI."""
+    path = B.build(checked=True)
+    lib_c = C.CDLL(path)
+    for name in declared_functions():
+        assert hasattr(lib_c, name), name
