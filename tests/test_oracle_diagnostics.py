@@ -74,3 +74,29 @@ def test_npmt_matches_a_node_by_node_loop():
         got = OB.npmt(lat, mac, cx, cy, r, inside_red)
         assert abs(got["e_npmt"] - want) <= 1e-13 * want
         assert abs(got["m_R_in"] - sums["Ri"]) <= 1e-12 and abs(got["m_B_out"] - sums["Bo"]) <= 1e-12
+
+
+def test_circle_fit_recovers_an_exact_circle_and_the_interface_points():
+    """The algebraic circle fit (contact-angle measurement) recovers the centre and radius of
+    points lying exactly on a circle to 1e-12, whatever their spread (a slip in the moment
+    algebra or the normal equations shows up here, not only as a few degrees of angle); and
+    the interface points of a field rho^N = (R - r) clipped to [-1, 1] around that circle are
+    its linear-interpolation crossings, which lie within 0.03 of the circle for R = 9."""
+    nx, ny, xc, yc, R = 40, 30, 19.3, 12.7, 9.0
+    rng = np.random.default_rng(3)
+    for n in (3, 7, 200):
+        t = rng.uniform(0.0, 2 * math.pi, n) if n > 3 else np.array([0.1, 2.0, 4.1])
+        x, y = xc + R * np.cos(t) - nx / 2, yc + R * np.sin(t) - ny / 2
+        z = x * x + y * y
+        mom = dict(n=float(n), Sx=x.sum(), Sy=y.sum(), Sxx=(x * x).sum(), Syy=(y * y).sum(), Sxy=(x * y).sum(),
+                   Szx=(z * x).sum(), Szy=(z * y).sum(), Sz=z.sum())
+        fx, fy, fR = OB.circle_fit(mom, nx, ny)
+        assert abs(fx - xc) <= 1e-12 * nx and abs(fy - yc) <= 1e-12 * ny and abs(fR - R) <= 1e-12 * R, (n, fx, fy, fR)
+    g = I.periodic_box_droplet(nx, ny, R=0.0)
+    lat = O.make_lattice(g, math.radians(90))
+    yy, xx = np.mgrid[0:ny, 0:nx].astype(float)
+    rn = torch.from_numpy(np.clip(R - np.hypot(xx - xc, yy - yc), -1.0, 1.0))
+    mom = OB.interface_moments(lat, rn)
+    fx, fy, fR = OB.circle_fit(mom, nx, ny)
+    assert mom["n"] > 20
+    assert abs(fx - xc) <= 0.03 and abs(fy - yc) <= 0.03 and abs(fR - R) <= 0.03, (fx, fy, fR)
