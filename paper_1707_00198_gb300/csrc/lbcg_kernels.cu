@@ -980,7 +980,10 @@ __device__ __forceinline__ void staged_pair(const S* row, int a, float& lo, floa
 template <typename S, int NTH, bool kSchemeB>
 __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSweepFMinBlocks16) k_sweepf(SweepArgs A) {
   using T = float;
-  constexpr int RR = 5;   // rho^N / flags ring (rows r-4 .. r)
+  // rho^N / flag / neighbour-mask ring of rows r-2 .. r: row r takes row r-3's slot in stage 1
+  // of iteration r; row r-3's last readers were stage 2 of iteration r-1 (other threads, before
+  // that iteration's barriers) and stage 3 of iteration r-1 (only the owning thread)
+  constexpr int RR = 3;
   constexpr int RN = 3;   // n, grad ring (rows r-3 .. r-1)
   constexpr int RF = 2;   // f totals / (rho_R, rho_B) ring (rows r-2, r-1; row r is written last)
   using P = Pair<T>;
@@ -996,7 +999,7 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
   S* sraw = reinterpret_cast<S*>(sraw_bytes);
   __shared__ __align__(8) uint64_t sbar[2];
   // the staged rows' flags and neighbour-solid masks ([slot][0: flags, 1: mask][byte]), and the
-  // mask of rows r-4 .. r for the collision two rows later
+  // mask of rows r-2 .. r for the collision two rows later
   __shared__ __align__(16) uint8_t sfg[2][2][NTH + 32];
   __shared__ uint8_t snb[RR][NTH];
 
@@ -1053,7 +1056,7 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
   };
 
   int ym3 = 0, ym2 = 0, ym1 = 0, ym0 = 0;
-  int s4 = 0, s3 = 1, s2 = 2, s1 = 3, s0 = 4;
+  int s2 = 0, s1 = 1, s0 = 2;   // ring slots of rows r-2, r-1, r
   int n2 = 0, n1 = 1, n0 = 2;
   int q2 = 0, q1 = 1;   // f-total slots of rows r-2 and r-1
   // thread-private values carried between rows in registers: the f totals and (rho_R, rho_B)
@@ -1092,12 +1095,10 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
   // one row of the sweep; false once some thread of the block lost its wait for the row
   auto body = [&](const int r) -> bool {
     {
-      const int t4 = s4;
-      s4 = s3;
-      s3 = s2;
+      const int t2 = s2;
       s2 = s1;
       s1 = s0;
-      s0 = t4;
+      s0 = t2;
       const int tq = q2;
       q2 = q1;
       q1 = tq;
