@@ -241,8 +241,10 @@ lbcg_status lbcg_set_poll_limit(lbcg_handle* h, int32_t polls);
  * read those states and run in FP64 (reverse_fp32 = 0: the gradient of the trajectory's map
  * evaluated in double) or in FP32 (reverse_fp32 = 1: several times faster on this GPU, whose
  * FP64 latency dominates the reverse sweep); the per-node parameter adjoints are summed in
- * double either way.  Device memory for nsteps/checkpoint + checkpoint states and the adjoint
- * arrays is allocated for the call and freed before it returns. */
+ * double either way.  A second, internal stream recomputes the states of one segment while the
+ * handle's stream reverses the next (the call synchronises both before it returns).  Device
+ * memory for nsteps/checkpoint + 2*checkpoint states, one more wall-kernel output and the
+ * adjoint arrays is allocated for the call and freed before it returns. */
 enum { LBCG_OBJ_WEIGHTED = 0, LBCG_OBJ_FINGER_LENGTH = 1, LBCG_OBJ_RED_MASS = 2 };
 typedef struct {
   int64_t nsteps, checkpoint;

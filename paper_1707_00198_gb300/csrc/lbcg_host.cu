@@ -886,7 +886,9 @@ lbcg_status adjoint_run(lbcg_handle* h, const lbcg_adjoint_spec* spec, lbcg_grad
   const size_t sb = lbcg_state_bytes(h);
   AdjBuffers B(h);
   constexpr size_t r8 = sizeof(R);
-  double *ckpt, *seg, *pwork;
+  double *ckpt, *pwork;
+  double* segs[2];   // the states of two checkpoint segments: one recomputed while the other is reversed
+  void* wall2;       // the recompute's own wall-kernel output (it may run beside the forward pass)
   R *lamA, *lamB, *work, *c_dev;
   R *nsx, *nsy, *ct, *st;
   int *pick0, *pick1;
@@ -898,7 +900,8 @@ lbcg_status adjoint_run(lbcg_handle* h, const lbcg_adjoint_spec* spec, lbcg_grad
   const int kFwd = 9 + 9 + 3 + 2 + 2 + 2 + 4 + 2 + 1;
   const int kRev = 9 + 9 + 2 + 2 + 1;
   const int kWork = 2 * kFwd + kRev;
-  if (!B.get(&ckpt, sb * (size_t)nseg) || !B.get(&seg, sb * (size_t)K) || !B.get(&lamA, 18 * (size_t)N * r8) ||
+  if (!B.get(&ckpt, sb * (size_t)nseg) || !B.get(&segs[0], sb * (size_t)K) || !B.get(&segs[1], sb * (size_t)K) ||
+      !B.get(&wall2, 4 * (size_t)h->node_total * compute_size(h->prec)) || !B.get(&lamA, 18 * (size_t)N * r8) ||
       !B.get(&lamB, 18 * (size_t)N * r8) || !B.get(&work, (size_t)kWork * N * r8) ||
       !B.get(&pwork, 4 * (size_t)N * 8) || !B.get(&c_dev, (size_t)N * r8) || !B.get(&nsx, (size_t)N * r8) ||
       !B.get(&nsy, (size_t)N * r8) || !B.get(&ct, (size_t)N * r8) || !B.get(&st, (size_t)N * r8) ||
@@ -1000,10 +1003,133 @@ lbcg_status adjoint_run(lbcg_handle* h, const lbcg_adjoint_spec* spec, lbcg_grad
     V[q].p_hB = A.p_hB;
     V[q].p_theta = A.p_theta;
   }
-  // ---- forward with checkpoints (the handle ends at step T)
+  // ---- recompute and reverse on two streams.  The states of checkpoint segment k (its
+  // checkpoint, then K - 1 steps) depend only on checkpoint k, so a side stream recomputes
+  // segment k - 1 into one of two state buffers while the handle's stream reverses segment k
+  // from the other; ready[b] marks segs[b] recomputed, done[b] its reverse finished.  The
+  // recompute writes its own wall-kernel output (wall2), so that the last segment's recompute
+  // can also run beside the forward steps.  Each segment's launches are captured once per
+  // (kind, length, buffer, adjoint buffer parity) as a CUDA graph and replayed.
+  struct Side {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // ready[2], done[2], checkpoints taken
+    ~Side() {
+      if (st) {
+        cudaStreamSynchronize(st);
+        cudaStreamDestroy(st);
+      }
+      for (cudaEvent_t e : ev)
+        if (e) cudaEventDestroy(e);
+    }
+  } side;
+  CK(h, cudaStreamCreateWithFlags(&side.st, cudaStreamNonBlocking));
+  for (cudaEvent_t& e : side.ev) CK(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  cudaEvent_t* const ready = side.ev;
+  cudaEvent_t* const done = side.ev + 2;
+  const cudaEvent_t ck_taken = side.ev[4];
+  struct SegGraph {
+    int kind;   // 0: recompute, 1: reverse
+    int64_t ns;
+    int buf;
+    bool lam_in_a;
+    cudaGraphExec_t exec;
+  };
+  struct SegGraphs {
+    std::vector<SegGraph> v;
+    ~SegGraphs() {
+      for (SegGraph& g : v) cudaGraphExecDestroy(g.exec);
+    }
+  } graphs;
+  R* const lam_a = lamA;
+  R* const lam_b = lamB;
+  auto enqueue_recompute = [&](int64_t ns, int b) -> cudaError_t {
+    for (int64_t j = 1; j < ns; ++j) {
+      LaunchStep p = make_launch(h, 0, nullptr, 0, h->ntiles);
+      p.src = reinterpret_cast<char*>(segs[b]) + sb * (j - 1);
+      p.dst = reinterpret_cast<char*>(segs[b]) + sb * j;
+      p.wall = wall2;
+      const cudaError_t e = launch_step(h->prec, p, side.st);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  };
+  // reverse of one segment: the intermediates of its last state, then per reverse step those of
+  // the state before it, in the other set
+  auto enqueue_reverse = [&](int64_t ns, bool lam_in_a, int b) -> cudaError_t {
+    R* lc = lam_in_a ? lam_a : lam_b;
+    R* ln = lam_in_a ? lam_b : lam_a;
+    int q = 0;
+    AdjDevT<R> cur = V[q];
+    cur.src = reinterpret_cast<char*>(segs[b]) + sb * (ns - 1);
+    cudaError_t e = adjoint_forward<R>(cur, h->stream);
+    if (e != cudaSuccess) return e;
+    for (int64_t j = ns - 1; j >= 0; --j) {
+      cur = V[q];
+      cur.src = reinterpret_cast<char*>(segs[b]) + sb * j;
+      cur.lam_next = lc;
+      cur.lam = ln;
+      if (j > 0) {
+        AdjDevT<R> prev = V[q ^ 1];
+        prev.src = reinterpret_cast<char*>(segs[b]) + sb * (j - 1);
+        e = adjoint_step<R>(cur, &prev, h->stream);
+      } else {
+        e = adjoint_step<R>(cur, nullptr, h->stream);
+      }
+      if (e != cudaSuccess) return e;
+      std::swap(lc, ln);
+      q ^= 1;
+    }
+    return cudaSuccess;
+  };
+  auto replay = [&](int kind, int64_t ns, int b, bool lam_in_a, cudaStream_t st) -> lbcg_status {
+    cudaGraphExec_t exec = nullptr;
+    for (const SegGraph& g : graphs.v)
+      if (g.kind == kind && g.ns == ns && g.buf == b && g.lam_in_a == lam_in_a) exec = g.exec;
+    if (!exec) {
+      cudaGraph_t g = nullptr;
+      CK(h, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      const cudaError_t le = kind == 0 ? enqueue_recompute(ns, b) : enqueue_reverse(ns, lam_in_a, b);
+      const cudaError_t ee = cudaStreamEndCapture(st, &g);
+      if (le != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(h, le, "adjoint launch during capture");
+      }
+      if (ee != cudaSuccess) return cuda_fail(h, ee, "cudaStreamEndCapture (adjoint)");
+      const cudaError_t ie = cudaGraphInstantiate(&exec, g, 0);
+      cudaGraphDestroy(g);
+      if (ie != cudaSuccess) return cuda_fail(h, ie, "cudaGraphInstantiate (adjoint)");
+      graphs.v.push_back({kind, ns, b, lam_in_a, exec});
+    }
+    CK(h, cudaGraphLaunch(exec, st));
+    return LBCG_OK;
+  };
+  // the states of segment k into segs[k & 1], on the side stream, once that buffer's previous
+  // segment is reversed
+  auto start_recompute = [&](int64_t k) -> lbcg_status {
+    const int b = int(k & 1);
+    const int64_t ns = std::min<int64_t>(K, T - k * K);
+    CK(h, cudaStreamWaitEvent(side.st, done[b], 0));
+    CK(h, cudaMemcpyAsync(segs[b], reinterpret_cast<char*>(ckpt) + sb * k, sb, cudaMemcpyDeviceToDevice, side.st));
+    if (ns > 1) {
+      const lbcg_status r = replay(0, ns, b, false, side.st);
+      if (r != LBCG_OK) return r;
+    }
+    CK(h, cudaEventRecord(ready[b], side.st));
+    return LBCG_OK;
+  };
+  for (int b = 0; b < 2; ++b)   // the slots the push never writes
+    CK(h, cudaMemsetAsync(segs[b], 0, sb * (size_t)K, h->stream));
+  // ---- forward with checkpoints (the handle ends at step T); the last segment's recompute
+  // starts beside its forward steps
   for (int64_t k = 0; k < nseg; ++k) {
     CK(h, cudaMemcpyAsync(reinterpret_cast<char*>(ckpt) + sb * k, h->pool[h->cur], sb, cudaMemcpyDeviceToDevice,
                           h->stream));
+    if (k == nseg - 1) {
+      CK(h, cudaEventRecord(ck_taken, h->stream));
+      CK(h, cudaStreamWaitEvent(side.st, ck_taken, 0));
+      s = start_recompute(k);
+      if (s != LBCG_OK) return s;
+    }
     s = lbcg_step(h, std::min<int64_t>(K, T - k * K));
     if (s != LBCG_OK) return s;
   }
@@ -1068,79 +1194,19 @@ lbcg_status adjoint_run(lbcg_handle* h, const lbcg_adjoint_spec* spec, lbcg_grad
   S0.src = h->pool[h->cur];
   S0.lam = lamA;
   CK(h, adjoint_seed<R>(S0, c_dev, spec->objective == LBCG_OBJ_RED_MASS, h->stream));
-  // ---- reverse, one checkpoint segment at a time.  A segment's work (recompute its states
-  // from the checkpoint, then reverse its steps) is captured once per (length, adjoint
-  // buffer parity) as a CUDA graph and replayed; only the checkpoint copy is outside.
-  CK(h, cudaMemsetAsync(seg, 0, sb * (size_t)K, h->stream));   // slots the push never writes
-  auto enqueue_segment = [&](int64_t ns, bool lam_in_a) -> cudaError_t {
-    for (int64_t j = 1; j < ns; ++j) {
-      LaunchStep p = make_launch(h, 0, nullptr, 0, h->ntiles);
-      p.src = reinterpret_cast<char*>(seg) + sb * (j - 1);
-      p.dst = reinterpret_cast<char*>(seg) + sb * j;
-      cudaError_t e = launch_step(h->prec, p, h->stream);
-      if (e != cudaSuccess) return e;
-    }
-    R* lc = lam_in_a ? lamA : lamB;
-    R* ln = lam_in_a ? lamB : lamA;
-    // prologue: the intermediates of the segment's last state; then each reverse step also
-    // computes those of the state before it, in the other set
-    int q = 0;
-    AdjDevT<R> cur = V[q];
-    cur.src = reinterpret_cast<char*>(seg) + sb * (ns - 1);
-    cudaError_t e = adjoint_forward<R>(cur, h->stream);
-    if (e != cudaSuccess) return e;
-    for (int64_t j = ns - 1; j >= 0; --j) {
-      cur = V[q];
-      cur.src = reinterpret_cast<char*>(seg) + sb * j;
-      cur.lam_next = lc;
-      cur.lam = ln;
-      if (j > 0) {
-        AdjDevT<R> prev = V[q ^ 1];
-        prev.src = reinterpret_cast<char*>(seg) + sb * (j - 1);
-        e = adjoint_step<R>(cur, &prev, h->stream);
-      } else {
-        e = adjoint_step<R>(cur, nullptr, h->stream);
-      }
-      if (e != cudaSuccess) return e;
-      std::swap(lc, ln);
-      q ^= 1;
-    }
-    return cudaSuccess;
-  };
-  struct SegGraph {
-    int64_t ns;
-    bool lam_in_a;
-    cudaGraphExec_t exec;
-  };
-  struct SegGraphs {
-    std::vector<SegGraph> v;
-    ~SegGraphs() {
-      for (SegGraph& g : v) cudaGraphExecDestroy(g.exec);
-    }
-  } graphs;
+  // ---- reverse, one checkpoint segment at a time, each beside the recompute of the next
   bool lam_in_a = true;   // the seed is in lamA
   for (int64_t k = nseg - 1; k >= 0; --k) {
+    const int b = int(k & 1);
     const int64_t ns = std::min<int64_t>(K, T - k * K);
-    CK(h, cudaMemcpyAsync(seg, reinterpret_cast<char*>(ckpt) + sb * k, sb, cudaMemcpyDeviceToDevice, h->stream));
-    cudaGraphExec_t exec = nullptr;
-    for (const SegGraph& g : graphs.v)
-      if (g.ns == ns && g.lam_in_a == lam_in_a) exec = g.exec;
-    if (!exec) {
-      cudaGraph_t g = nullptr;
-      CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-      const cudaError_t le = enqueue_segment(ns, lam_in_a);
-      const cudaError_t ee = cudaStreamEndCapture(h->stream, &g);
-      if (le != cudaSuccess) {
-        if (g) cudaGraphDestroy(g);
-        return cuda_fail(h, le, "adjoint launch during capture");
-      }
-      if (ee != cudaSuccess) return cuda_fail(h, ee, "cudaStreamEndCapture (adjoint)");
-      const cudaError_t ie = cudaGraphInstantiate(&exec, g, 0);
-      cudaGraphDestroy(g);
-      if (ie != cudaSuccess) return cuda_fail(h, ie, "cudaGraphInstantiate (adjoint)");
-      graphs.v.push_back({ns, lam_in_a, exec});
+    if (k >= 1) {
+      s = start_recompute(k - 1);
+      if (s != LBCG_OK) return s;
     }
-    CK(h, cudaGraphLaunch(exec, h->stream));
+    CK(h, cudaStreamWaitEvent(h->stream, ready[b], 0));
+    s = replay(1, ns, b, lam_in_a, h->stream);
+    if (s != LBCG_OK) return s;
+    CK(h, cudaEventRecord(done[b], h->stream));
     if (ns & 1) lam_in_a = !lam_in_a;
   }
   // ---- parameter adjoints
