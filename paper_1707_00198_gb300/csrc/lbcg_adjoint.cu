@@ -573,32 +573,36 @@ __global__ void __launch_bounds__(kAdjThreads) k_fwd_dn(AdjDevT<R> A) {
   if (i < A.N) fwd_dn_body(A, i);
 }
 
-// The reverse of step j (A) in three stages, each fused with the stage of the forward
-// intermediates of the state before it (B, step j - 1) that has the same dependency on the
-// neighbours: (adj_collide, fwd_local), (adj_normal, fwd_grad), (adj_rho, fwd_dn).  A and B
+// The reverse of step j (A) in three stages, each paired in one launch with the stage of the
+// forward intermediates of the state before it (B, step j - 1) that has the same dependency on
+// the neighbours: (adj_collide, fwd_local), (adj_normal, fwd_grad), (adj_rho, fwd_dn).  A and B
 // share the reverse arrays and parameter adjoints but have their own forward intermediates
-// and scatter targets, so the two halves of a kernel touch disjoint data.  fwd = 0 for the
-// first step of a segment (the state before it is not recomputed yet).
+// and scatter targets, so the two halves of a launch touch disjoint data and run in separate
+// blocks side by side: blocks [0, nrev) take the reverse stage, the rest (none for the first
+// step of a segment, whose previous state is not recomputed yet) the forward stage.
 template <typename R>
-__global__ void __launch_bounds__(kAdjThreads) k_rev_collide(AdjDevT<R> A, AdjDevT<R> B, int fwd) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(kAdjThreads) k_rev_collide(AdjDevT<R> A, AdjDevT<R> B, int nrev) {
+  const bool rev = int(blockIdx.x) < nrev;
+  const int i = (rev ? blockIdx.x : blockIdx.x - nrev) * blockDim.x + threadIdx.x;
   if (i >= A.N) return;
-  adj_collide_body(A, i);
-  if (fwd) fwd_local_body(B, i);
+  if (rev) adj_collide_body(A, i);
+  else fwd_local_body(B, i);
 }
 template <typename R>
-__global__ void __launch_bounds__(kAdjThreads) k_rev_normal(AdjDevT<R> A, AdjDevT<R> B, int fwd) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(kAdjThreads) k_rev_normal(AdjDevT<R> A, AdjDevT<R> B, int nrev) {
+  const bool rev = int(blockIdx.x) < nrev;
+  const int i = (rev ? blockIdx.x : blockIdx.x - nrev) * blockDim.x + threadIdx.x;
   if (i >= A.N) return;
-  adj_normal_body(A, i);
-  if (fwd) fwd_grad_body(B, i);
+  if (rev) adj_normal_body(A, i);
+  else fwd_grad_body(B, i);
 }
 template <typename R>
-__global__ void __launch_bounds__(kAdjThreads) k_rev_rho(AdjDevT<R> A, AdjDevT<R> B, int fwd) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(kAdjThreads) k_rev_rho(AdjDevT<R> A, AdjDevT<R> B, int nrev) {
+  const bool rev = int(blockIdx.x) < nrev;
+  const int i = (rev ? blockIdx.x : blockIdx.x - nrev) * blockDim.x + threadIdx.x;
   if (i >= A.N) return;
-  adj_rho_body(A, i);
-  if (fwd) fwd_dn_body(B, i);
+  if (rev) adj_rho_body(A, i);
+  else fwd_dn_body(B, i);
 }
 template <typename R>
 __global__ void __launch_bounds__(kAdjThreads) k_adj_rho(AdjDevT<R> A) {
@@ -651,10 +655,10 @@ template <typename R>
 cudaError_t adjoint_step(const AdjDevT<R>& A, const AdjDevT<R>* B, cudaStream_t st) {
   const int b = nblk(A.N);
   const AdjDevT<R>& Bv = B ? *B : A;
-  const int fwd = B ? 1 : 0;
-  k_rev_collide<R><<<b, kAdjThreads, 0, st>>>(A, Bv, fwd);
-  k_rev_normal<R><<<b, kAdjThreads, 0, st>>>(A, Bv, fwd);
-  k_rev_rho<R><<<b, kAdjThreads, 0, st>>>(A, Bv, fwd);
+  const int g = B ? 2 * b : b;
+  k_rev_collide<R><<<g, kAdjThreads, 0, st>>>(A, Bv, b);
+  k_rev_normal<R><<<g, kAdjThreads, 0, st>>>(A, Bv, b);
+  k_rev_rho<R><<<g, kAdjThreads, 0, st>>>(A, Bv, b);
   return cudaGetLastError();
 }
 
