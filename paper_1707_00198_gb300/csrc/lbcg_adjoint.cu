@@ -17,9 +17,10 @@
 //                 Eq. 28/29 applied to rho^N (a scatter);
 //   adj_rho     : reverse of Eq. 12 and 16, then of the Zou-He columns -> lambda.
 // The three forward stages of step j - 1 have the same neighbour dependencies as the three
-// reverse stages of step j, so a reverse step runs as three kernels, each doing one reverse
-// stage of step j and one forward stage of step j - 1 (double-buffered intermediates); only
-// the first reversed step of a checkpoint segment needs the three forward kernels alone.
+// reverse stages of step j, so a reverse step runs as three launches, each with one reverse
+// stage of step j and, in separate blocks beside it, one forward stage of step j - 1
+// (double-buffered intermediates); only the first reversed step of a checkpoint segment needs
+// the three forward kernels alone.
 // A value that a stencil reads on a solid neighbour is that node's Eq. 29 virtual value, a
 // weighted mean of its own fluid neighbours; the transpose scatters straight through that
 // mean onto those fluid nodes.  The kernels are templates on their arithmetic R: double, or

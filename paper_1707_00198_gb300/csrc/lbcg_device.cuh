@@ -39,6 +39,10 @@ __host__ __device__ constexpr int sweep_width(bool /*fp64*/) { return kSweepThre
 // FP32 storage and 16-bit storage
 constexpr int kSweepFMinBlocks = 5;
 constexpr int kSweepFMinBlocks16 = 7;
+// set in a strip's lattice index (int4 .x): k_sweepf walks that segment from its top row down
+// (its results are the same either way; neighbouring segments of a strip alternate, so both
+// reach their shared boundary rows at about the same time and the second read hits L2)
+constexpr int kStripDown = 1 << 30;
 
 // ------------------------------------------------------------------ device error word
 // Bits of a handle's device error word: a sweep block's wait for a staged row ran out; its

@@ -226,13 +226,17 @@ void build_strips(lbcg_handle* h, std::vector<int4>& strips) {
       const long long k = nx_strips >= target ? 1 : (target + nx_strips - 1) / nx_strips;
       rows = int(std::max<long long>(min_rows, (L.ny + k - 1) / k));
     }
+    // the FP32-arithmetic sweep walks every other segment of a strip downwards, so that the
+    // two segments at each boundary reach its rows at about the same time (their second read
+    // then hits L2); neighbouring strips keep the same pattern and run side by side
     for (int x0 = 0; x0 < L.nx; x0 += W)
-      for (int y0 = 0; y0 < L.ny; y0 += rows) {
+      for (int y0 = 0, k = 0; y0 < L.ny; y0 += rows, ++k) {
         const int y1 = std::min(y0 + rows, L.ny);
         bool any = false;
         for (int y = y0; y < y1 && !any; ++y)
           for (int x = x0; x < std::min(x0 + W, L.nx) && !any; ++x) any = L.solid[(size_t)y * L.nx + x] == 0;
-        if (any) strips.push_back(make_int4(int(l), x0, y0, y1));
+        const int down = (!fp64 && (k & 1)) ? kStripDown : 0;
+        if (any) strips.push_back(make_int4(int(l) | down, x0, y0, y1));
       }
   }
 }

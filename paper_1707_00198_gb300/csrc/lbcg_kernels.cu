@@ -624,7 +624,7 @@ __global__ void __launch_bounds__(NTH, sizeof(typename Store<S>::T) == 4 ? 1024 
 
   const int4 sp = A.strips[blockIdx.x];
   const int t = threadIdx.x;
-  if (t == 0) sL = A.lats[sp.x];
+  if (t == 0) sL = A.lats[sp.x & ~kStripDown];
   __syncthreads();
   const int nx = sL.nx, ny = sL.ny, pitch = sL.pitch;
   const bool px = sL.bcx == BC_PERIODIC, py = sL.bcy == BC_PERIODIC, inout = sL.bcx == BC_INOUT;
@@ -1005,7 +1005,8 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
 
   const int4 sp = A.strips[blockIdx.x];
   const int t = threadIdx.x;
-  if (t == 0) sL = A.lats[sp.x];
+  const bool down = (sp.x & kStripDown) != 0;
+  if (t == 0) sL = A.lats[sp.x & ~kStripDown];
   __syncthreads();
   const int nx = sL.nx, ny = sL.ny, pitch = sL.pitch;
   const bool px = sL.bcx == BC_PERIODIC, py = sL.bcy == BC_PERIODIC, inout = sL.bcx == BC_INOUT;
@@ -1028,6 +1029,11 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
   const bool interior = t >= 2 && t < NTH - 2 && cx < nx;
   const bool edge = inout && (xm == 0 || xm == nx - 1);
   const int ys = sp.z, ye = sp.w;
+  // the sweep runs over rows r = ys - 2 .. ye + 1 in this order; yrow(r) is the lattice row
+  // (before wrapping) that sweep row r stands for: r itself, or the mirror image in the
+  // segment for a downward sweep, whose stencils then take row r - 1 of the sweep as y + 1
+  const int yflip = ys + ye - 1;
+  auto yrow = [&](int r) { return down ? yflip - r : r; };
   const int colk[3] = {(xl >> 5) * kSeg + (xl & 31) * 2, (xm >> 5) * kSeg + (xm & 31) * 2,
                        (xr >> 5) * kSeg + (xr & 31) * 2};
   const int rowseg = (pitch >> 5) * kSeg;
@@ -1090,7 +1096,7 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
     mbar_init_fence();
   }
   __syncthreads();
-  if (t == 0) stage_row(map_row(ys - 2), (ys - 2) & 1);
+  if (t == 0) stage_row(map_row(yrow(ys - 2)), (ys - 2) & 1);
 
   // one row of the sweep; false once some thread of the block lost its wait for the row
   auto body = [&](const int r) -> bool {
@@ -1104,20 +1110,20 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
       q1 = tq;
       g_old = g_new;
       if (r == ys - 2) {
-        ym3 = map_row(r - 3);
-        ym2 = map_row(r - 2);
-        ym1 = map_row(r - 1);
+        ym3 = map_row(yrow(r - 3));
+        ym2 = map_row(yrow(r - 2));
+        ym1 = map_row(yrow(r - 1));
       } else {
         ym3 = ym2;
         ym2 = ym1;
         ym1 = ym0;
       }
-      ym0 = map_row(r);
+      ym0 = map_row(yrow(r));
     }
     // the next row's populations (bulk copy) and flag travel while this row is processed;
     // its slot held row r - 1, whose last reader finished before the previous barriers
     if (r + 1 <= ye + 1) {
-      const int y = map_row(r + 1);
+      const int y = map_row(yrow(r + 1));
       if (t == 0) stage_row(y, (r + 1) & 1);
     }
     const int p = r - 2;
@@ -1213,9 +1219,9 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
           nxv = wall[2 * NTOT + k];
           nyv = wall[3 * NTOT + k];
         } else {
-          const T* rm = srn[s2];
+          const T* rm = srn[down ? s0 : s2];   // rows y - 1, y, y + 1
           const T* rc = srn[s1];
-          const T* rp = srn[s0];
+          const T* rp = srn[down ? s2 : s0];
           const T w1 = T(1.0 / 9.0), w2 = T(1.0 / 36.0);
           ax = w1 * (rc[tc + 1] - rc[tc - 1]) + w2 * (rp[tc + 1] - rp[tc - 1] + rm[tc + 1] - rm[tc - 1]);
           ay = w1 * (rp[tc] - rm[tc]) + w2 * (rp[tc + 1] + rp[tc - 1] - rm[tc - 1] - rm[tc + 1]);
@@ -1232,8 +1238,8 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
         const long long NTOT = A.node_total;
         const T* wall = static_cast<const T*>(A.wall) + sL.node_off;
         T vx = T(0), vy = T(0), den = T(0);
-        const int yr[3] = {ym2, ym1, ym0};
-        const int sr[3] = {s2, s1, s0};
+        const int yr[3] = {down ? ym0 : ym2, ym1, down ? ym2 : ym0};   // rows y - 1, y, y + 1
+        const int sr[3] = {down ? s0 : s2, s1, down ? s2 : s0};
 #pragma unroll
         for (int b = 1; b < 9; ++b) {
           if (!(sfl[sr[ey(b) + 1]][tc + ex(b)] & F_SOLID)) {
@@ -1262,9 +1268,9 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
     const V rb = srb[q2][t];
     const T rhoR = rb.x, rhoB = rb.y, rn = srn[s2][t];
     // grad n (Eq. 28), curvature (Eq. 13), force (Eq. 10)
-    const V* nm = sn[n2];
+    const V* nm = sn[down ? n0 : n2];   // n of rows y - 1, y, y + 1
     const V* n0v = sn[n1];
-    const V* np = sn[n0];
+    const V* np = sn[down ? n2 : n0];
     const V W1 = P::mk(T(1.0 / 9.0), T(1.0 / 9.0)), W2 = P::mk(T(1.0 / 36.0), T(1.0 / 36.0));
     const V nm_l = nm[t - 1], nm_c = nm[t], nm_r = nm[t + 1];
     const V n0_l = n0v[t - 1], n0_c = n0v[t], n0_r = n0v[t + 1];
@@ -1353,7 +1359,7 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
     pert[7] = -pert[5];
     pert[6] = -pert[8];
     const int kn = ym2 * rowseg + colk[1];
-    const int rowk[3] = {ym3 * rowseg, ym2 * rowseg, ym1 * rowseg};
+    const int rowk[3] = {(down ? ym1 : ym3) * rowseg, ym2 * rowseg, (down ? ym3 : ym1) * rowseg};   // y - 1, y, y + 1
     uint32_t srh = 0;
     if constexpr (Store<S>::kDeviation) srh = sr_node(srk, kn);
     const T cg = fmaf(cR, T(2.0f * kK), T(-kK));   // K (2 cR - 1), deviation storage only
@@ -1373,7 +1379,8 @@ __global__ void __launch_bounds__(NTH, sizeof(S) == 4 ? kSweepFMinBlocks : kSwee
       for (int a = 0; a < 9; ++a) emit(dst + rowk[ey(a) + 1] + colk[ex(a) + 1] + a * kDir, a);
     } else {
       const bool okx[3] = {px || cx - 1 >= 0, true, px || cx + 1 < nx};
-      const bool oky[3] = {py || p - 1 >= 0, true, py || p + 1 < ny};
+      const int yp = yrow(p);
+      const bool oky[3] = {py || yp - 1 >= 0, true, py || yp + 1 < ny};
 #pragma unroll
       for (int a = 0; a < 9; ++a) {
         int k = kn + a * kDir;
