@@ -48,6 +48,7 @@ template <typename R>
 __device__ __forceinline__ bool nb_solid(const AdjDevT<R>& A, int j, int a) {
   return (A.nbm[j] >> (a - 1)) & 1u;
 }
+__device__ __forceinline__ bool mask_bit(unsigned m, int a) { return (m >> (a - 1)) & 1u; }
 template <typename R>
 __device__ __forceinline__ uint8_t flag_at(const AdjDevT<R>& A, int x, int y) {
   return A.flags[A.L.node_off + (long long)y * A.L.pitch + x];
@@ -62,12 +63,11 @@ template <typename R>
 __device__ __forceinline__ void fwd_local_body(const AdjDevT<R>& A, const int i) {
   const int x = i % A.L.nx, y = i / A.L.nx;
   const int N = A.N;
+  // The kernels of the reverse sweep run a few warps per SM, so each memory round trip on a
+  // thread's path counts: a node's loads are issued together, before its solid test (the
+  // slots of a solid node are read but not used).
+  const bool solid = is_solid(A, x, y);
   A.lnt_x[i] = A.lnt_y[i] = A.lrnt[i] = R(0.0);
-  if (is_solid(A, x, y)) {
-    for (int a = 0; a < 9; ++a) A.fr[a * N + i] = A.fb[a * N + i] = R(0.0);
-    A.rr[i] = A.rb[i] = A.rn[i] = R(0.0);
-    return;
-  }
   R fr[9], fb[9], rR, rB;
   if (A.src_fp32) {
     // FP32 forward: its post-Zou-He populations, converted to the reverse arithmetic
@@ -84,6 +84,11 @@ __device__ __forceinline__ void fwd_local_body(const AdjDevT<R>& A, const int i)
       fr[a] = R(fr64[a]);
       fb[a] = R(fb64[a]);
     }
+  }
+  if (solid) {
+    for (int a = 0; a < 9; ++a) A.fr[a * N + i] = A.fb[a * N + i] = R(0.0);
+    A.rr[i] = A.rb[i] = A.rn[i] = R(0.0);
+    return;
   }
   for (int a = 0; a < 9; ++a) {
     A.fr[a * N + i] = fr[a];
@@ -149,6 +154,9 @@ template <typename R>
 __device__ __forceinline__ void fwd_grad_body(const AdjDevT<R>& A, const int i) {
   const int x = i % A.L.nx, y = i / A.L.nx;
   const uint8_t f = flag_at(A, x, y);
+  const unsigned msk = A.nbm[i];
+  const R nsx = A.nsx[i], nsy = A.nsy[i];
+  const R c = A.cos_t[i], s = A.sin_t[i];
   A.pick[i] = 0;
   if (f & F_SOLID) {
     A.grx[i] = A.gry[i] = A.gcx[i] = A.gcy[i] = R(0.0);
@@ -157,7 +165,7 @@ __device__ __forceinline__ void fwd_grad_body(const AdjDevT<R>& A, const int i) 
   }
   R gx = R(0.0), gy = R(0.0);
   for (int a = 1; a < 9; ++a) {
-    const R t = rmul(wgt<R>(a), read_field(A, A.rn, mapx(A, x + ex(a)), mapy(A, y + ey(a)), nb_solid(A, i, a)));
+    const R t = rmul(wgt<R>(a), read_field(A, A.rn, mapx(A, x + ex(a)), mapy(A, y + ey(a)), mask_bit(msk, a)));
     if (ex(a) == 1) gx = radd(gx, t);
     if (ex(a) == -1) gx = radd(gx, -t);
     if (ey(a) == 1) gy = radd(gy, t);
@@ -172,8 +180,6 @@ __device__ __forceinline__ void fwd_grad_body(const AdjDevT<R>& A, const int i) 
   const R mag = rsqrt_(radd(rmul(gx, gx), rmul(gy, gy)));
   if ((f & F_OFB) && mag > eps) {
     const R esx = rdiv(gx, mag), esy = rdiv(gy, mag);
-    const R nsx = A.nsx[i], nsy = A.nsy[i];
-    const R c = A.cos_t[i], s = A.sin_t[i];
     const R f1x = rsub(rmul(nsx, c), rmul(nsy, s)), f1y = radd(rmul(nsx, s), rmul(nsy, c));
     const R f2x = radd(rmul(nsx, c), rmul(nsy, s)), f2y = radd(rmul(-nsx, s), rmul(nsy, c));
     const R a1 = rsub(f1x, esx), b1 = rsub(f1y, esy), a2 = rsub(f2x, esx), b2 = rsub(f2y, esy);
@@ -196,10 +202,12 @@ __device__ __forceinline__ void fwd_dn_body(const AdjDevT<R>& A, const int i) {
   const int x = i % A.L.nx, y = i / A.L.nx;
   const int N = A.N;
   R d[4] = {0, 0, 0, 0};
-  if (!is_solid(A, x, y)) {
+  const bool solid = is_solid(A, x, y);
+  const unsigned msk = A.nbm[i];
+  if (!solid) {
     for (int a = 1; a < 9; ++a) {
       const int x2 = mapx(A, x + ex(a)), y2 = mapy(A, y + ey(a));
-      const bool sn = nb_solid(A, i, a);
+      const bool sn = mask_bit(msk, a);
       const R tx = wgt<R>(a) * read_field(A, A.nxv, x2, y2, sn);
       const R ty = wgt<R>(a) * read_field(A, A.nyv, x2, y2, sn);
       d[0] += ex(a) * tx;
@@ -219,9 +227,26 @@ __device__ __forceinline__ void adj_collide_body(const AdjDevT<R>& A, const int 
   const int x = i % A.L.nx, y = i / A.L.nx;
   const int N = A.N;
   const LatDev& L = A.L;
-  for (int a = 0; a < 9; ++a) A.lf_r[a * N + i] = A.lf_b[a * N + i] = R(0.0);
-  A.ln_x[i] = A.ln_y[i] = A.lg_x[i] = A.lg_y[i] = A.lrn[i] = R(0.0);
-  if (is_solid(A, x, y)) return;
+  // the node's masks, forward intermediates and parameter adjoints so far, all in flight
+  // together before the solid test
+  const bool solid = is_solid(A, x, y);
+  const unsigned msk = A.nbm[i];
+  R fr[9], fb[9], f[9];
+  for (int a = 0; a < 9; ++a) {
+    fr[a] = A.fr[a * N + i];
+    fb[a] = A.fb[a * N + i];
+    f[a] = fr[a] + fb[a];
+  }
+  const R rhoR = A.rr[i], rhoB = A.rb[i], rn = A.rn[i];
+  const R nxo = A.nxv[i], nyo = A.nyv[i];
+  const R gx = A.gcx[i], gy = A.gcy[i];
+  const R dxx = A.dn[i], dxy = A.dn[N + i], dyx = A.dn[2 * N + i], dyy = A.dn[3 * N + i];
+  const double p_hR0 = A.p_hR[i], p_hB0 = A.p_hB[i], p_sigma0 = A.p_sigma[i];
+  if (solid) {
+    for (int a = 0; a < 9; ++a) A.lf_r[a * N + i] = A.lf_b[a * N + i] = R(0.0);
+    A.ln_x[i] = A.ln_y[i] = A.lg_x[i] = A.lg_y[i] = A.lrn[i] = R(0.0);
+    return;
+  }
   const bool px = L.bcx == BC_PERIODIC, py = L.bcy == BC_PERIODIC;
   // adjoint of the post-collision, recoloured values (oR_a, oB_a) leaving this node
   R mR[9], mB[9];
@@ -232,24 +257,14 @@ __device__ __forceinline__ void adj_collide_body(const AdjDevT<R>& A, const int 
       const int xr = x + ex(a), yr = y + ey(a);
       if ((!px && (xr < 0 || xr >= L.nx)) || (!py && (yr < 0 || yr >= L.ny))) continue;
       const int xd = mapx(A, xr), yd = mapy(A, yr);
-      if (nb_solid(A, i, a)) slot = opp(a);
+      if (mask_bit(msk, a)) slot = opp(a);
       else j = yd * L.nx + xd;
     }
     mR[a] = A.lam_next[(2 * slot) * N + j];
     mB[a] = A.lam_next[(2 * slot + 1) * N + j];
   }
   // forward recomputation of the node-local quantities
-  R fr[9], fb[9], f[9];
-  for (int a = 0; a < 9; ++a) {
-    fr[a] = A.fr[a * N + i];
-    fb[a] = A.fb[a * N + i];
-    f[a] = fr[a] + fb[a];
-  }
-  const R rhoR = A.rr[i], rhoB = A.rb[i], rn = A.rn[i];
   const R rho = rhoR + rhoB, ir = R(1.0) / rho;
-  const R nxo = A.nxv[i], nyo = A.nyv[i];
-  const R gx = A.gcx[i], gy = A.gcy[i];
-  const R dxx = A.dn[i], dxy = A.dn[N + i], dyx = A.dn[2 * N + i], dyy = A.dn[3 * N + i];
   const R kappa = -nxo * nxo * dyy - nyo * nyo * dxx + nxo * nyo * (dxy + dyx);
   const R hsk = R(0.5) * R(L.sigma) * kappa;
   const R Fx = hsk * gx, Fy = hsk * gy;
@@ -377,8 +392,8 @@ __device__ __forceinline__ void adj_collide_body(const AdjDevT<R>& A, const int 
   // sv = inv_nu / (3 + inv_nu / 2); inv_nu = (1 + rn) hR + (1 - rn) hB
   const R linv = lsv * R(3.0) / (den_sv * den_sv);
   R lrn_loc = (R(L.h_inv_nuR) - R(L.h_inv_nuB)) * linv;
-  A.p_hR[i] += (1 + rn) * linv;
-  A.p_hB[i] += (1 - rn) * linv;
+  A.p_hR[i] = p_hR0 + (1 + rn) * linv;
+  A.p_hB[i] = p_hB0 + (1 - rn) * linv;
   // u = (j + F/2) / rho
   const R ljx = lux * ir, ljy = luy * ir;
   lFx += R(0.5) * ljx;
@@ -388,7 +403,7 @@ __device__ __forceinline__ void adj_collide_body(const AdjDevT<R>& A, const int 
   // F = (sigma kappa / 2) g
   const R lhsk = gx * lFx + gy * lFy;
   const R lgx = hsk * lFx, lgy = hsk * lFy;
-  A.p_sigma[i] += R(0.5) * kappa * lhsk;
+  A.p_sigma[i] = p_sigma0 + R(0.5) * kappa * lhsk;
   const R lk = R(0.5) * R(L.sigma) * lhsk;
   // kappa = -nx^2 dyy - ny^2 dxx + nx ny (dxy + dyx)
   lnx += (-2 * nxo * dyy + nyo * (dxy + dyx)) * lk;
@@ -401,7 +416,7 @@ __device__ __forceinline__ void adj_collide_body(const AdjDevT<R>& A, const int 
     const R lyy = -nxo * nxo * lk;   // d_y n_y
     for (int a = 1; a < 9; ++a) {
       const R w = R(3.0) * wgt<R>(a);
-      scatter_field(A, A.lnt_x, A.lnt_y, mapx(A, x + ex(a)), mapy(A, y + ey(a)), nb_solid(A, i, a),
+      scatter_field(A, A.lnt_x, A.lnt_y, mapx(A, x + ex(a)), mapy(A, y + ey(a)), mask_bit(msk, a),
                     w * (ex(a) * lxx + ey(a) * lxy),
                     w * (ex(a) * lyx + ey(a) * lyy));
     }
@@ -426,11 +441,20 @@ __device__ __forceinline__ void adj_collide_body(const AdjDevT<R>& A, const int 
 template <typename R>
 __device__ __forceinline__ void adj_normal_body(const AdjDevT<R>& A, const int i) {
   const int x = i % A.L.nx, y = i / A.L.nx;
-  if (is_solid(A, x, y)) return;
+  // everything the node reads, in flight together before the solid test
+  const bool solid = is_solid(A, x, y);
+  const unsigned msk = A.nbm[i];
   const R lnx = A.ln_x[i] + A.lnt_x[i], lny = A.ln_y[i] + A.lnt_y[i];
   R lgx = A.lg_x[i], lgy = A.lg_y[i];
+  const R gcx = A.gcx[i], gcy = A.gcy[i];
+  const int pick = A.pick[i];
+  const R grx = A.grx[i], gry = A.gry[i];
+  const R nsx = A.nsx[i], nsy = A.nsy[i];
+  const R c = A.cos_t[i], s = A.sin_t[i];
+  const double p_theta0 = A.p_theta[i];
+  if (solid) return;
   {
-    const R gx = A.gcx[i], gy = A.gcy[i];
+    const R gx = gcx, gy = gcy;
     const R m = sqrt(gx * gx + gy * gy);
     if (m > A.n_eps) {   // below it n is frozen in the reverse sweep (see AdjDev::n_eps)
       const R im = R(1.0) / m, nx = gx * im, ny = gy * im;
@@ -440,12 +464,9 @@ __device__ __forceinline__ void adj_normal_body(const AdjDevT<R>& A, const int i
     }
   }
   R lrx = lgx, lry = lgy;
-  const int pick = A.pick[i];
   if (pick != 0) {
-    const R gx = A.grx[i], gy = A.gry[i];
+    const R gx = grx, gy = gry;
     const R m = sqrt(gx * gx + gy * gy);
-    const R nsx = A.nsx[i], nsy = A.nsy[i];
-    const R c = A.cos_t[i], s = A.sin_t[i];
     R nfx, nfy, dfx, dfy;
     if (pick == 1) {   // rotation by +theta; d n_f / d theta = (-n_fy, n_fx)
       nfx = nsx * c - nsy * s;
@@ -461,11 +482,11 @@ __device__ __forceinline__ void adj_normal_body(const AdjDevT<R>& A, const int i
     const R proj = (nfx * lgx + nfy * lgy) / m;
     lrx = gx * proj;
     lry = gy * proj;
-    A.p_theta[i] += m * (dfx * lgx + dfy * lgy);
+    A.p_theta[i] = p_theta0 + m * (dfx * lgx + dfy * lgy);
   }
   if (lrx != R(0.0) || lry != R(0.0))
     for (int a = 1; a < 9; ++a)
-      scatter_field(A, A.lrnt, static_cast<R*>(nullptr), mapx(A, x + ex(a)), mapy(A, y + ey(a)), nb_solid(A, i, a),
+      scatter_field(A, A.lrnt, static_cast<R*>(nullptr), mapx(A, x + ex(a)), mapy(A, y + ey(a)), mask_bit(msk, a),
                     R(3.0) * wgt<R>(a) * (ex(a) * lrx + ey(a) * lry), R(0.0));
 }
 
@@ -474,16 +495,25 @@ template <typename R>
 __device__ __forceinline__ void adj_rho_body(const AdjDevT<R>& A, const int i) {
   const int x = i % A.L.nx, y = i / A.L.nx;
   const int N = A.N;
-  for (int a = 0; a < 18; ++a) A.lam[a * N + i] = R(0.0);
-  if (is_solid(A, x, y)) return;
+  // the node's inputs, in flight together before the solid test
+  const bool solid = is_solid(A, x, y);
   const R lrn = A.lrn[i] + A.lrnt[i];
-  const R rR = A.rr[i], rB = A.rb[i], rho = rR + rB;
-  const R ir2 = R(1.0) / (rho * rho);
-  const R cR = 2 * rB * ir2 * lrn, cB = -2 * rR * ir2 * lrn;
+  const R rR = A.rr[i], rB = A.rb[i];
   R lr[9], lb[9];
   for (int a = 0; a < 9; ++a) {
-    lr[a] = A.lf_r[a * N + i] + cR;
-    lb[a] = A.lf_b[a * N + i] + cB;
+    lr[a] = A.lf_r[a * N + i];
+    lb[a] = A.lf_b[a * N + i];
+  }
+  if (solid) {
+    for (int a = 0; a < 18; ++a) A.lam[a * N + i] = R(0.0);
+    return;
+  }
+  const R rho = rR + rB;
+  const R ir2 = R(1.0) / (rho * rho);
+  const R cR = 2 * rB * ir2 * lrn, cB = -2 * rR * ir2 * lrn;
+  for (int a = 0; a < 9; ++a) {
+    lr[a] += cR;
+    lb[a] += cB;
   }
   const LatDev& L = A.L;
   R sr[9], sb[9];   // adjoint of the stored values
