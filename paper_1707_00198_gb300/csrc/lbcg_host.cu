@@ -98,6 +98,15 @@ struct lbcg_handle {
   int nofb = 0;
   double* d_obs = nullptr;   // partials then outputs
   cudaGraphExec_t graph = nullptr;
+  // batches: the captured graph runs the lattices [0, split) and [split, n) as two parallel
+  // branches, so that one half's wall kernel runs beside the other half's bulk kernel (the
+  // lattices are independent); 0 = one branch.  First strip / tile / wall group of the second
+  // half, and the second branch's capture stream and fork / join events.
+  int split = 0;
+  int split_strip = 0, split_tile = 0, split_group = 0;
+  std::vector<int> group_lat;   // lattice of each wall group
+  cudaStream_t stream2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::vector<uint8_t> flags_host;
   std::vector<OfbEntry> ofb_host;
   bool profiling = false;
@@ -271,6 +280,18 @@ LaunchStep make_launch(lbcg_handle* h, int src, double* macro, int tile_begin, i
   return p;
 }
 
+// the launch of one branch of a split graph: lattices [0, split) (half 0) or [split, n)
+LaunchStep make_launch_half(lbcg_handle* h, int src, int half) {
+  LaunchStep p = make_launch(h, src, nullptr, half ? h->split_tile : 0, half ? h->ntiles : h->split_tile);
+  const int s0 = half ? h->split_strip : 0, s1 = half ? h->nstrips : h->split_strip;
+  const int g0 = half ? h->split_group : 0, g1 = half ? h->ngroups : h->split_group;
+  p.strips = h->d_strips + s0;
+  p.nstrips = s1 - s0;
+  p.groups = h->d_groups + g0;
+  p.ngroups = g1 - g0;
+  return p;
+}
+
 void free_handle(lbcg_handle* h) {
   if (!h) return;
   if (h->graph) cudaGraphExecDestroy(h->graph);
@@ -280,6 +301,9 @@ void free_handle(lbcg_handle* h) {
                   h->d_obs,   h->d_strips, h->d_nbmask, h->d_err, h->d_usnap, h->d_sr_epoch};
   if (h->stream) cudaStreamSynchronize(h->stream);
   for (void* p : ptrs) dev_free(h, p);
+  if (h->stream2) cudaStreamDestroy(h->stream2);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }
@@ -302,6 +326,40 @@ lbcg_status upload_tiles(lbcg_handle* h) {
     return fail(LBCG_E_NOMEM, "cannot allocate the strip list");
   if (!strips.empty())
     CK(h, cudaMemcpy(h->d_strips, strips.data(), strips.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  // the split of a batch into two graph branches of about equal node counts; strips, tiles and
+  // wall groups are all in lattice order, so each half is a contiguous range of each list
+  h->split = 0;
+  const int n = int(h->lats.size());
+  if (n >= 2) {
+    auto nodes = [&](int l) { return (long long)h->lats[l].nx * h->lats[l].ny; };
+    long long total = 0, acc = 0;
+    for (int l = 0; l < n; ++l) total += nodes(l);
+    // the first half: lattices [0, k) with acc = their nodes closest to total / 2, 1 <= k < n
+    int k = 0;
+    while (k < n - 1 && 2 * (acc + nodes(k)) <= total) acc += nodes(k++);
+    if (k < n - 1 && total - 2 * acc > 2 * (acc + nodes(k)) - total) acc += nodes(k++);
+    k = std::max(k, 1);
+    auto first = [&](const std::vector<int4>& v) {
+      int i = 0;
+      while (i < int(v.size()) && (v[i].x & ~kStripDown) < k) ++i;
+      return i;
+    };
+    auto sorted = [](const std::vector<int4>& v) {
+      for (size_t i = 1; i < v.size(); ++i)
+        if ((v[i].x & ~kStripDown) < (v[i - 1].x & ~kStripDown)) return false;
+      return true;
+    };
+    bool groups_sorted = true;
+    int g = 0;
+    for (size_t i = 1; i < h->group_lat.size(); ++i) groups_sorted = groups_sorted && h->group_lat[i] >= h->group_lat[i - 1];
+    while (g < int(h->group_lat.size()) && h->group_lat[g] < k) ++g;
+    if (sorted(strips) && sorted(tiles) && groups_sorted) {
+      h->split = k;
+      h->split_strip = first(strips);
+      h->split_tile = first(tiles);
+      h->split_group = g;
+    }
+  }
   return LBCG_OK;
 }
 
@@ -482,6 +540,8 @@ lbcg_status lbcg_create_batch(int32_t n, const lbcg_geometry* geoms, const lbcg_
     build_wall_groups(views, ofb, gmax, groups, wband, wvirt, wsten);
   }
   h->ngroups = int(groups.size());
+  h->group_lat.clear();
+  for (const WallGroup& G : groups) h->group_lat.push_back(G.lat);
   const size_t es = elem_size(precision), cs = compute_size(precision);
   auto alloc = [&](void** p, size_t bytes) { return dev_alloc(h, p, bytes); };
   bool ok = alloc(&h->pool[0], 18 * (size_t)node_total * es) && alloc(&h->pool[1], 18 * (size_t)node_total * es) &&
@@ -606,10 +666,33 @@ lbcg_status lbcg_step(lbcg_handle* h, int64_t nsteps) {
         // 16-bit storage: each replay advances the counter that keys the stochastic rounding,
         // and the 32 captured steps carry their index within the replay
         if (h->prec >= 2) le = launch_sr_tick(h->d_sr_epoch, h->stream);
+        // a batch: the second half's steps in a branch forked from the capture and joined
+        // back at its end
+        const bool fork = h->split > 0 && le == cudaSuccess;
+        if (fork) {
+          if (!h->stream2) le = cudaStreamCreateWithFlags(&h->stream2, cudaStreamNonBlocking);
+          if (le == cudaSuccess && !h->ev_fork) le = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+          if (le == cudaSuccess && !h->ev_join) le = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
+          if (le == cudaSuccess) le = cudaEventRecord(h->ev_fork, h->stream);
+          if (le == cudaSuccess) le = cudaStreamWaitEvent(h->stream2, h->ev_fork, 0);
+        }
+        const bool forked = fork && le == cudaSuccess;
         for (int k = 0; k < kGraphSteps && le == cudaSuccess; ++k) {
-          LaunchStep q = make_launch(h, k & 1, nullptr, 0, h->ntiles);
-          q.sr_step = uint32_t(k);
-          le = launch_step(h->prec, q, h->stream);
+          if (forked) {
+            LaunchStep q0 = make_launch_half(h, k & 1, 0), q1 = make_launch_half(h, k & 1, 1);
+            q0.sr_step = q1.sr_step = uint32_t(k);
+            le = launch_step(h->prec, q0, h->stream);
+            if (le == cudaSuccess) le = launch_step(h->prec, q1, h->stream2);
+          } else {
+            LaunchStep q = make_launch(h, k & 1, nullptr, 0, h->ntiles);
+            q.sr_step = uint32_t(k);
+            le = launch_step(h->prec, q, h->stream);
+          }
+        }
+        if (forked) {   // join the branch even after a failed launch, so that the capture can end
+          const cudaError_t je = cudaEventRecord(h->ev_join, h->stream2);
+          const cudaError_t we = je == cudaSuccess ? cudaStreamWaitEvent(h->stream, h->ev_join, 0) : je;
+          if (le == cudaSuccess) le = we;
         }
         cudaError_t ee = cudaStreamEndCapture(h->stream, &g);
         if (le != cudaSuccess) return cuda_fail(h, le, "launch during capture");
