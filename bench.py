@@ -463,8 +463,10 @@ def run_ours(args):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks.start()
+    launches0 = lat.step_launches
     ms = timed_steps(lat, stream, args.steps, flush)
     torch.cuda.synchronize()
+    launches = lat.step_launches - launches0   # kernel launches of the timed region, graph nodes counted
     clk = clocks.stop()
     if ws > 1:
         torch.distributed.barrier()
@@ -476,7 +478,6 @@ def run_ours(args):
     lbcg.lbcg_profile(lat.h, False)
     ms_max, nf_total = reduce_over_ranks(ms, nf, ws, "cuda")
     value = nf_total * args.steps / (ms_max / 1e3) / 1e6
-    launches = args.steps * lat.launches_per_step
     obs = lbcg.lbcg_observables(lat.h, 0, lbcg.obs_spec(ny=geoms[0].ny), raise_on_diverged=False)
 
     # ---- roofline of the dominant kernel (k_step)

@@ -301,9 +301,13 @@ lbcg_status lbcg_diagnostics(lbcg_handle* h, int32_t lattice, const lbcg_diag_sp
 lbcg_status lbcg_profile(lbcg_handle* h, int32_t enable);
 lbcg_status lbcg_kernel_times(lbcg_handle* h, double* ms2, int64_t* steps);
 
-/* Number of kernel launches one time step enqueues, and the number of lattice nodes
- * (fluid and solid) all lattices hold. */
+/* Number of kernel launches one directly launched time step enqueues (the wall kernel and the
+ * bulk kernel), the number of kernel launches lbcg_step has enqueued on the handle since it was
+ * created (each kernel node of a replayed graph counts: a batch's graph runs its lattices as
+ * up to 3 parallel branches of their own launches), and the number of lattice nodes (fluid and
+ * solid) all lattices hold. */
 int32_t lbcg_launches_per_step(const lbcg_handle* h);
+int64_t lbcg_step_launches(const lbcg_handle* h);
 int64_t lbcg_total_nodes(const lbcg_handle* h);
 
 lbcg_status lbcg_destroy(lbcg_handle* h);

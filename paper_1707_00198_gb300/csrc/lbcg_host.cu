@@ -43,6 +43,7 @@ std::mutex g_alloc_mutex;
 lbcg_allocator g_allocator = {nullptr, nullptr, nullptr};
 
 constexpr int kGraphSteps = 32;   // steps per captured graph (even: the graph starts and ends on pool A)
+constexpr int kGraphBranches = 3; // parallel branches of a batch's graph (groups of lattices)
 constexpr int kDefaultTY = 8;
 constexpr int kSMs = 152;
 
@@ -98,15 +99,18 @@ struct lbcg_handle {
   int nofb = 0;
   double* d_obs = nullptr;   // partials then outputs
   cudaGraphExec_t graph = nullptr;
-  // batches: the captured graph runs the lattices [0, split) and [split, n) as two parallel
-  // branches, so that one half's wall kernel runs beside the other half's bulk kernel (the
-  // lattices are independent); 0 = one branch.  First strip / tile / wall group of the second
-  // half, and the second branch's capture stream and fork / join events.
-  int split = 0;
-  int split_strip = 0, split_tile = 0, split_group = 0;
+  int64_t graph_kernels = 0;    // kernel nodes of the captured graph
+  int64_t step_launches = 0;    // kernel launches lbcg_step has enqueued (graph nodes counted)
+  // batches: the captured graph runs nbranch groups of consecutive lattices (about equal node
+  // counts) as parallel branches, so that one group's wall kernel and launch tail run beside
+  // the others' bulk kernels (the lattices are independent).  Branch b has strips
+  // [br_strip[b], br_strip[b+1]), and likewise tiles and wall groups; branches 1.. are
+  // captured from their own streams, forked from and joined back to the handle's stream.
+  int nbranch = 1;
+  int br_strip[kGraphBranches + 1] = {}, br_tile[kGraphBranches + 1] = {}, br_group[kGraphBranches + 1] = {};
   std::vector<int> group_lat;   // lattice of each wall group
-  cudaStream_t stream2 = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaStream_t br_stream[kGraphBranches] = {};
+  cudaEvent_t ev_fork = nullptr, ev_join[kGraphBranches] = {};
   std::vector<uint8_t> flags_host;
   std::vector<OfbEntry> ofb_host;
   bool profiling = false;
@@ -280,15 +284,13 @@ LaunchStep make_launch(lbcg_handle* h, int src, double* macro, int tile_begin, i
   return p;
 }
 
-// the launch of one branch of a split graph: lattices [0, split) (half 0) or [split, n)
-LaunchStep make_launch_half(lbcg_handle* h, int src, int half) {
-  LaunchStep p = make_launch(h, src, nullptr, half ? h->split_tile : 0, half ? h->ntiles : h->split_tile);
-  const int s0 = half ? h->split_strip : 0, s1 = half ? h->nstrips : h->split_strip;
-  const int g0 = half ? h->split_group : 0, g1 = half ? h->ngroups : h->split_group;
-  p.strips = h->d_strips + s0;
-  p.nstrips = s1 - s0;
-  p.groups = h->d_groups + g0;
-  p.ngroups = g1 - g0;
+// the launch of branch b of a graph split over lattice groups
+LaunchStep make_launch_branch(lbcg_handle* h, int src, int b) {
+  LaunchStep p = make_launch(h, src, nullptr, h->br_tile[b], h->br_tile[b + 1]);
+  p.strips = h->d_strips + h->br_strip[b];
+  p.nstrips = h->br_strip[b + 1] - h->br_strip[b];
+  p.groups = h->d_groups + h->br_group[b];
+  p.ngroups = h->br_group[b + 1] - h->br_group[b];
   return p;
 }
 
@@ -301,9 +303,11 @@ void free_handle(lbcg_handle* h) {
                   h->d_obs,   h->d_strips, h->d_nbmask, h->d_err, h->d_usnap, h->d_sr_epoch};
   if (h->stream) cudaStreamSynchronize(h->stream);
   for (void* p : ptrs) dev_free(h, p);
-  if (h->stream2) cudaStreamDestroy(h->stream2);
+  for (int b = 0; b < kGraphBranches; ++b) {
+    if (h->br_stream[b]) cudaStreamDestroy(h->br_stream[b]);
+    if (h->ev_join[b]) cudaEventDestroy(h->ev_join[b]);
+  }
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
-  if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }
@@ -326,39 +330,44 @@ lbcg_status upload_tiles(lbcg_handle* h) {
     return fail(LBCG_E_NOMEM, "cannot allocate the strip list");
   if (!strips.empty())
     CK(h, cudaMemcpy(h->d_strips, strips.data(), strips.size() * sizeof(int4), cudaMemcpyHostToDevice));
-  // the split of a batch into two graph branches of about equal node counts; strips, tiles and
-  // wall groups are all in lattice order, so each half is a contiguous range of each list
-  h->split = 0;
+  // the split of a batch into graph branches of about equal node counts; strips, tiles and
+  // wall groups are all in lattice order, so each branch is a contiguous range of each list
+  h->nbranch = 1;
   const int n = int(h->lats.size());
-  if (n >= 2) {
+  const int nb = std::min(kGraphBranches, n);
+  auto lat_of = [](const int4& e) { return e.x & ~kStripDown; };
+  bool sorted = true;
+  for (size_t i = 1; i < strips.size(); ++i) sorted = sorted && lat_of(strips[i]) >= lat_of(strips[i - 1]);
+  for (size_t i = 1; i < tiles.size(); ++i) sorted = sorted && lat_of(tiles[i]) >= lat_of(tiles[i - 1]);
+  for (size_t i = 1; i < h->group_lat.size(); ++i) sorted = sorted && h->group_lat[i] >= h->group_lat[i - 1];
+  if (nb >= 2 && sorted) {
     auto nodes = [&](int l) { return (long long)h->lats[l].nx * h->lats[l].ny; };
-    long long total = 0, acc = 0;
+    long long total = 0;
     for (int l = 0; l < n; ++l) total += nodes(l);
-    // the first half: lattices [0, k) with acc = their nodes closest to total / 2, 1 <= k < n
-    int k = 0;
-    while (k < n - 1 && 2 * (acc + nodes(k)) <= total) acc += nodes(k++);
-    if (k < n - 1 && total - 2 * acc > 2 * (acc + nodes(k)) - total) acc += nodes(k++);
-    k = std::max(k, 1);
-    auto first = [&](const std::vector<int4>& v) {
+    // branch b ends at the first lattice boundary whose node count reaches (b + 1) / nb of
+    // the total, leaving at least one lattice to each later branch
+    int lat_end[kGraphBranches + 1] = {};
+    long long acc = 0;
+    int l = 0;
+    for (int br = 0; br < nb - 1; ++br) {
+      do acc += nodes(l++);
+      while (l < n - (nb - 1 - br) && acc * nb < total * (br + 1));
+      lat_end[br + 1] = l;
+    }
+    lat_end[nb] = n;
+    auto first = [&](const std::vector<int4>& v, int lat) {
       int i = 0;
-      while (i < int(v.size()) && (v[i].x & ~kStripDown) < k) ++i;
+      while (i < int(v.size()) && lat_of(v[i]) < lat) ++i;
       return i;
     };
-    auto sorted = [](const std::vector<int4>& v) {
-      for (size_t i = 1; i < v.size(); ++i)
-        if ((v[i].x & ~kStripDown) < (v[i - 1].x & ~kStripDown)) return false;
-      return true;
-    };
-    bool groups_sorted = true;
-    int g = 0;
-    for (size_t i = 1; i < h->group_lat.size(); ++i) groups_sorted = groups_sorted && h->group_lat[i] >= h->group_lat[i - 1];
-    while (g < int(h->group_lat.size()) && h->group_lat[g] < k) ++g;
-    if (sorted(strips) && sorted(tiles) && groups_sorted) {
-      h->split = k;
-      h->split_strip = first(strips);
-      h->split_tile = first(tiles);
-      h->split_group = g;
+    for (int br = 0; br <= nb; ++br) {
+      h->br_strip[br] = first(strips, lat_end[br]);
+      h->br_tile[br] = first(tiles, lat_end[br]);
+      int g = 0;
+      while (g < int(h->group_lat.size()) && h->group_lat[g] < lat_end[br]) ++g;
+      h->br_group[br] = g;
     }
+    h->nbranch = nb;
   }
   return LBCG_OK;
 }
@@ -653,6 +662,7 @@ lbcg_status lbcg_step(lbcg_handle* h, int64_t nsteps) {
       p.ev = h->events.data() + h->events_used;
       h->events_used += 4;
       CK(h, launch_step(h->prec, p, h->stream));
+      h->step_launches += step_kernels(p);
       h->cur ^= 1;
       h->step += 1;
       nsteps -= 1;
@@ -665,33 +675,43 @@ lbcg_status lbcg_step(lbcg_handle* h, int64_t nsteps) {
         cudaError_t le = cudaSuccess;
         // 16-bit storage: each replay advances the counter that keys the stochastic rounding,
         // and the 32 captured steps carry their index within the replay
-        if (h->prec >= 2) le = launch_sr_tick(h->d_sr_epoch, h->stream);
-        // a batch: the second half's steps in a branch forked from the capture and joined
-        // back at its end
-        const bool fork = h->split > 0 && le == cudaSuccess;
-        if (fork) {
-          if (!h->stream2) le = cudaStreamCreateWithFlags(&h->stream2, cudaStreamNonBlocking);
-          if (le == cudaSuccess && !h->ev_fork) le = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
-          if (le == cudaSuccess && !h->ev_join) le = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
-          if (le == cudaSuccess) le = cudaEventRecord(h->ev_fork, h->stream);
-          if (le == cudaSuccess) le = cudaStreamWaitEvent(h->stream2, h->ev_fork, 0);
+        int64_t nk = 0;
+        if (h->prec >= 2) {
+          le = launch_sr_tick(h->d_sr_epoch, h->stream);
+          nk += 1;
         }
-        const bool forked = fork && le == cudaSuccess;
+        // a batch: branches 1.. forked from the capture and joined back at its end
+        int nfork = 0;   // branches 1 .. nfork have joined the capture
+        if (h->nbranch > 1 && le == cudaSuccess) {
+          if (!h->ev_fork) le = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+          if (le == cudaSuccess) le = cudaEventRecord(h->ev_fork, h->stream);
+          for (int b = 1; b < h->nbranch && le == cudaSuccess; ++b) {
+            if (!h->br_stream[b]) le = cudaStreamCreateWithFlags(&h->br_stream[b], cudaStreamNonBlocking);
+            if (le == cudaSuccess && !h->ev_join[b]) le = cudaEventCreateWithFlags(&h->ev_join[b], cudaEventDisableTiming);
+            if (le == cudaSuccess) le = cudaStreamWaitEvent(h->br_stream[b], h->ev_fork, 0);
+            if (le == cudaSuccess) nfork = b;
+          }
+        }
+        const bool forked = h->nbranch > 1 && nfork == h->nbranch - 1 && le == cudaSuccess;
         for (int k = 0; k < kGraphSteps && le == cudaSuccess; ++k) {
           if (forked) {
-            LaunchStep q0 = make_launch_half(h, k & 1, 0), q1 = make_launch_half(h, k & 1, 1);
-            q0.sr_step = q1.sr_step = uint32_t(k);
-            le = launch_step(h->prec, q0, h->stream);
-            if (le == cudaSuccess) le = launch_step(h->prec, q1, h->stream2);
+            for (int b = 0; b < h->nbranch && le == cudaSuccess; ++b) {
+              LaunchStep q = make_launch_branch(h, k & 1, b);
+              q.sr_step = uint32_t(k);
+              le = launch_step(h->prec, q, b ? h->br_stream[b] : h->stream);
+              nk += step_kernels(q);
+            }
           } else {
             LaunchStep q = make_launch(h, k & 1, nullptr, 0, h->ntiles);
             q.sr_step = uint32_t(k);
             le = launch_step(h->prec, q, h->stream);
+            nk += step_kernels(q);
           }
         }
-        if (forked) {   // join the branch even after a failed launch, so that the capture can end
-          const cudaError_t je = cudaEventRecord(h->ev_join, h->stream2);
-          const cudaError_t we = je == cudaSuccess ? cudaStreamWaitEvent(h->stream, h->ev_join, 0) : je;
+        // join every forked branch, also after a failed launch, so that the capture can end
+        for (int b = 1; b <= nfork; ++b) {
+          const cudaError_t je = cudaEventRecord(h->ev_join[b], h->br_stream[b]);
+          const cudaError_t we = je == cudaSuccess ? cudaStreamWaitEvent(h->stream, h->ev_join[b], 0) : je;
           if (le == cudaSuccess) le = we;
         }
         cudaError_t ee = cudaStreamEndCapture(h->stream, &g);
@@ -700,13 +720,17 @@ lbcg_status lbcg_step(lbcg_handle* h, int64_t nsteps) {
         cudaError_t ie = cudaGraphInstantiate(&h->graph, g, 0);
         cudaGraphDestroy(g);
         if (ie != cudaSuccess) return cuda_fail(h, ie, "cudaGraphInstantiate");
+        h->graph_kernels = nk;
       }
       CK(h, cudaGraphLaunch(h->graph, h->stream));
+      h->step_launches += h->graph_kernels;
       nsteps -= kGraphSteps;
       h->step += kGraphSteps;
       continue;
     }
-    CK(h, launch_step(h->prec, make_launch(h, h->cur, nullptr, 0, h->ntiles), h->stream));
+    const LaunchStep p = make_launch(h, h->cur, nullptr, 0, h->ntiles);
+    CK(h, launch_step(h->prec, p, h->stream));
+    h->step_launches += step_kernels(p);
     h->cur ^= 1;
     h->step += 1;
     nsteps -= 1;
@@ -1466,6 +1490,8 @@ int32_t lbcg_launches_per_step(const lbcg_handle* h) {
   if (!h) return 0;
   return (h->ngroups > 0 ? 1 : 0) + ((h->sweep ? h->nstrips : h->ntiles) > 0 ? 1 : 0);
 }
+
+int64_t lbcg_step_launches(const lbcg_handle* h) { return h ? h->step_launches : 0; }
 
 int64_t lbcg_total_nodes(const lbcg_handle* h) {
   if (!h) return 0;

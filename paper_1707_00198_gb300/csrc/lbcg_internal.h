@@ -40,6 +40,10 @@ struct LaunchStep {
 };
 
 cudaError_t launch_step(int prec, const LaunchStep& p, cudaStream_t st);
+// the number of kernels launch_step launches for p (the wall kernel, the bulk kernel)
+inline int step_kernels(const LaunchStep& p) {
+  return (p.ngroups > 0 ? 1 : 0) + ((p.sweep && p.macro == nullptr) ? (p.nstrips > 0 ? 1 : 0) : (p.ntiles > 0 ? 1 : 0));
+}
 // Advances the stochastic-rounding replay counter (one single-thread launch).
 cudaError_t launch_sr_tick(uint32_t* epoch, cudaStream_t st);
 // One-time kernel attributes for a precision (the sweep's dynamic shared memory); called

@@ -123,6 +123,7 @@ def library():
         "lbcg_profile": (C.c_int, [H, C.c_int32]),
         "lbcg_kernel_times": (C.c_int, [H, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
         "lbcg_launches_per_step": (C.c_int32, [H]),
+        "lbcg_step_launches": (C.c_int64, [H]),
         "lbcg_total_nodes": (C.c_int64, [H]),
         "lbcg_destroy": (C.c_int, [H]),
         "lbcg_last_error": (C.c_char_p, []),
@@ -144,7 +145,7 @@ def library():
 def exported_symbols() -> list:
     return ["lbcg_create", "lbcg_create_batch", "lbcg_step", "lbcg_observables", "lbcg_get_populations",
             "lbcg_set_populations", "lbcg_get_fields", "lbcg_state_bytes", "lbcg_upload_state",
-            "lbcg_download_state", "lbcg_set_sweep", "lbcg_set_tile", "lbcg_profile", "lbcg_kernel_times", "lbcg_launches_per_step", "lbcg_total_nodes", "lbcg_destroy",
+            "lbcg_download_state", "lbcg_set_sweep", "lbcg_set_tile", "lbcg_profile", "lbcg_kernel_times", "lbcg_launches_per_step", "lbcg_step_launches", "lbcg_total_nodes", "lbcg_destroy",
             "lbcg_last_error", "lbcg_field_moments_noalloc", "lbcg_adjoint", "lbcg_autotune", "lbcg_schedule", "lbcg_diagnostics",
             "lbcg_set_poll_limit", "lbcg_set_allocator"]
 
@@ -317,6 +318,10 @@ def lbcg_launches_per_step(h: int) -> int:
     return int(library().lbcg_launches_per_step(h))
 
 
+def lbcg_step_launches(h: int) -> int:
+    return int(library().lbcg_step_launches(h))
+
+
 def lbcg_total_nodes(h: int) -> int:
     return int(library().lbcg_total_nodes(h))
 
@@ -423,6 +428,10 @@ class Lattice:
     @property
     def launches_per_step(self) -> int:
         return lbcg_launches_per_step(self.h)
+
+    @property
+    def step_launches(self) -> int:
+        return lbcg_step_launches(self.h)
 
     @property
     def total_nodes(self) -> int:

@@ -245,6 +245,27 @@ def test_batched_lattices_equal_their_single_runs():
         B.close()
 
 
+def test_step_launch_count_of_direct_steps_and_branched_graphs():
+    # one lattice: every step (graph replay or direct) launches the wall and the bulk kernel;
+    # a batch of 4: its 32-step graph runs 3 branches, each with its own two launches per step
+    from paper_1707_00198_gb300.lbcg import Lattice
+    g, p = I.config_static_droplet()
+    L = Lattice(g, p, "fp32")
+    assert L.launches_per_step == 2 and L.step_launches == 0
+    L.step(32)
+    L.step(5)
+    assert L.step_launches == 37 * 2
+    L.close()
+    gs = [I.displacement_channel(W=20 + 4 * i, L=110, x_I=25.0, seed=6 + i, noise=1e-3) for i in range(4)]
+    ps = [I.fingering_params(5.0, 0.1, 60.0)] * 4
+    B = Lattice(gs, ps, "fp32")
+    B.step(32)
+    assert B.step_launches == 32 * 3 * 2
+    B.step(1)
+    assert B.step_launches == 32 * 3 * 2 + 2
+    B.close()
+
+
 def test_graph_replay_matches_direct_steps():
     # 70 steps use two 32-step graph replays plus direct launches; 70 single calls use none
     g, p = I.config_static_droplet()
