@@ -196,6 +196,17 @@ size_t lbcg_state_bytes(const lbcg_handle* h);
 lbcg_status lbcg_upload_state(lbcg_handle* h, const void* host_in, size_t bytes);
 lbcg_status lbcg_download_state(lbcg_handle* h, void* host_out, size_t bytes);
 
+/* Host state in, `nsteps` >= 0 steps, host state out: the same result as lbcg_upload_state,
+ * lbcg_step(nsteps) with direct launches and lbcg_download_state, but the lattices of a batch
+ * move in up to 8 groups of consecutive lattices (about equal node counts) whose copies and
+ * steps overlap: group g's steps start when its upload lands, its download when its steps end,
+ * while later groups are still uploading (the lattices are independent).  host_in and host_out
+ * hold lbcg_state_bytes(h) bytes in the layout of lbcg_upload_state (pinned for full copy
+ * speed) and may be the same buffer.  Ordered after the work already on the handle's stream;
+ * synchronises before returning (the device error word is checked as in lbcg_download_state).
+ * The copies run on two streams of the handle's own. */
+lbcg_status lbcg_step_host(lbcg_handle* h, const void* host_in, void* host_out, size_t bytes, int64_t nsteps);
+
 /* Schedule of the fused step kernel.  The default is the y-sweep (k_sweep): blocks of 128
  * threads own strips of 124 columns and walk up `rows`-row segments of them (rows = 0 picks
  * the segment height so that every SM gets several strips).  lbcg_set_tile switches to 2-D

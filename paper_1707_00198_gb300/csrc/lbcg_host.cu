@@ -44,6 +44,7 @@ lbcg_allocator g_allocator = {nullptr, nullptr, nullptr};
 
 constexpr int kGraphSteps = 32;   // steps per captured graph (even: the graph starts and ends on pool A)
 constexpr int kGraphBranches = 3; // parallel branches of a batch's graph (groups of lattices)
+constexpr int kHostGroups = 8;    // lattice groups whose copies lbcg_step_host overlaps
 constexpr int kDefaultTY = 8;
 constexpr int kSMs = 152;
 
@@ -101,14 +102,21 @@ struct lbcg_handle {
   cudaGraphExec_t graph = nullptr;
   int64_t graph_kernels = 0;    // kernel nodes of the captured graph
   int64_t step_launches = 0;    // kernel launches lbcg_step has enqueued (graph nodes counted)
-  // batches: the captured graph runs nbranch groups of consecutive lattices (about equal node
-  // counts) as parallel branches, so that one group's wall kernel and launch tail run beside
-  // the others' bulk kernels (the lattices are independent).  Branch b has strips
-  // [br_strip[b], br_strip[b+1]), and likewise tiles and wall groups; branches 1.. are
-  // captured from their own streams, forked from and joined back to the handle's stream.
-  int nbranch = 1;
-  int br_strip[kGraphBranches + 1] = {}, br_tile[kGraphBranches + 1] = {}, br_group[kGraphBranches + 1] = {};
+  // Strips, tiles and wall groups are listed in lattice order: lattice l has strips
+  // [lat_strip[l], lat_strip[l+1]), and likewise tiles and groups (empty vectors: not in order,
+  // and the lattices are then never launched apart).
   std::vector<int> group_lat;   // lattice of each wall group
+  std::vector<int> lat_strip, lat_tile, lat_group;
+  // batches: the captured graph runs nbranch groups of consecutive lattices (about equal node
+  // counts; branch b has lattices [br_lat[b], br_lat[b+1])) as parallel branches, so that one
+  // group's wall kernel and launch tail run beside the others' bulk kernels (the lattices are
+  // independent); branches 1.. are captured from their own streams, forked from and joined
+  // back to the handle's stream.
+  int nbranch = 1;
+  int br_lat[kGraphBranches + 1] = {};
+  // lbcg_step_host: the streams of the uploads and of the downloads, and its events
+  cudaStream_t io_stream[2] = {};
+  std::vector<cudaEvent_t> io_events;
   cudaStream_t br_stream[kGraphBranches] = {};
   cudaEvent_t ev_fork = nullptr, ev_join[kGraphBranches] = {};
   std::vector<uint8_t> flags_host;
@@ -284,14 +292,37 @@ LaunchStep make_launch(lbcg_handle* h, int src, double* macro, int tile_begin, i
   return p;
 }
 
-// the launch of branch b of a graph split over lattice groups
-LaunchStep make_launch_branch(lbcg_handle* h, int src, int b) {
-  LaunchStep p = make_launch(h, src, nullptr, h->br_tile[b], h->br_tile[b + 1]);
-  p.strips = h->d_strips + h->br_strip[b];
-  p.nstrips = h->br_strip[b + 1] - h->br_strip[b];
-  p.groups = h->d_groups + h->br_group[b];
-  p.ngroups = h->br_group[b + 1] - h->br_group[b];
+// the launch of one step of the lattices [l0, l1) alone (the lists are in lattice order)
+LaunchStep make_launch_lats(lbcg_handle* h, int src, int l0, int l1) {
+  LaunchStep p = make_launch(h, src, nullptr, h->lat_tile[l0], h->lat_tile[l1]);
+  p.strips = h->d_strips + h->lat_strip[l0];
+  p.nstrips = h->lat_strip[l1] - h->lat_strip[l0];
+  p.groups = h->d_groups + h->lat_group[l0];
+  p.ngroups = h->lat_group[l1] - h->lat_group[l0];
   return p;
+}
+
+// splits the lattices into ng >= 1 groups of consecutive lattices of about equal node counts,
+// each with at least one lattice: group g is [end[g], end[g+1]); returns the number of groups
+// (1 if the lists are not in lattice order)
+int split_lattices(const lbcg_handle* h, int ng, int* end) {
+  const int n = int(h->lats.size());
+  ng = std::max(1, std::min(ng, n));
+  if (h->lat_strip.empty()) ng = 1;
+  auto nodes = [&](int l) { return (long long)h->lats[l].nx * h->lats[l].ny; };
+  long long total = 0, acc = 0;
+  for (int l = 0; l < n; ++l) total += nodes(l);
+  // group g ends at the first lattice boundary whose node count reaches (g + 1) / ng of the
+  // total, leaving at least one lattice to each later group
+  int l = 0;
+  end[0] = 0;
+  for (int g = 0; g < ng - 1; ++g) {
+    do acc += nodes(l++);
+    while (l < n - (ng - 1 - g) && acc * ng < total * (g + 1));
+    end[g + 1] = l;
+  }
+  end[ng] = n;
+  return ng;
 }
 
 void free_handle(lbcg_handle* h) {
@@ -307,6 +338,9 @@ void free_handle(lbcg_handle* h) {
     if (h->br_stream[b]) cudaStreamDestroy(h->br_stream[b]);
     if (h->ev_join[b]) cudaEventDestroy(h->ev_join[b]);
   }
+  for (cudaStream_t st : h->io_stream)
+    if (st) cudaStreamDestroy(st);
+  for (cudaEvent_t e : h->io_events) cudaEventDestroy(e);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
@@ -330,45 +364,31 @@ lbcg_status upload_tiles(lbcg_handle* h) {
     return fail(LBCG_E_NOMEM, "cannot allocate the strip list");
   if (!strips.empty())
     CK(h, cudaMemcpy(h->d_strips, strips.data(), strips.size() * sizeof(int4), cudaMemcpyHostToDevice));
-  // the split of a batch into graph branches of about equal node counts; strips, tiles and
-  // wall groups are all in lattice order, so each branch is a contiguous range of each list
-  h->nbranch = 1;
+  // per-lattice ranges of the three lists, and the graph branches of a batch
   const int n = int(h->lats.size());
-  const int nb = std::min(kGraphBranches, n);
   auto lat_of = [](const int4& e) { return e.x & ~kStripDown; };
   bool sorted = true;
   for (size_t i = 1; i < strips.size(); ++i) sorted = sorted && lat_of(strips[i]) >= lat_of(strips[i - 1]);
   for (size_t i = 1; i < tiles.size(); ++i) sorted = sorted && lat_of(tiles[i]) >= lat_of(tiles[i - 1]);
   for (size_t i = 1; i < h->group_lat.size(); ++i) sorted = sorted && h->group_lat[i] >= h->group_lat[i - 1];
-  if (nb >= 2 && sorted) {
-    auto nodes = [&](int l) { return (long long)h->lats[l].nx * h->lats[l].ny; };
-    long long total = 0;
-    for (int l = 0; l < n; ++l) total += nodes(l);
-    // branch b ends at the first lattice boundary whose node count reaches (b + 1) / nb of
-    // the total, leaving at least one lattice to each later branch
-    int lat_end[kGraphBranches + 1] = {};
-    long long acc = 0;
-    int l = 0;
-    for (int br = 0; br < nb - 1; ++br) {
-      do acc += nodes(l++);
-      while (l < n - (nb - 1 - br) && acc * nb < total * (br + 1));
-      lat_end[br + 1] = l;
-    }
-    lat_end[nb] = n;
+  h->lat_strip.clear();
+  h->lat_tile.clear();
+  h->lat_group.clear();
+  if (sorted) {
     auto first = [&](const std::vector<int4>& v, int lat) {
       int i = 0;
       while (i < int(v.size()) && lat_of(v[i]) < lat) ++i;
       return i;
     };
-    for (int br = 0; br <= nb; ++br) {
-      h->br_strip[br] = first(strips, lat_end[br]);
-      h->br_tile[br] = first(tiles, lat_end[br]);
+    for (int l = 0; l <= n; ++l) {
+      h->lat_strip.push_back(first(strips, l));
+      h->lat_tile.push_back(first(tiles, l));
       int g = 0;
-      while (g < int(h->group_lat.size()) && h->group_lat[g] < lat_end[br]) ++g;
-      h->br_group[br] = g;
+      while (g < int(h->group_lat.size()) && h->group_lat[g] < l) ++g;
+      h->lat_group.push_back(g);
     }
-    h->nbranch = nb;
   }
+  h->nbranch = split_lattices(h, kGraphBranches, h->br_lat);
   return LBCG_OK;
 }
 
@@ -696,7 +716,7 @@ lbcg_status lbcg_step(lbcg_handle* h, int64_t nsteps) {
         for (int k = 0; k < kGraphSteps && le == cudaSuccess; ++k) {
           if (forked) {
             for (int b = 0; b < h->nbranch && le == cudaSuccess; ++b) {
-              LaunchStep q = make_launch_branch(h, k & 1, b);
+              LaunchStep q = make_launch_lats(h, k & 1, h->br_lat[b], h->br_lat[b + 1]);
               q.sr_step = uint32_t(k);
               le = launch_step(h->prec, q, b ? h->br_stream[b] : h->stream);
               nk += step_kernels(q);
@@ -931,6 +951,63 @@ lbcg_status lbcg_download_state(lbcg_handle* h, void* host_out, size_t bytes) {
   if (!host_out || bytes != lbcg_state_bytes(h)) return fail(LBCG_E_ARG, "state size mismatch");
   CK(h, cudaMemcpyAsync(host_out, h->pool[h->cur], bytes, cudaMemcpyDeviceToHost, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
+  return check_device_error(h);
+}
+
+lbcg_status lbcg_step_host(lbcg_handle* h, const void* host_in, void* host_out, size_t bytes, int64_t nsteps) {
+  Range range_("lbcg_step_host");
+  lbcg_status s = check_handle(h);
+  if (s != LBCG_OK) return s;
+  if (!host_in || !host_out || bytes != lbcg_state_bytes(h)) return fail(LBCG_E_ARG, "state size mismatch");
+  if (nsteps < 0) return fail(LBCG_E_ARG, "nsteps < 0");
+  // groups of consecutive lattices: each is uploaded, stepped and downloaded on its own, the
+  // uploads one after another on one stream, the steps on the handle's stream as each upload
+  // lands, the downloads on a third stream as each group's steps end
+  int end[kHostGroups + 1];
+  const int ng = split_lattices(h, kHostGroups, end);
+  for (int q = 0; q < 2; ++q)
+    if (!h->io_stream[q]) CK(h, cudaStreamCreateWithFlags(&h->io_stream[q], cudaStreamNonBlocking));
+  while (h->io_events.size() < size_t(2 * kHostGroups + 1)) {
+    cudaEvent_t e;
+    CK(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    h->io_events.push_back(e);
+  }
+  cudaEvent_t* const ev_in = h->io_events.data();
+  cudaEvent_t* const ev_done = ev_in + kHostGroups;
+  const cudaEvent_t ev_start = ev_in[2 * kHostGroups];
+  const int n = int(h->lats.size());
+  const size_t es = elem_size(h->prec);
+  auto off = [&](int l) { return size_t(l < n ? h->lats[l].pop_off : 18 * h->node_total) * es; };
+  const int c0 = h->cur, c1 = h->cur ^ int(nsteps & 1);   // the pools of the state before and after
+  const char* in = static_cast<const char*>(host_in);
+  char* out = static_cast<char*>(host_out);
+  CK(h, cudaEventRecord(ev_start, h->stream));   // after the work already on the handle's stream
+  CK(h, cudaStreamWaitEvent(h->io_stream[0], ev_start, 0));
+  for (int g = 0; g < ng; ++g) {
+    CK(h, cudaMemcpyAsync(static_cast<char*>(h->pool[c0]) + off(end[g]), in + off(end[g]), off(end[g + 1]) - off(end[g]),
+                          cudaMemcpyHostToDevice, h->io_stream[0]));
+    CK(h, cudaEventRecord(ev_in[g], h->io_stream[0]));
+  }
+  for (int g = 0; g < ng; ++g) {
+    CK(h, cudaStreamWaitEvent(h->stream, ev_in[g], 0));
+    for (int64_t k = 0; k < nsteps; ++k) {
+      LaunchStep p = ng > 1 ? make_launch_lats(h, c0 ^ int(k & 1), end[g], end[g + 1])
+                            : make_launch(h, c0 ^ int(k & 1), nullptr, 0, h->ntiles);
+      p.sr_step = uint32_t(h->step + k);
+      CK(h, launch_step(h->prec, p, h->stream));
+      h->step_launches += step_kernels(p);
+    }
+    CK(h, cudaEventRecord(ev_done[g], h->stream));
+  }
+  for (int g = 0; g < ng; ++g) {
+    CK(h, cudaStreamWaitEvent(h->io_stream[1], ev_done[g], 0));
+    CK(h, cudaMemcpyAsync(out + off(end[g]), static_cast<const char*>(h->pool[c1]) + off(end[g]),
+                          off(end[g + 1]) - off(end[g]), cudaMemcpyDeviceToHost, h->io_stream[1]));
+  }
+  CK(h, cudaStreamSynchronize(h->io_stream[1]));
+  CK(h, cudaStreamSynchronize(h->stream));
+  h->cur = c1;
+  h->step += nsteps;
   return check_device_error(h);
 }
 

@@ -123,6 +123,7 @@ def library():
         "lbcg_profile": (C.c_int, [H, C.c_int32]),
         "lbcg_kernel_times": (C.c_int, [H, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
         "lbcg_launches_per_step": (C.c_int32, [H]),
+        "lbcg_step_host": (C.c_int, [H, C.c_void_p, C.c_void_p, C.c_size_t, C.c_int64]),
         "lbcg_step_launches": (C.c_int64, [H]),
         "lbcg_total_nodes": (C.c_int64, [H]),
         "lbcg_destroy": (C.c_int, [H]),
@@ -145,7 +146,7 @@ def library():
 def exported_symbols() -> list:
     return ["lbcg_create", "lbcg_create_batch", "lbcg_step", "lbcg_observables", "lbcg_get_populations",
             "lbcg_set_populations", "lbcg_get_fields", "lbcg_state_bytes", "lbcg_upload_state",
-            "lbcg_download_state", "lbcg_set_sweep", "lbcg_set_tile", "lbcg_profile", "lbcg_kernel_times", "lbcg_launches_per_step", "lbcg_step_launches", "lbcg_total_nodes", "lbcg_destroy",
+            "lbcg_download_state", "lbcg_set_sweep", "lbcg_set_tile", "lbcg_profile", "lbcg_kernel_times", "lbcg_launches_per_step", "lbcg_step_host", "lbcg_step_launches", "lbcg_total_nodes", "lbcg_destroy",
             "lbcg_last_error", "lbcg_field_moments_noalloc", "lbcg_adjoint", "lbcg_autotune", "lbcg_schedule", "lbcg_diagnostics",
             "lbcg_set_poll_limit", "lbcg_set_allocator"]
 
@@ -231,6 +232,10 @@ def lbcg_upload_state(h: int, ptr: int, nbytes: int):
 
 def lbcg_download_state(h: int, ptr: int, nbytes: int):
     _check(library().lbcg_download_state(h, ptr, nbytes))
+
+
+def lbcg_step_host(h: int, ptr_in: int, ptr_out: int, nbytes: int, nsteps: int):
+    _check(library().lbcg_step_host(h, ptr_in, ptr_out, nbytes, nsteps))
 
 
 def lbcg_set_tile(h: int, ty: int):
