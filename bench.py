@@ -503,6 +503,7 @@ def run_ours(args):
     pin = torch.empty(sb, dtype=torch.uint8, pin_memory=True)
     lbcg.lbcg_download_state(lat.h, pin.data_ptr(), sb)
     Ke = max(3, min(args.steps, 20))
+    lbcg.lbcg_step_host(lat.h, pin.data_ptr(), pin.data_ptr(), sb, 1)   # untimed: its streams and events
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(Ke):

@@ -234,9 +234,9 @@ void build_strips(lbcg_handle* h, std::vector<int4>& strips) {
   for (const LatHost& L : h->lats) nx_strips += (L.nx + W - 1) / W;
   // automatic segment height: split the strips into about 32 blocks per SM (FP64: 8), with
   // at least 24 rows per segment (FP64: 8), since each segment also sweeps 4 warm-up rows.
-  // Blocks are launched in lattice / strip / segment order, so neighbouring segments run
-  // together and their shared halo rows stay in L2.  (Measured on a 64-channel batch and an
-  // 8192 x 4096 box: 32 blocks per SM beat 16 by 1.5-5 %; segments under 24 rows lose.)
+  // Blocks are launched in lattice / segment row / strip order (below).  (Measured on a
+  // 64-channel batch and an 8192 x 4096 box: 32 blocks per SM beat 16 by 1.5-5 %; segments
+  // under 24 rows lose.)
   const bool fp64 = h->prec == LBCG_FP64;
   const long long target = fp64 ? 152LL * 8 : 152LL * 32;
   const int min_rows = fp64 ? 8 : 24;
@@ -247,11 +247,14 @@ void build_strips(lbcg_handle* h, std::vector<int4>& strips) {
       const long long k = nx_strips >= target ? 1 : (target + nx_strips - 1) / nx_strips;
       rows = int(std::max<long long>(min_rows, (L.ny + k - 1) / k));
     }
-    // the FP32-arithmetic sweep walks every other segment of a strip downwards, so that the
-    // two segments at each boundary reach its rows at about the same time (their second read
-    // then hits L2); neighbouring strips keep the same pattern and run side by side
-    for (int x0 = 0; x0 < L.nx; x0 += W)
-      for (int y0 = 0, k = 0; y0 < L.ny; y0 += rows, ++k) {
+    // Blocks go out segment row by segment row (all strips of segment row 0, then row 1, ...),
+    // so that the blocks resident at a time cover whole bands of rows: x-neighbouring strips
+    // share their halo segments in L2.  The FP32-arithmetic sweep walks every other segment
+    // row downwards, so that the two segments at each boundary reach its rows at about the
+    // same time (their second read then hits L2).  (8192 x 4096 box: strip by strip instead,
+    // 157 B of DRAM traffic per fluid node and 0.886 ms per sweep; this order 147 B, 0.827 ms.)
+    for (int y0 = 0, k = 0; y0 < L.ny; y0 += rows, ++k)
+      for (int x0 = 0; x0 < L.nx; x0 += W) {
         const int y1 = std::min(y0 + rows, L.ny);
         bool any = false;
         for (int y = y0; y < y1 && !any; ++y)
