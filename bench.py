@@ -452,9 +452,11 @@ def run_ours(args):
     lat = lbcg.Lattice(geoms, prms, args.precision, stream=stream.cuda_stream)
     if args.ty:
         lat.set_tile(args.ty)
+    elif args.rows:
+        lat.set_sweep(args.rows)
     else:
         lat.autotune(AUTOTUNE_PROBE)   # sweep segment heights and tile shapes, on the initial state
-    sched = lat.schedule
+    sched, rows = lat.schedule, lat.sweep_rows
     lat.step(args.warmup)
     torch.cuda.synchronize()
     flush = torch.zeros(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda") if lat.state_bytes < 2 * L2_BYTES \
@@ -495,7 +497,9 @@ def run_ours(args):
             "traffic": traffic, "kernel": kname, "peak_source": peak_src,
             "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": step_ms,
             "kernel_ms_share": {"k_wall": kms[0] / ms_prof, "step kernel": kms[1] / ms_prof},
-            "kernel_ms_source": f"separate pass of {Kp} steps with CUDA events around each kernel"}
+            "kernel_ms_source": f"separate pass of {Kp} steps launched as the graph's branches, CUDA events "
+                                "around each kernel; per step, the time during which at least one branch's "
+                                "kernel of that kind ran (union of the event intervals)"}
     whole_gbs = alg_bytes * args.steps / (ms / 1e3) / 1e9
 
     # ---- end to end through the C ABI with host buffers (pinned): upload state, step, download
@@ -570,8 +574,10 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
                 "config": {"workload": args.workload, "description": desc, "lattices": len(geoms), "nodes": nodes,
-                           "schedule": (f"tiles 32x{sched}" if sched else "y-sweep, 124-column strips") +
-                           ("" if args.ty else " (chosen by lbcg_autotune)"),
+                           "schedule": (f"tiles 32x{sched}" if sched else
+                                        "y-sweep, 124-column strips, " +
+                                        (f"{rows}-row segments" if rows else "automatic segment height")) +
+                           ("" if (args.ty or args.rows) else " (chosen by lbcg_autotune)"),
                            "fluid_nodes_per_gpu": nf, "precision": args.precision,
                            "state_bytes": sb, "l2": "flushed before every timed step" if flush is not None
                            else "inputs larger than L2", "mlups_counts": "fluid-node updates"},
@@ -595,6 +601,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=("fp64", "fp32", "fp16", "bf16"))
     ap.add_argument("--lattices", type=int, default=64, help="channels of the batched sweep")
     ap.add_argument("--ty", type=int, default=0, help="tile height of k_step (4, 8, 16; 0 = default)")
+    ap.add_argument("--rows", type=int, default=0,
+                    help="y-sweep with this many rows per strip segment instead of lbcg_autotune's choice")
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")

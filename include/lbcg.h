@@ -273,14 +273,17 @@ lbcg_status lbcg_adjoint(lbcg_handle* h, const lbcg_adjoint_spec* spec, lbcg_gra
 /* Schedule of the step kernel.  lbcg_create picks the y-sweep over 124-column strips when
  * the strips give each of the 152 SMs a block, else 32-wide tiles (height 4 for FP64,
  * 8 otherwise); lbcg_set_sweep / lbcg_set_tile choose one explicitly.  lbcg_autotune times
- * `probe_steps` launches of each candidate (the sweep with automatic segments and with
- * segments of 24, 32, 48 and 64 rows; tiles 4, 8, 16) on the current state without advancing
- * it, keeps the fastest and writes it to *schedule (0 = sweep, else the tile height;
+ * each candidate (the sweep with automatic segments and with segments of 24, 32, 40, 48, 56,
+ * 64 and 80 rows; tiles 4, 8, 16) as lbcg_step runs it, a captured graph of `probe_steps`
+ * steps (with a batch's parallel branches) that rewrite the same next state from the current
+ * one without advancing it, keeps the fastest and writes it to *schedule (0 = sweep, else the tile height;
  * schedule may be NULL).  It synchronises the handle's stream.  The candidates
  * give the same result up to rounding order (FP32: a few ulp per step; FP64 within 1e-13).
- * lbcg_schedule reports the current choice with the same encoding. */
+ * lbcg_schedule reports the current choice with the same encoding, lbcg_sweep_rows the
+ * sweep's rows per strip segment (0: the automatic height; -1 for a NULL handle). */
 lbcg_status lbcg_autotune(lbcg_handle* h, int32_t probe_steps, int32_t* schedule);
 lbcg_status lbcg_schedule(const lbcg_handle* h, int32_t* schedule);
+int32_t lbcg_sweep_rows(const lbcg_handle* h);
 
 /* Steady-state diagnostics of Sec. III, in FP64 over one lattice's fluid nodes.
  *   e1: Eq. 45, max(|u_x - u_x'|, |u_y - u_y'|) between the current velocity and the one stored
@@ -303,12 +306,16 @@ typedef struct {
 } lbcg_diag;
 lbcg_status lbcg_diagnostics(lbcg_handle* h, int32_t lattice, const lbcg_diag_spec* spec, lbcg_diag* out);
 
-/* Kernel timing with CUDA events on the handle's stream.  While enabled, lbcg_step launches
- * the kernels of each step directly (no graph) with an event recorded before and after each
- * of its two kernels: the wall kernel (rho^N on the wall band, Eq. 28-36 on the outermost fluid
- * nodes) and the step kernel (y-sweep or tiles).  lbcg_kernel_times synchronises, returns in
- * ms2[0..1] the summed milliseconds of those two kernels over the steps taken since the last
- * call (or since enabling) and their number in *steps, and restarts the sums. */
+/* Kernel timing with CUDA events.  While enabled, lbcg_step launches the kernels of each step
+ * directly (no graph) in the arrangement its graph replays: a batch's lattice groups as
+ * parallel branches, each on its own stream (forked from the handle's stream once per call and
+ * joined back when the call returns), with an event recorded before and after each kernel: the
+ * wall kernel (rho^N on the wall band, Eq. 28-36 on the outermost fluid nodes) and the step
+ * kernel (y-sweep or tiles).  lbcg_kernel_times synchronises and returns in ms2[0..1], for the
+ * wall kernels and for the step kernels of the steps taken since the last call (or since
+ * enabling), the milliseconds during which at least one of them ran (the length of the union
+ * of their event intervals; with one branch, the sum of the kernel times), the number of steps
+ * in *steps, and restarts. */
 lbcg_status lbcg_profile(lbcg_handle* h, int32_t enable);
 lbcg_status lbcg_kernel_times(lbcg_handle* h, double* ms2, int64_t* steps);
 

@@ -122,8 +122,12 @@ struct lbcg_handle {
   std::vector<uint8_t> flags_host;
   std::vector<OfbEntry> ofb_host;
   bool profiling = false;
-  std::vector<cudaEvent_t> events;   // 4 per profiled step
+  std::vector<cudaEvent_t> events;   // 4 per profiled launch pair (wall kernel, step kernel)
   size_t events_used = 0;
+  int64_t prof_steps = 0;            // steps profiled since the last lbcg_kernel_times
+  cudaEvent_t prof_ref = nullptr;    // timing origin of the profiled launches
+  bool prof_ref_set = false;
+  bool prof_forked = false;          // the branch streams of a profiled batch await their join
 };
 
 namespace {
@@ -332,6 +336,7 @@ void free_handle(lbcg_handle* h) {
   if (!h) return;
   if (h->graph) cudaGraphExecDestroy(h->graph);
   for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+  if (h->prof_ref) cudaEventDestroy(h->prof_ref);
   void* ptrs[] = {h->pool[0], h->pool[1], h->d_flags,  h->d_wall,  h->d_macro, h->d_lats,
                   h->d_tiles, h->d_groups, h->d_wband, h->d_wvirt, h->d_wsten, h->d_ofb,
                   h->d_obs,   h->d_strips, h->d_nbmask, h->d_err, h->d_usnap, h->d_sr_epoch};
@@ -444,6 +449,81 @@ lbcg_status run_macro(lbcg_handle* h, int lat) {
 }  // namespace
 
 void lbcg::set_last_error(const char* msg) { g_err = msg; }
+
+namespace {
+
+// the streams and fork / join events of a batch's parallel branches
+cudaError_t ensure_branches(lbcg_handle* h) {
+  cudaError_t e = cudaSuccess;
+  if (!h->ev_fork) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+  for (int b = 1; b < h->nbranch && e == cudaSuccess; ++b) {
+    if (!h->br_stream[b]) e = cudaStreamCreateWithFlags(&h->br_stream[b], cudaStreamNonBlocking);
+    if (e == cudaSuccess && !h->ev_join[b]) e = cudaEventCreateWithFlags(&h->ev_join[b], cudaEventDisableTiming);
+  }
+  return e;
+}
+
+// Captures nsteps steps into an executable graph.  A batch runs as h->nbranch parallel
+// branches (branches 1.. forked from the handle's stream at the start and joined back at the
+// end).  probe = false: the steps advance from pool A (step k reads pool k & 1) and carry their
+// index k within the replay; 16-bit storage first advances the replay counter that keys the
+// stochastic rounding.  probe = true (lbcg_autotune): every step reads the current state and
+// writes the other pool, so replays do not advance the simulation, and the counter is left
+// alone.  *nk: the kernel nodes captured.
+lbcg_status capture_steps(lbcg_handle* h, int nsteps, bool probe, cudaGraphExec_t* out, int64_t* nk) {
+  cudaGraph_t g = nullptr;
+  CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t le = cudaSuccess;
+  *nk = 0;
+  if (!probe && h->prec >= 2) {
+    le = launch_sr_tick(h->d_sr_epoch, h->stream);
+    *nk += 1;
+  }
+  int nfork = 0;   // branches 1 .. nfork have joined the capture
+  if (h->nbranch > 1 && le == cudaSuccess) {
+    le = ensure_branches(h);
+    if (le == cudaSuccess) le = cudaEventRecord(h->ev_fork, h->stream);
+    for (int b = 1; b < h->nbranch && le == cudaSuccess; ++b) {
+      le = cudaStreamWaitEvent(h->br_stream[b], h->ev_fork, 0);
+      if (le == cudaSuccess) nfork = b;
+    }
+  }
+  const bool forked = h->nbranch > 1 && nfork == h->nbranch - 1 && le == cudaSuccess;
+  for (int k = 0; k < nsteps && le == cudaSuccess; ++k) {
+    const int src = probe ? h->cur : (k & 1);
+    if (forked) {
+      for (int b = 0; b < h->nbranch && le == cudaSuccess; ++b) {
+        LaunchStep q = make_launch_lats(h, src, h->br_lat[b], h->br_lat[b + 1]);
+        q.sr_step = uint32_t(k);
+        le = launch_step(h->prec, q, b ? h->br_stream[b] : h->stream);
+        *nk += step_kernels(q);
+      }
+    } else {
+      LaunchStep q = make_launch(h, src, nullptr, 0, h->ntiles);
+      q.sr_step = uint32_t(k);
+      le = launch_step(h->prec, q, h->stream);
+      *nk += step_kernels(q);
+    }
+  }
+  // join every forked branch, also after a failed launch, so that the capture can end
+  for (int b = 1; b <= nfork; ++b) {
+    const cudaError_t je = cudaEventRecord(h->ev_join[b], h->br_stream[b]);
+    const cudaError_t we = je == cudaSuccess ? cudaStreamWaitEvent(h->stream, h->ev_join[b], 0) : je;
+    if (le == cudaSuccess) le = we;
+  }
+  const cudaError_t ee = cudaStreamEndCapture(h->stream, &g);
+  if (le != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return cuda_fail(h, le, "launch during capture");
+  }
+  if (ee != cudaSuccess) return cuda_fail(h, ee, "cudaStreamEndCapture");
+  const cudaError_t ie = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (ie != cudaSuccess) return cuda_fail(h, ie, "cudaGraphInstantiate");
+  return LBCG_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -674,18 +754,34 @@ lbcg_status lbcg_step(lbcg_handle* h, int64_t nsteps) {
   if (nsteps < 0) return fail(LBCG_E_ARG, "nsteps < 0");
   while (nsteps > 0) {
     if (h->profiling) {
-      if (h->events.size() < h->events_used + 4) {
-        for (int k = 0; k < 4; ++k) {
-          cudaEvent_t e;
-          CK(h, cudaEventCreate(&e));
-          h->events.push_back(e);
-        }
+      // direct launches in the graph's arrangement: a batch's branches on their own streams,
+      // forked once and joined when this call ends; events before and after every kernel
+      const int nb = h->nbranch;
+      if (!h->prof_ref) CK(h, cudaEventCreate(&h->prof_ref));
+      if (!h->prof_ref_set) {
+        CK(h, cudaEventRecord(h->prof_ref, h->stream));
+        h->prof_ref_set = true;
       }
-      LaunchStep p = make_launch(h, h->cur, nullptr, 0, h->ntiles);
-      p.ev = h->events.data() + h->events_used;
-      h->events_used += 4;
-      CK(h, launch_step(h->prec, p, h->stream));
-      h->step_launches += step_kernels(p);
+      if (nb > 1 && !h->prof_forked) {
+        CK(h, ensure_branches(h));
+        CK(h, cudaEventRecord(h->ev_fork, h->stream));
+        for (int b = 1; b < nb; ++b) CK(h, cudaStreamWaitEvent(h->br_stream[b], h->ev_fork, 0));
+        h->prof_forked = true;
+      }
+      while (h->events.size() < h->events_used + 4 * size_t(nb)) {
+        cudaEvent_t e;
+        CK(h, cudaEventCreate(&e));
+        h->events.push_back(e);
+      }
+      for (int b = 0; b < nb; ++b) {
+        LaunchStep p = nb > 1 ? make_launch_lats(h, h->cur, h->br_lat[b], h->br_lat[b + 1])
+                              : make_launch(h, h->cur, nullptr, 0, h->ntiles);
+        p.ev = h->events.data() + h->events_used;
+        h->events_used += 4;
+        CK(h, launch_step(h->prec, p, b ? h->br_stream[b] : h->stream));
+        h->step_launches += step_kernels(p);
+      }
+      h->prof_steps += 1;
       h->cur ^= 1;
       h->step += 1;
       nsteps -= 1;
@@ -693,57 +789,8 @@ lbcg_status lbcg_step(lbcg_handle* h, int64_t nsteps) {
     }
     if (nsteps >= kGraphSteps && h->cur == 0) {
       if (!h->graph) {
-        cudaGraph_t g = nullptr;
-        CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-        cudaError_t le = cudaSuccess;
-        // 16-bit storage: each replay advances the counter that keys the stochastic rounding,
-        // and the 32 captured steps carry their index within the replay
-        int64_t nk = 0;
-        if (h->prec >= 2) {
-          le = launch_sr_tick(h->d_sr_epoch, h->stream);
-          nk += 1;
-        }
-        // a batch: branches 1.. forked from the capture and joined back at its end
-        int nfork = 0;   // branches 1 .. nfork have joined the capture
-        if (h->nbranch > 1 && le == cudaSuccess) {
-          if (!h->ev_fork) le = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
-          if (le == cudaSuccess) le = cudaEventRecord(h->ev_fork, h->stream);
-          for (int b = 1; b < h->nbranch && le == cudaSuccess; ++b) {
-            if (!h->br_stream[b]) le = cudaStreamCreateWithFlags(&h->br_stream[b], cudaStreamNonBlocking);
-            if (le == cudaSuccess && !h->ev_join[b]) le = cudaEventCreateWithFlags(&h->ev_join[b], cudaEventDisableTiming);
-            if (le == cudaSuccess) le = cudaStreamWaitEvent(h->br_stream[b], h->ev_fork, 0);
-            if (le == cudaSuccess) nfork = b;
-          }
-        }
-        const bool forked = h->nbranch > 1 && nfork == h->nbranch - 1 && le == cudaSuccess;
-        for (int k = 0; k < kGraphSteps && le == cudaSuccess; ++k) {
-          if (forked) {
-            for (int b = 0; b < h->nbranch && le == cudaSuccess; ++b) {
-              LaunchStep q = make_launch_lats(h, k & 1, h->br_lat[b], h->br_lat[b + 1]);
-              q.sr_step = uint32_t(k);
-              le = launch_step(h->prec, q, b ? h->br_stream[b] : h->stream);
-              nk += step_kernels(q);
-            }
-          } else {
-            LaunchStep q = make_launch(h, k & 1, nullptr, 0, h->ntiles);
-            q.sr_step = uint32_t(k);
-            le = launch_step(h->prec, q, h->stream);
-            nk += step_kernels(q);
-          }
-        }
-        // join every forked branch, also after a failed launch, so that the capture can end
-        for (int b = 1; b <= nfork; ++b) {
-          const cudaError_t je = cudaEventRecord(h->ev_join[b], h->br_stream[b]);
-          const cudaError_t we = je == cudaSuccess ? cudaStreamWaitEvent(h->stream, h->ev_join[b], 0) : je;
-          if (le == cudaSuccess) le = we;
-        }
-        cudaError_t ee = cudaStreamEndCapture(h->stream, &g);
-        if (le != cudaSuccess) return cuda_fail(h, le, "launch during capture");
-        if (ee != cudaSuccess) return cuda_fail(h, ee, "cudaStreamEndCapture");
-        cudaError_t ie = cudaGraphInstantiate(&h->graph, g, 0);
-        cudaGraphDestroy(g);
-        if (ie != cudaSuccess) return cuda_fail(h, ie, "cudaGraphInstantiate");
-        h->graph_kernels = nk;
+        const lbcg_status cs = capture_steps(h, kGraphSteps, false, &h->graph, &h->graph_kernels);
+        if (cs != LBCG_OK) return cs;
       }
       CK(h, cudaGraphLaunch(h->graph, h->stream));
       h->step_launches += h->graph_kernels;
@@ -757,6 +804,13 @@ lbcg_status lbcg_step(lbcg_handle* h, int64_t nsteps) {
     h->cur ^= 1;
     h->step += 1;
     nsteps -= 1;
+  }
+  if (h->prof_forked) {   // the profiled branches rejoin the handle's stream
+    for (int b = 1; b < h->nbranch; ++b) {
+      CK(h, cudaEventRecord(h->ev_join[b], h->br_stream[b]));
+      CK(h, cudaStreamWaitEvent(h->stream, h->ev_join[b], 0));
+    }
+    h->prof_forked = false;
   }
   return LBCG_OK;
 }
@@ -1486,13 +1540,16 @@ lbcg_status lbcg_autotune(lbcg_handle* h, int32_t probe_steps, int32_t* schedule
     cudaGraphExecDestroy(h->graph);
     h->graph = nullptr;
   }
-  // the y-sweep at the automatic segment height and at fixed heights, then the tiles
+  // the y-sweep at the automatic segment height and at fixed heights, then the tiles; each
+  // timed as what lbcg_step replays: a captured graph of probe_steps steps (with a batch's
+  // parallel branches), whose steps all rewrite the same next state
   struct Cand {
     int sweep, ty, rows;
   };
-  const Cand cand[8] = {{1, h->ty, 0}, {1, h->ty, 24}, {1, h->ty, 32}, {1, h->ty, 48},
-                        {1, h->ty, 64}, {0, 4, 0},     {0, 8, 0},     {0, 16, 0}};
-  const int ncand = 8;
+  const Cand cand[] = {{1, h->ty, 0}, {1, h->ty, 24}, {1, h->ty, 32}, {1, h->ty, 40}, {1, h->ty, 48},
+                       {1, h->ty, 56}, {1, h->ty, 64}, {1, h->ty, 80}, {0, 4, 0},      {0, 8, 0},
+                       {0, 16, 0}};
+  const int ncand = int(sizeof(cand) / sizeof(cand[0]));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   CK(h, cudaEventCreate(&e0));
   cudaError_t e = cudaEventCreate(&e1);
@@ -1504,14 +1561,16 @@ lbcg_status lbcg_autotune(lbcg_handle* h, int32_t probe_steps, int32_t* schedule
     h->sweep_rows = cand[c].rows;
     s = upload_tiles(h);
     if (s != LBCG_OK) break;
-    // src = current state, dst = the other buffer: repeated launches rewrite the same next
-    // state, so the probe does not advance the simulation
-    const LaunchStep p = make_launch(h, h->cur, nullptr, 0, h->ntiles);
-    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = launch_step(h->prec, p, h->stream);
+    cudaGraphExec_t gx = nullptr;
+    int64_t nk = 0;
+    s = capture_steps(h, probe_steps, true, &gx, &nk);
+    if (s != LBCG_OK) break;
+    e = cudaGraphLaunch(gx, h->stream);   // first replay: uploads the graph, warms the caches
     if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
-    for (int k = 0; k < probe_steps && e == cudaSuccess; ++k) e = launch_step(h->prec, p, h->stream);
+    if (e == cudaSuccess) e = cudaGraphLaunch(gx, h->stream);
     if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    cudaGraphExecDestroy(gx);
     float ms = 0.f;
     if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
     if (e == cudaSuccess && (c == 0 || ms < best_ms)) {
@@ -1540,12 +1599,16 @@ lbcg_status lbcg_schedule(const lbcg_handle* h, int32_t* schedule) {
   return LBCG_OK;
 }
 
+int32_t lbcg_sweep_rows(const lbcg_handle* h) { return h ? h->sweep_rows : -1; }
+
 lbcg_status lbcg_profile(lbcg_handle* h, int32_t enable) {
   lbcg_status s = check_handle(h);
   if (s != LBCG_OK) return s;
   CK(h, cudaStreamSynchronize(h->stream));
   h->profiling = enable != 0;
   h->events_used = 0;
+  h->prof_steps = 0;
+  h->prof_ref_set = false;
   return LBCG_OK;
 }
 
@@ -1555,14 +1618,34 @@ lbcg_status lbcg_kernel_times(lbcg_handle* h, double* ms2, int64_t* steps) {
   if (!ms2 || !steps) return fail(LBCG_E_ARG, "NULL output");
   CK(h, cudaStreamSynchronize(h->stream));
   ms2[0] = ms2[1] = 0.0;
-  for (size_t i = 0; i + 4 <= h->events_used; i += 4)
-    for (int k = 0; k < 2; ++k) {
-      float t = 0.f;
-      CK(h, cudaEventElapsedTime(&t, h->events[i + 2 * k], h->events[i + 2 * k + 1]));
-      ms2[k] += t;
+  // per kernel kind, the length of the union of its launches' event intervals (the time at
+  // least one of them ran: branches of a batch overlap; one branch gives the plain sum)
+  for (int k = 0; k < 2; ++k) {
+    std::vector<std::pair<float, float>> iv;
+    for (size_t i = 0; i + 4 <= h->events_used; i += 4) {
+      float t0 = 0.f, t1 = 0.f;
+      CK(h, cudaEventElapsedTime(&t0, h->prof_ref, h->events[i + 2 * k]));
+      CK(h, cudaEventElapsedTime(&t1, h->prof_ref, h->events[i + 2 * k + 1]));
+      iv.emplace_back(t0, t1);
     }
-  *steps = (int64_t)(h->events_used / 4);
+    std::sort(iv.begin(), iv.end());
+    double total = 0.0, a = 0.0, b = -1e30;
+    for (const auto& q : iv) {
+      if (q.first > b) {
+        if (b > a) total += b - a;
+        a = q.first;
+        b = q.second;
+      } else if (q.second > b) {
+        b = q.second;
+      }
+    }
+    if (b > a) total += b - a;
+    ms2[k] = total;
+  }
+  *steps = h->prof_steps;
   h->events_used = 0;
+  h->prof_steps = 0;
+  h->prof_ref_set = false;
   return LBCG_OK;
 }
 

@@ -134,6 +134,7 @@ def library():
         "lbcg_autotune": (C.c_int, [H, C.c_int32, C.POINTER(C.c_int32)]),
         "lbcg_diagnostics": (C.c_int, [H, C.c_int32, C.POINTER(lbcg_diag_spec), C.POINTER(lbcg_diag)]),
         "lbcg_schedule": (C.c_int, [H, C.POINTER(C.c_int32)]),
+        "lbcg_sweep_rows": (C.c_int32, [H]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -147,7 +148,7 @@ def exported_symbols() -> list:
     return ["lbcg_create", "lbcg_create_batch", "lbcg_step", "lbcg_observables", "lbcg_get_populations",
             "lbcg_set_populations", "lbcg_get_fields", "lbcg_state_bytes", "lbcg_upload_state",
             "lbcg_download_state", "lbcg_set_sweep", "lbcg_set_tile", "lbcg_profile", "lbcg_kernel_times", "lbcg_launches_per_step", "lbcg_step_host", "lbcg_step_launches", "lbcg_total_nodes", "lbcg_destroy",
-            "lbcg_last_error", "lbcg_field_moments_noalloc", "lbcg_adjoint", "lbcg_autotune", "lbcg_schedule", "lbcg_diagnostics",
+            "lbcg_last_error", "lbcg_field_moments_noalloc", "lbcg_adjoint", "lbcg_autotune", "lbcg_schedule", "lbcg_sweep_rows", "lbcg_diagnostics",
             "lbcg_set_poll_limit", "lbcg_set_allocator"]
 
 
@@ -425,6 +426,10 @@ class Lattice:
     @property
     def schedule(self) -> int:
         return lbcg_schedule(self.h)
+
+    @property
+    def sweep_rows(self) -> int:
+        return int(library().lbcg_sweep_rows(self.h))
 
     @property
     def state_bytes(self) -> int:

@@ -266,6 +266,31 @@ def test_step_launch_count_of_direct_steps_and_branched_graphs():
     B.close()
 
 
+def test_profiled_branched_steps_time_their_kernels_and_keep_the_bits():
+    # profiling launches a batch's branches directly on their streams with events around each
+    # kernel: the results equal unprofiled steps, and the kernel times (union of the branches'
+    # intervals) fit inside the elapsed time of the steps
+    from paper_1707_00198_gb300 import lbcg
+    gs, ps = I.channel_sweep(6, seed=2, wmin=20, wmax=50)
+    A, B = lbcg.Lattice(gs, ps, "fp32"), lbcg.Lattice(gs, ps, "fp32")
+    lbcg.lbcg_profile(A.h, True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    A.step(10)
+    kms, n = lbcg.lbcg_kernel_times(A.h)
+    e1.record()
+    torch.cuda.synchronize()
+    lbcg.lbcg_profile(A.h, False)
+    B.step(10)
+    assert n == 10 and kms[0] > 0 and kms[1] > 0
+    assert kms[1] <= e0.elapsed_time(e1) * 1.05 + 0.05, (kms, e0.elapsed_time(e1))
+    for i in range(len(gs)):
+        assert np.array_equal(A.populations(i), B.populations(i)), i
+    A.close()
+    B.close()
+
+
 def test_graph_replay_matches_direct_steps():
     # 70 steps use two 32-step graph replays plus direct launches; 70 single calls use none
     g, p = I.config_static_droplet()
@@ -364,6 +389,27 @@ def test_autotune_keeps_the_state_and_parity():
     out = L.populations()
     L.close()
     assert float(np.abs(out - ref).max()) <= TOL64
+
+
+def test_autotune_of_a_batch_keeps_the_state_and_the_rounding_keys():
+    # the probes are captured graphs with the batch's parallel branches; they rewrite the same
+    # next state and leave the stochastic-rounding replay counter alone, so a 16-bit batch that
+    # autotunes and one that does not step to the same bits (sweep heights do not change bits)
+    from paper_1707_00198_gb300.lbcg import Lattice
+    gs, ps = I.channel_sweep(7, seed=5, wmin=20, wmax=60)
+    A, B = Lattice(gs, ps, "fp16"), Lattice(gs, ps, "fp16")
+    A.step(5)
+    B.step(5)
+    before = [A.populations(i) for i in range(len(gs))]
+    sched = A.autotune(3)
+    assert all(np.array_equal(A.populations(i), b) for i, b in enumerate(before))
+    A.step(40)
+    B.step(40)
+    if sched == 0 and B.schedule == 0:
+        for i in range(len(gs)):
+            assert np.array_equal(A.populations(i), B.populations(i)), i
+    A.close()
+    B.close()
 
 
 def test_wettability_slopes_of_the_paper():
