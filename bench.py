@@ -362,6 +362,38 @@ def sequential_rate(lbcg, geoms, prms, precision: str, K: int, W: int, stream) -
             "schedules": "each handle's own lbcg_autotune choice"}
 
 
+def config_rates(lbcg, stream, K: int = 640) -> dict:
+    """MLUPS of single lattices at the paper's configuration sizes, each on the schedule
+    lbcg_autotune picks for it and replayed from its CUDA graph: the static droplet (100x50,
+    FP64), capillary filling (1200x80, FP32) and the fingering channel (2000x102, M=1, Ca=0.05,
+    theta=90 deg; FP32, FP16 and BF16 storage).  Their states fit in L2 and are not flushed
+    between steps, so these are L2-resident rates."""
+    cases = [("static_droplet_100x50", I.config_static_droplet(), ("fp64",)),
+             ("capillary_1200x80", I.config_capillary(), ("fp64", "fp32")),
+             ("fingering_2000x102", I.config_fingering(M=1.0, Ca=0.05, theta_deg=90.0), ("fp32", "fp16", "bf16"))]
+    out = {"l2": "resident (states of 0.7-30 MB, not flushed)", "steps": K}
+    for name, (g, p), precs in cases:
+        nf = int((g.solid == 0).sum())
+        for prec in precs:
+            L = lbcg.Lattice(g, p, prec, stream=stream.cuda_stream)
+            try:
+                L.autotune(AUTOTUNE_PROBE)
+                L.step(64)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                L.step(K)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+                out[f"{name}_{prec}"] = {"MLUPS": nf * K / (ms / 1e3) / 1e6, "us_per_step": ms / K * 1e3,
+                                         "schedule": f"tiles 32x{L.schedule}" if L.schedule else
+                                         f"y-sweep, {L.sweep_rows or 'automatic'}-row segments"}
+            finally:
+                L.close()
+    return out
+
+
 def observable_errors(lbcg, stream) -> dict:
     """Error of each storage form's observables against an FP64 run of the same case: the
     sessile droplet (100x50, theta 60 deg) after 2000 steps -- contact angle and colour masses --
@@ -556,6 +588,8 @@ def run_ours(args):
 
     # ---- observable error of the storage forms against FP64 (rank 0)
     obs_err = observable_errors(lbcg, stream) if (rank == 0 and not args.no_forms) else None
+    # ---- single lattices at the paper's configuration sizes (rank 0)
+    cfg_rates = config_rates(lbcg, stream) if (rank == 0 and not args.no_forms) else None
 
     # ---- the discrete adjoint on the 400x42 channel (FP64, rank 0)
     adj = None
@@ -583,7 +617,8 @@ def run_ours(args):
                            else "inputs larger than L2", "mlups_counts": "fluid-node updates"},
                 "hbm_gbs_alg": whole_gbs, "hbm_frac_alg": whole_gbs / peak,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-                "forms": forms, "observable_error_vs_fp64": obs_err, "batched_vs_sequential": seq, "adjoint": adj,
+                "forms": forms, "observable_error_vs_fp64": obs_err, "batched_vs_sequential": seq,
+                "config_sizes": cfg_rates, "adjoint": adj,
                 "nonfinite_lattice0": obs.get("nonfinite", None)}
         print(json.dumps(line), flush=True)
     if ws > 1:
