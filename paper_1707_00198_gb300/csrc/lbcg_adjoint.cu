@@ -587,6 +587,29 @@ __device__ __forceinline__ void adj_rho_body(const AdjDevT<R>& A, const int i) {
 
 inline int nblk(int n) { return (n + kAdjThreads - 1) / kAdjThreads; }
 
+// Programmatic dependent launch.  The kernels of a reverse sweep are short, latency-bound
+// grids, each depending on the one before it.  A kernel launched by launch_dep may be scheduled
+// once every block of the kernel before it has run its dep_trigger (placed after all of a
+// block's stores) or exited; its threads wait in dep_wait (the hardware's wait for the full
+// completion and memory flush of that kernel) before they read anything.  So the next grid's
+// launch overlaps the tail of the last one.  For a kernel launched the ordinary way both
+// instructions do nothing.
+__device__ __forceinline__ void dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void dep_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+template <typename... P, typename... Q>
+cudaError_t launch_dep(void (*k)(P...), int grid, cudaStream_t st, Q... args) {
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(unsigned(grid));
+  cfg.blockDim = dim3(kAdjThreads);
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 // Forward intermediates of one state (the prologue of a segment's reverse sweep).
 template <typename R>
 __global__ void __launch_bounds__(kAdjThreads) k_fwd_local(AdjDevT<R> A) {
@@ -595,13 +618,17 @@ __global__ void __launch_bounds__(kAdjThreads) k_fwd_local(AdjDevT<R> A) {
 }
 template <typename R>
 __global__ void __launch_bounds__(kAdjThreads) k_fwd_grad(AdjDevT<R> A) {
+  dep_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < A.N) fwd_grad_body(A, i);
+  dep_trigger();
 }
 template <typename R>
 __global__ void __launch_bounds__(kAdjThreads) k_fwd_dn(AdjDevT<R> A) {
+  dep_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < A.N) fwd_dn_body(A, i);
+  dep_trigger();
 }
 
 // The reverse of step j (A) in three stages, each paired in one launch with the stage of the
@@ -615,25 +642,34 @@ template <typename R>
 __global__ void __launch_bounds__(kAdjThreads) k_rev_collide(AdjDevT<R> A, AdjDevT<R> B, int nrev) {
   const bool rev = int(blockIdx.x) < nrev;
   const int i = (rev ? blockIdx.x : blockIdx.x - nrev) * blockDim.x + threadIdx.x;
-  if (i >= A.N) return;
-  if (rev) adj_collide_body(A, i);
-  else fwd_local_body(B, i);
+  dep_wait();
+  if (i < A.N) {
+    if (rev) adj_collide_body(A, i);
+    else fwd_local_body(B, i);
+  }
+  dep_trigger();
 }
 template <typename R>
 __global__ void __launch_bounds__(kAdjThreads) k_rev_normal(AdjDevT<R> A, AdjDevT<R> B, int nrev) {
   const bool rev = int(blockIdx.x) < nrev;
   const int i = (rev ? blockIdx.x : blockIdx.x - nrev) * blockDim.x + threadIdx.x;
-  if (i >= A.N) return;
-  if (rev) adj_normal_body(A, i);
-  else fwd_grad_body(B, i);
+  dep_wait();
+  if (i < A.N) {
+    if (rev) adj_normal_body(A, i);
+    else fwd_grad_body(B, i);
+  }
+  dep_trigger();
 }
 template <typename R>
 __global__ void __launch_bounds__(kAdjThreads) k_rev_rho(AdjDevT<R> A, AdjDevT<R> B, int nrev) {
   const bool rev = int(blockIdx.x) < nrev;
   const int i = (rev ? blockIdx.x : blockIdx.x - nrev) * blockDim.x + threadIdx.x;
-  if (i >= A.N) return;
-  if (rev) adj_rho_body(A, i);
-  else fwd_dn_body(B, i);
+  dep_wait();
+  if (i < A.N) {
+    if (rev) adj_rho_body(A, i);
+    else fwd_dn_body(B, i);
+  }
+  dep_trigger();
 }
 template <typename R>
 __global__ void __launch_bounds__(kAdjThreads) k_adj_rho(AdjDevT<R> A) {
@@ -674,9 +710,10 @@ template <typename R>
 cudaError_t adjoint_forward(const AdjDevT<R>& A, cudaStream_t st) {
   const int b = nblk(A.N);
   k_fwd_local<R><<<b, kAdjThreads, 0, st>>>(A);
-  k_fwd_grad<R><<<b, kAdjThreads, 0, st>>>(A);
-  k_fwd_dn<R><<<b, kAdjThreads, 0, st>>>(A);
-  return cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = launch_dep(k_fwd_grad<R>, b, st, A);
+  if (e == cudaSuccess) e = launch_dep(k_fwd_dn<R>, b, st, A);
+  return e;
 }
 
 // One reverse step: lam <- (d step / d state)^T lam_next, parameter adjoints accumulated,
@@ -687,10 +724,10 @@ cudaError_t adjoint_step(const AdjDevT<R>& A, const AdjDevT<R>* B, cudaStream_t 
   const int b = nblk(A.N);
   const AdjDevT<R>& Bv = B ? *B : A;
   const int g = B ? 2 * b : b;
-  k_rev_collide<R><<<g, kAdjThreads, 0, st>>>(A, Bv, b);
-  k_rev_normal<R><<<g, kAdjThreads, 0, st>>>(A, Bv, b);
-  k_rev_rho<R><<<g, kAdjThreads, 0, st>>>(A, Bv, b);
-  return cudaGetLastError();
+  cudaError_t e = launch_dep(k_rev_collide<R>, g, st, A, Bv, b);
+  if (e == cudaSuccess) e = launch_dep(k_rev_normal<R>, g, st, A, Bv, b);
+  if (e == cudaSuccess) e = launch_dep(k_rev_rho<R>, g, st, A, Bv, b);
+  return e;
 }
 
 template <typename R>
