@@ -101,6 +101,18 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// Programmatic dependent launch of the tile schedule (launch_all): on a small lattice a step's
+// two kernels are short grids, each waiting for the one before it, so the gap between one
+// grid's end and the next one's start is a visible part of the step.  k_wall and k_step are
+// then launched with programmatic stream serialisation: the next grid may be scheduled once
+// every block of the grid before it has run dep_trigger (after its last store) or exited, and
+// every thread of it runs dep_wait -- the hardware's wait for the full completion and memory
+// flush of that grid -- before it reads or writes anything the grid before it reads or
+// writes (populations, the wall kernel's output); only the static lattice tables are read
+// before the wait.  For a kernel launched the ordinary way both instructions do nothing.
+__device__ __forceinline__ void dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void dep_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 template <typename S>
 __global__ void __launch_bounds__(kWallThreads, sizeof(S) == 8 ? 3 : 5) k_wall(const LatDev* __restrict__ lats,
                                                           const WallGroup* __restrict__ groups,
@@ -123,8 +135,10 @@ __global__ void __launch_bounds__(kWallThreads, sizeof(S) == 8 ? 3 : 5) k_wall(c
   // the group's sizes against the shared tables (uniform over the block)
   if (!checked(G.nwall >= 0 && G.nwall <= kWallMaxNodes && G.nvirt >= 0 && G.nvirt <= kWallVirtCap &&
                    G.nband >= 1 && (G.nband + 3) / 4 * 4 <= kWallCap && G.nband + G.nvirt <= kWallCap,
-               err))
+               err)) {
+    dep_wait();
     return;
+  }
   // the group's tables, copied to shared memory in 16-byte pieces that are all in flight at
   // once (band0 is a multiple of 4 and the band list is padded, so the last piece is in bounds)
   {
@@ -151,6 +165,7 @@ __global__ void __launch_bounds__(kWallThreads, sizeof(S) == 8 ? 3 : 5) k_wall(c
   }
   if (t == 0) sL = lats[G.lat];
   cp_async_wait_all();
+  dep_wait();   // the populations of the step before are complete from here on
   __syncthreads();
   // phase 1, UW band nodes at a time: their populations first, then the Zou-He columns and
   // rho^N (indices past the end repeat the last node, so that no load sits behind a branch)
@@ -207,6 +222,7 @@ __global__ void __launch_bounds__(kWallThreads, sizeof(S) == 8 ? 3 : 5) k_wall(c
     for (int a = 0; a < 8; ++a) ok = ok && s_sten[w].i[a] < G.nband + G.nvirt;
     if (checked(ok, err)) wall_node<T>(sL, s_ofb[w], s_sten[w], val, wall, node_total);
   }
+  dep_trigger();
 }
 
 
@@ -294,6 +310,7 @@ __global__ void __launch_bounds__(32 * TY, sizeof(typename Store<S>::T) == 4 ? 1
     const long long k = (long long)sym[cy] * pitch + sxm[cx];
     sfl[i] = checked(in_extent(k, 1, sL.plane), A.err) ? fl[k] : uint8_t(F_SOLID);
   }
+  dep_wait();   // the populations and the wall kernel's output are complete from here on
   __syncthreads();
 
   auto load = [&](int c3x, int c3y, T fr_[9], T fb_[9]) {
@@ -560,6 +577,7 @@ __global__ void __launch_bounds__(32 * TY, sizeof(typename Store<S>::T) == 4 ? 1
       if (checked(in_extent((long long)k + slot * kDir, 2, 18 * sL.plane), A.err))
         store_pair_sr<S>(dst + k + slot * kDir, oR, oB, wgt<T>(a) * r0, sr_bits(srh, a));
     }
+    dep_trigger();
   }
 }
 
@@ -1466,17 +1484,37 @@ __global__ void k_from_storage(const LatDev* __restrict__ lats, int lat, const S
 // advances the replay counter of the stochastic-rounding keys (once per replayed graph)
 __global__ void k_sr_tick(uint32_t* epoch) { *epoch += 1u; }
 
+// launches kernel k on `grid` blocks of `block` threads; with `dep` set, as a programmatic
+// dependent launch of the kernel before it in the stream (the kernel's dep_wait orders it)
+template <typename... P, typename... Q>
+static void launch_k(void (*k)(P...), int grid, int block, cudaStream_t st, bool dep, Q... args) {
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(unsigned(grid));
+  cfg.blockDim = dim3(unsigned(block));
+  cfg.stream = st;
+  cfg.attrs = dep ? at : nullptr;
+  cfg.numAttrs = dep ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, k, static_cast<P>(args)...);   // errors: cudaGetLastError below
+}
+
 template <typename S>
 static cudaError_t launch_all(const LaunchStep& p, cudaStream_t st) {
   using T = typename Store<S>::T;
   auto rec = [&](int i) {
     if (p.ev) cudaEventRecord(p.ev[i], st);
   };
+  // the tile schedule's steps are dependent launches (not while the kernels are timed one by
+  // one with events, nor for the macro-field pass); the sweep's kernels are long enough that
+  // it measured no gain there
+  const bool tiles = !(p.sweep && p.macro == nullptr);
+  const bool dep = tiles && p.ev == nullptr && p.macro == nullptr;
   rec(0);
   if (p.ngroups > 0)
-    k_wall<S><<<p.ngroups, kWallThreads, 0, st>>>(p.lats, p.groups, p.wband, p.wvirt, p.wsten, p.ofb,
-                                                  static_cast<const S*>(p.src), static_cast<T*>(p.wall),
-                                                  p.node_total, p.err);
+    launch_k(k_wall<S>, p.ngroups, kWallThreads, st, dep, p.lats, p.groups, p.wband, p.wvirt, p.wsten, p.ofb,
+             static_cast<const S*>(p.src), static_cast<T*>(p.wall), p.node_total, p.err);
   rec(1);
   rec(2);
   if (p.sweep && p.macro == nullptr) {
@@ -1496,15 +1534,15 @@ static cudaError_t launch_all(const LaunchStep& p, cudaStream_t st) {
     switch (p.ty) {
       case 4:
         if (macro) k_step<S, 4, true><<<p.ntiles, 128, 0, st>>>(A);
-        else k_step<S, 4, false><<<p.ntiles, 128, 0, st>>>(A);
+        else launch_k(k_step<S, 4, false>, p.ntiles, 128, st, dep, A);
         break;
       case 16:
         if (macro) k_step<S, 16, true><<<p.ntiles, 512, 0, st>>>(A);
-        else k_step<S, 16, false><<<p.ntiles, 512, 0, st>>>(A);
+        else launch_k(k_step<S, 16, false>, p.ntiles, 512, st, dep, A);
         break;
       default:
         if (macro) k_step<S, 8, true><<<p.ntiles, 256, 0, st>>>(A);
-        else k_step<S, 8, false><<<p.ntiles, 256, 0, st>>>(A);
+        else launch_k(k_step<S, 8, false>, p.ntiles, 256, st, dep, A);
         break;
     }
   }
