@@ -105,13 +105,24 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // two kernels are short grids, each waiting for the one before it, so the gap between one
 // grid's end and the next one's start is a visible part of the step.  k_wall and k_step are
 // then launched with programmatic stream serialisation: the next grid may be scheduled once
-// every block of the grid before it has run dep_trigger (after its last store) or exited, and
-// every thread of it runs dep_wait -- the hardware's wait for the full completion and memory
-// flush of that grid -- before it reads or writes anything the grid before it reads or
-// writes (populations, the wall kernel's output); only the static lattice tables are read
-// before the wait.  For a kernel launched the ordinary way both instructions do nothing.
+// every block of the grid before it has run dep_trigger or exited, and every thread of it
+// runs dep_wait -- the hardware's wait for the full completion and memory flush of that
+// grid -- before it reads or writes anything the grid before it reads or writes
+// (populations, the wall kernel's output); only the static lattice tables are read before
+// the wait.  For a kernel launched the ordinary way both instructions do nothing.
+// Where the trigger sits decides only when the next grid's blocks are scheduled, never what
+// they read.  FP32 and 16-bit storage trigger at the start of each block: the next grid then
+// becomes resident and stages its tables while this one runs (it is scheduled only once every
+// block of this grid has started, so its waiting blocks never hold resources this grid still
+// needs); measured 1200x80 FP32 13.1 -> 10.6 us per step and 2000x102 20.2 -> 17.3 against a
+// trigger after the last store.  FP64 triggers after each block's last store: its blocks hold
+// several times the registers, and resident waiting FP64 blocks slowed the kernels running
+// beside them on another stream (the FP64 adjoint, whose recompute runs on a side stream:
+// 118 -> 177 us per step with the early trigger).
 __device__ __forceinline__ void dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void dep_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+template <typename S>
+constexpr bool kEarlyTrigger = sizeof(typename Store<S>::T) == 4;
 
 template <typename S>
 __global__ void __launch_bounds__(kWallThreads, sizeof(S) == 8 ? 3 : 5) k_wall(const LatDev* __restrict__ lats,
@@ -132,6 +143,7 @@ __global__ void __launch_bounds__(kWallThreads, sizeof(S) == 8 ? 3 : 5) k_wall(c
   __shared__ LatDev sL;
   const WallGroup G = groups[blockIdx.x];
   const int t = threadIdx.x;
+  if constexpr (kEarlyTrigger<S>) dep_trigger();
   // the group's sizes against the shared tables (uniform over the block)
   if (!checked(G.nwall >= 0 && G.nwall <= kWallMaxNodes && G.nvirt >= 0 && G.nvirt <= kWallVirtCap &&
                    G.nband >= 1 && (G.nband + 3) / 4 * 4 <= kWallCap && G.nband + G.nvirt <= kWallCap,
@@ -222,7 +234,7 @@ __global__ void __launch_bounds__(kWallThreads, sizeof(S) == 8 ? 3 : 5) k_wall(c
     for (int a = 0; a < 8; ++a) ok = ok && s_sten[w].i[a] < G.nband + G.nvirt;
     if (checked(ok, err)) wall_node<T>(sL, s_ofb[w], s_sten[w], val, wall, node_total);
   }
-  dep_trigger();
+  if constexpr (!kEarlyTrigger<S>) dep_trigger();
 }
 
 
@@ -290,6 +302,7 @@ __global__ void __launch_bounds__(32 * TY, sizeof(typename Store<S>::T) == 4 ? 1
   const int4 tl = A.tiles[blockIdx.x];
   const int x0 = tl.y, y0 = tl.z;
   const int tid = threadIdx.x;
+  if constexpr (!MACRO && kEarlyTrigger<S>) dep_trigger();
   if (tid == 0) sL = A.lats[tl.x];
   __syncthreads();
   // lattice constants in registers (shared memory cannot alias the global stores below)
@@ -577,7 +590,7 @@ __global__ void __launch_bounds__(32 * TY, sizeof(typename Store<S>::T) == 4 ? 1
       if (checked(in_extent((long long)k + slot * kDir, 2, 18 * sL.plane), A.err))
         store_pair_sr<S>(dst + k + slot * kDir, oR, oB, wgt<T>(a) * r0, sr_bits(srh, a));
     }
-    dep_trigger();
+    if constexpr (!kEarlyTrigger<S>) dep_trigger();
   }
 }
 
