@@ -54,6 +54,8 @@ def workload(name: str, rank: int = 0, lattices: int = 64):
     if name == "fingering":
         g, p = I.config_fingering(M=1.0, Ca=0.05, theta_deg=90.0, seed=0)
         return ([g], [p]), "displacement channel 2000x102, M=1, Ca=0.05, theta=90deg"
+    if name == "fingering_grid":
+        return I.fingering_grid(), "75 displacement channels 2000x102, the full (M, Ca, theta) grid"
     if name == "static_droplet":
         g, p = I.config_static_droplet()
         return ([g], [p]), "static droplet 100x50, R=20, theta=60deg"
@@ -394,6 +396,26 @@ def config_rates(lbcg, stream, K: int = 640) -> dict:
     return out
 
 
+def fingering_grid_rates(lbcg, stream, K: int = 320, W: int = 10) -> dict:
+    """MLUPS of the viscous-fingering study run as one batch -- a 2000x102 channel for each of
+    the 75 (M, Ca, theta) points of the grids (15.3 M fluid nodes) -- in FP32 and the two 16-bit
+    storage forms, each on the schedule lbcg_autotune picks and replayed from its CUDA graph.
+    The states (1.1-2.2 GB) are larger than L2."""
+    geoms, prms = I.fingering_grid()
+    nf = fluid_nodes(geoms)
+    out = {"lattices": len(geoms), "fluid_nodes": nf, "steps": K, "l2": "inputs larger than L2"}
+    for prec in ("fp32", "fp16", "bf16"):
+        L, ms, _, _ = measure_form(geoms, prms, prec, K, W, stream)
+        try:
+            out[prec] = {"MLUPS": nf * K / (ms / 1e3) / 1e6, "ms_per_step": ms / K,
+                         "hbm_gbs_alg": 36 * STORE_BYTES[prec] * nf * K / (ms / 1e3) / 1e9,
+                         "schedule": f"tiles 32x{L.schedule}" if L.schedule else
+                         f"y-sweep, {L.sweep_rows or 'automatic'}-row segments"}
+        finally:
+            L.close()
+    return out
+
+
 def observable_errors(lbcg, stream) -> dict:
     """Error of each storage form's observables against an FP64 run of the same case: the
     sessile droplet (100x50, theta 60 deg) after 2000 steps -- contact angle and colour masses --
@@ -590,6 +612,7 @@ def run_ours(args):
     obs_err = observable_errors(lbcg, stream) if (rank == 0 and not args.no_forms) else None
     # ---- single lattices at the paper's configuration sizes (rank 0)
     cfg_rates = config_rates(lbcg, stream) if (rank == 0 and not args.no_forms) else None
+    grid_rates = fingering_grid_rates(lbcg, stream) if (rank == 0 and not args.no_forms) else None
 
     # ---- the discrete adjoint on the 400x42 channel (FP64, rank 0)
     adj = None
@@ -618,7 +641,7 @@ def run_ours(args):
                 "hbm_gbs_alg": whole_gbs, "hbm_frac_alg": whole_gbs / peak,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
                 "forms": forms, "observable_error_vs_fp64": obs_err, "batched_vs_sequential": seq,
-                "config_sizes": cfg_rates, "adjoint": adj,
+                "config_sizes": cfg_rates, "fingering_grid_batch": grid_rates, "adjoint": adj,
                 "nonfinite_lattice0": obs.get("nonfinite", None)}
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -632,7 +655,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", default="batched_sweep",
-                    choices=("batched_sweep", "capillary", "fingering", "static_droplet", "roofline_box"))
+                    choices=("batched_sweep", "fingering_grid", "capillary", "fingering", "static_droplet",
+                             "roofline_box"))
     ap.add_argument("--precision", default="fp32", choices=("fp64", "fp32", "fp16", "bf16"))
     ap.add_argument("--lattices", type=int, default=64, help="channels of the batched sweep")
     ap.add_argument("--ty", type=int, default=0, help="tile height of k_step (4, 8, 16; 0 = default)")

@@ -279,6 +279,15 @@ def config_fingering(M: float = 1.0, Ca: float = 0.05, theta_deg: float = 90.0, 
     return displacement_channel(W=100, L=2000, x_I=100.0, seed=seed), fingering_params(M, Ca, theta_deg)
 
 
+def fingering_grid():
+    """The viscous-fingering study as one batch: a 2000x102 channel (width 100, interface at
+    x = 100, its own interface noise from seed i) for every (M, Ca, theta) of the grids,
+    M x Ca x theta = 5 x 3 x 5 = 75 channels; returns (geometries, params)."""
+    pts = [(M, Ca, th) for M in M_GRID for Ca in CA_GRID for th in THETA_GRID]
+    geoms, prms = zip(*[config_fingering(M=M, Ca=Ca, theta_deg=th, seed=i) for i, (M, Ca, th) in enumerate(pts)])
+    return list(geoms), list(prms)
+
+
 def config_wettability(theta_deg: float, seed: int = 0):
     """Sec. III.D.2 (wettability): 630x60 domain (58 fluid rows between two wall rows), flat
     initial interface at x = 30, Poiseuille inlet of maximum u0 = 0.1, pressure outlet,
