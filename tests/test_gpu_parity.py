@@ -291,6 +291,42 @@ def test_profiled_branched_steps_time_their_kernels_and_keep_the_bits():
     B.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16"])
+@pytest.mark.parametrize("ty", [4, 8, 16])
+def test_dependent_launches_of_the_tile_schedule_keep_the_bits(prec, ty):
+    # the tile schedule's kernels are programmatic dependent launches (the FP32 and 16-bit ones
+    # triggering their successor at the start of each block); while profiled they are plain
+    # launches with events between them.  100 direct steps either way give the same bits, and
+    # so do 100 steps replayed from the step graph (FP64, FP32; 16-bit storage draws other
+    # rounding keys there), on a single lattice (open columns, walls) and on a batch whose graph
+    # runs parallel branches
+    from paper_1707_00198_gb300 import lbcg
+    g1 = I.displacement_channel(W=20, L=110, x_I=25.0, seed=6, noise=1e-3)
+    p1 = I.fingering_params(M=5.0, Ca=0.1, theta_deg=60.0)
+    g2 = I.cylinder_droplet(60, 50, Rs=10.0, cx=30.0, cy=18.0, Rd=9.0, theta=math.radians(110), noise=1e-3,
+                            seed=13, analytic_normal=False)
+    p2 = I.Params(theta=math.radians(110), sigma=0.02)
+    for gs, ps in (([g1], [p1]), ([g1, g2, g1, g2], [p1, p2, p1, p2])):
+        runs = [lbcg.Lattice(gs, ps, prec) for _ in range(3)]
+        for L in runs:
+            L.set_tile(ty)
+        A, C, B = runs
+        lbcg.lbcg_profile(A.h, True)
+        for _ in range(100):
+            A.step(1)
+            C.step(1)
+        lbcg.lbcg_profile(A.h, False)
+        B.step(100)
+        for i in range(len(gs)):
+            a = A.populations(i)
+            assert np.isfinite(a).all()
+            assert np.array_equal(a, C.populations(i)), (prec, ty, len(gs), i)
+            if prec != "fp16":
+                assert np.array_equal(a, B.populations(i)), (prec, ty, len(gs), i)
+        for L in runs:
+            L.close()
+
+
 def test_graph_replay_matches_direct_steps():
     # 70 steps use two 32-step graph replays plus direct launches; 70 single calls use none
     g, p = I.config_static_droplet()
