@@ -181,9 +181,39 @@ def recorded_traffic(kernel: str, n_fluid: int):
         rec = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))[kernel]
     except Exception:
         return None
-    if rec.get("src_digest") != kernel_source_digest():
+    if rec.get("src_digest") != kernel_source_digest() or "dram_bytes_per_fluid_node" not in rec:
         return None
     return rec["dram_bytes_per_fluid_node"] * n_fluid
+
+
+def recorded_counter(kernel: str, key: str):
+    """A per-fluid-node figure of `kernel` recorded from ncu in profiles/ncu_traffic.json, or
+    None if it is absent or the kernel source changed since the counters were taken."""
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))[kernel]
+    except Exception:
+        return None
+    if rec.get("src_digest") != kernel_source_digest() or key not in rec:
+        return None
+    return rec[key]
+
+
+def fp64_rate_tflops(n: int = 4096, reps: int = 3) -> float:
+    """Measured FP64 rate of this GPU: cuBLAS DGEMM (torch.matmul of two float64 n x n
+    matrices), best of `reps`, CUDA events, 2 n^3 flops."""
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    best = float("inf")
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    del a, b
+    return 2 * n ** 3 / (best / 1e3) / 1e12
 
 
 def cpu_model() -> str:
@@ -554,6 +584,17 @@ def run_ours(args):
             "kernel_ms_source": f"separate pass of {Kp} steps launched as the graph's branches, CUDA events "
                                 "around each kernel; per step, the time during which at least one branch's "
                                 "kernel of that kind ran (union of the event intervals)"}
+    flops_node = recorded_counter(kname, "fp64_flops_per_fluid_node") if args.precision == "fp64" else None
+    if flops_node is not None:
+        # the FP64 sweep is bound by FP64 arithmetic, not by memory: its roofline is the FP64
+        # flops it executes (DFMA counted twice, DADD and DMUL once; from ncu) against the
+        # measured DGEMM rate (GB300's FP64 units: 1.25 TFLOP/s nominal)
+        fp64_peak = fp64_rate_tflops()
+        ach = flops_node * nf / (step_ms / 1e3) / 1e12
+        roof.update({"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak,
+                     "peak_source": "measured: cuBLAS DGEMM 4096^3 through torch.matmul, best of 3",
+                     "fp64_flops_per_fluid_node": flops_node, "hbm_achieved_gbs": achieved,
+                     "hbm_frac": achieved / peak})
     whole_gbs = alg_bytes * args.steps / (ms / 1e3) / 1e9
 
     # ---- end to end through the C ABI with host buffers (pinned): upload state, step, download
