@@ -257,6 +257,13 @@ void build_strips(lbcg_handle* h, std::vector<int4>& strips) {
     // row downwards, so that the two segments at each boundary reach its rows at about the
     // same time (their second read then hits L2).  (8192 x 4096 box: strip by strip instead,
     // 157 B of DRAM traffic per fluid node and 0.886 ms per sweep; this order 147 B, 0.827 ms.)
+    // The lattice's rows are cut into as many segments as the height asks for, of equal
+    // heights (72 rows at 64: 36 + 36, not 64 + 8): the same rows and warm-up rows in all, but
+    // blocks of about equal length (64-channel batch, FP32: 0.2988-0.3013 -> 0.2965 ms per step).
+    {
+      const int nseg = (L.ny + rows - 1) / rows;
+      rows = (L.ny + nseg - 1) / nseg;
+    }
     for (int y0 = 0, k = 0; y0 < L.ny; y0 += rows, ++k)
       for (int x0 = 0; x0 < L.nx; x0 += W) {
         const int y1 = std::min(y0 + rows, L.ny);
